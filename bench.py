@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the PFSM scan on GB300: GB/s scanned and matches/s, exact.
+
+One step = one pass of the whole scan (reinitialise at every position,
+advance every live instance, report every match) over one synthetic text:
+by default the position NFA of 256 DNA motifs (~5.3k states, delta rows as
+bitsets at load) over 64 MiB of GC=0.4 DNA with a motif planted every ~10 kB.
+
+Printed: ONE JSON line (rank 0) with
+  value      GB/s scanned, text resident in HBM, device-timed per step with
+             CUDA events on the scan's stream; L2 is flushed between steps
+             (the 64 MiB text fits in the 129 MB L2)
+  e2e        the same metric through the public API with host buffers: the
+             pinned text is copied to the device, scanned, and the matches
+             copied back inside the timed region
+  roofline   the tile kernel's algorithmic bytes (text read + 12 B per match
+             written) over its CUDA-event duration, against the measured HBM
+             copy bandwidth
+  cpu_baseline  the CPU oracle on a bounded sample of the same text
+  clocks     SM clocks and throttle reasons sampled during the timed region
+  workloads  the other scan shapes measured the same way (DNA DFA, byte trie)
+
+--impl reference times the CPU oracle (the only reference this method has)
+on the same workload, one bounded sample per step.
+
+Multi-GPU (torchrun): every rank scans its own text of the same shape (weak
+scaling, no collective on the data path); value = all bytes / max time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+HBM_FALLBACK = 6800.0
+
+WORKLOADS = {
+    "motif_nfa_64mib": "position NFA, 256 DNA motifs (~5.3k states), 64 MiB GC=0.4 text, "
+                       "motif planted every ~10 kB",
+    "dna_dfa_1mib": "random DFA, 64 states (dead 63, finals 1-8), 1 MiB uniform DNA text",
+    "byte_trie_1gib": "trie DFA of 1000 byte signatures (~19k states), 1 GiB uniform bytes, "
+                      "one signature planted per 64 KiB",
+}
+
+
+def make_workload(name, seed):
+    if name == "motif_nfa_64mib":
+        a, t, _, _ = W.workload_motif_nfa(seed)
+    elif name == "dna_dfa_1mib":
+        a, t = W.workload_dna_dfa(seed if seed else 1)
+    elif name == "byte_trie_1gib":
+        a, t, _, _, _ = W.workload_byte_trie(seed)
+    else:
+        raise ValueError(name)
+    return a, t
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(aut, text, seconds_target=12.0):
+    """The oracle as it is, single thread, on a prefix of the text sized to
+    take roughly `seconds_target` (probe on 256 KiB first)."""
+    import oracle
+    probe = min(len(text), 256 << 10)
+    t0 = time.perf_counter()
+    oracle.scan(aut, text[:probe])
+    dt = max(1e-6, time.perf_counter() - t0)
+    n = int(min(len(text), max(probe, probe * seconds_target / dt)))
+    n = max(probe, (n >> 16) << 16) if n > probe else probe
+    t0 = time.perf_counter()
+    m = oracle.scan(aut, text[:n])
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d bytes of the text (every match starting there), %.1f s, "
+                      "%d matches" % (n, dt, len(m)),
+            "matches_per_s": len(m) / dt}
+
+
+def device_time_steps(P, pf, aut_id, text_dev, out, status, steps, flush, stream):
+    """Per-step CUDA-event durations (ms) of pfsm_scan_async on `stream`,
+    with an L2 flush (untimed) before every step."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            evs[i][0].record(stream)
+            P.pfsm_scan_async(pf.ctx, aut_id, text_dev, None, out, status[i], stream=stream)
+            evs[i][1].record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1110_1716_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hbm, peak_kind = measured_peaks()
+    pf = P.Pfsm(local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def measure(name, steps, warmup, seed):
+        aut, text = make_workload(name, seed + rank)
+        aid = pf.load(aut)
+        if args.params:
+            P.pfsm_set_params(pf.ctx, aid, json.loads(args.params))
+        tdev = pf.to_device(text)
+        n = len(text)
+        # size the output from one counting pass, then keep it resident
+        st, cnt = P.pfsm_scan(pf.ctx, aid, tdev, None, None, 0)
+        cap = int(cnt) + 1024
+        out = torch.empty((cap, 3), dtype=torch.int32, device=dev)
+        status = torch.zeros((max(steps, warmup), 2), dtype=torch.int64, device=dev)
+        device_time_steps(P, pf, aid, tdev, out, status, warmup, flush, stream)
+        P.pfsm_set_timing(pf.ctx, True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            time.sleep(0.2)
+            t0 = time.perf_counter()
+            ms = device_time_steps(P, pf, aid, tdev, out, status, steps, flush, stream)
+            wall = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        kms, klaunch = P.pfsm_kernel_time(pf.ctx)
+        P.pfsm_set_timing(pf.ctx, False)
+        stat = status[:steps].cpu().numpy()
+        assert (stat[:, 1] == 0).all(), "scan reported an error"
+        assert (stat[:, 0] == cnt).all(), "match count changed between steps"
+        step_ms = float(np.mean(ms))
+        if world > 1:
+            t = torch.tensor([step_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            step_ms = float(t.item())
+        kernel_ms = kms / max(1, klaunch)
+        algo_bytes = n + 12 * int(cnt)
+        kind = 0 if hasattr(aut, "delta") else 1
+        launches_per_step = 2 if kind == 0 else 1
+        res = {
+            "workload": name, "desc": WORKLOADS[name], "bytes": n, "matches": int(cnt),
+            "ms_per_step": step_ms, "gbps": n / (step_ms * 1e-3) / 1e9 * world,
+            "matches_per_s": cnt / (step_ms * 1e-3) * world,
+            "kernel_ms": kernel_ms, "params": P.pfsm_get_params(pf.ctx, aid),
+            "roofline": {"bound": "hbm", "achieved": algo_bytes / (kernel_ms * 1e-3) / 1e9,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": algo_bytes / (kernel_ms * 1e-3) / 1e9 / hbm,
+                         "traffic": None, "peak_source": peak_kind,
+                         "algorithmic_bytes": algo_bytes},
+            "clocks": clk.summary(), "gpu_launches": launches_per_step * steps,
+            "wall_s": wall,
+        }
+        # end to end through the public API: pinned host text -> device ->
+        # scan -> matches back to the host, every step
+        host = torch.from_numpy(text).pin_memory()
+        host_out = torch.empty((cap, 3), dtype=torch.int32).pin_memory()
+        dbuf = torch.empty(n, dtype=torch.uint8, device=dev)
+        e2e = []
+        for i in range(max(3, min(steps, 20))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                dbuf.copy_(host, non_blocking=True)
+                st, c2 = P.pfsm_scan(pf.ctx, aid, dbuf, None, out, cap, stream=stream)
+                host_out[:c2].copy_(out[:c2], non_blocking=True)
+            stream.synchronize()
+            e2e.append(time.perf_counter() - t0)
+            assert c2 == cnt
+        e2e_s = float(np.median(e2e))
+        res["e2e"] = {"value": n / e2e_s / 1e9 * world, "unit": "GB/s",
+                      "h2d_bytes_per_step": n, "d2h_bytes_per_step": 12 * int(cnt)}
+        res["aut"], res["text"] = aut, text
+        P.pfsm_unload(pf.ctx, aid)
+        del tdev, out, dbuf
+        return res
+
+    main = measure(args.workload, args.steps, args.warmup, args.seed)
+    others = {}
+    if not args.only:
+        for name in WORKLOADS:
+            if name == args.workload:
+                continue
+            steps = 200 if name == "dna_dfa_1mib" else 20
+            r = measure(name, steps, 5, 0)
+            others[name] = {k: r[k] for k in ("desc", "bytes", "matches", "ms_per_step", "gbps",
+                                              "matches_per_s", "kernel_ms", "roofline", "e2e",
+                                              "params")}
+    if rank != 0:
+        return None
+    line = {
+        "metric": "GB/s scanned (exact match set) of the PFSM scan",
+        "value": main["gbps"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded generators; no public dataset exists for this method)",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload],
+                   "bytes_per_gpu": main["bytes"], "matches": main["matches"],
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": "replicas" if world == 1 else "weak, one text per rank",
+                   "params": main["params"]},
+        "matches_per_s": main["matches_per_s"],
+        "kernel_ms": main["kernel_ms"],
+        "roofline": main["roofline"],
+        "e2e": main["e2e"],
+        "clocks": main["clocks"],
+        "gpu_launches": main["gpu_launches"],
+        "workloads": others,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(main["aut"], main["text"])
+    return line
+
+
+def run_reference(args):
+    """The oracle (plain C, one host core) on bounded samples of the same
+    workload, one sample per step."""
+    import oracle
+    oracle.build()
+    aut, text = make_workload(args.workload, args.seed)
+    probe = min(len(text), 128 << 10)
+    t0 = time.perf_counter()
+    oracle.scan(aut, text[:probe])
+    dt = max(1e-6, time.perf_counter() - t0)
+    budget = 150.0 / max(1, args.steps + args.warmup)     # seconds per step
+    n = int(min(len(text), max(probe, probe * budget / dt)))
+    n = max(4096, (n >> 12) << 12)
+    times = []
+    cnt = 0
+    for i in range(args.warmup + args.steps):
+        lo = (i * n) % max(1, len(text) - n)
+        t0 = time.perf_counter()
+        m = oracle.scan(aut, text, lo, lo + n)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+            cnt += len(m)
+    step_s = float(np.mean(times))
+    value = n / step_s / 1e9
+    return {
+        "impl": "reference",
+        "metric": "GB/s scanned (exact match set) of the PFSM scan",
+        "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d starts per step (matches starting in a window of the "
+                                   "text), %d matches over the timed steps" % (n, cnt)},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="motif_nfa_64mib", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--params", default="", help="JSON pfsm_params overrides")
+    ap.add_argument("--only", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+
+    import __graft_entry__
+    __graft_entry__.build()
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * pfsm.h - C ABI of the GB300 PFSM scan library (libpfsm.so).
+ *
+ * The operation (Sec. III.A-B of Quesada, Berzal, Cortijo, "Treating Insomnia,
+ * Amnesia, and Acalculia in Regular Expression Matching"): a Parallel Finite
+ * State Machine (Sigma, Q, q0, delta, F, L, l) is reinitialised at every input
+ * symbol, so an instance starts at q0 at every position i and carries i as its
+ * tag; every live instance advances on each symbol through delta; whenever a
+ * transition lands on a final state f, (start = tag, end = current position,
+ * f) is a match. The library reports the full set
+ *
+ *     M(t, A) = { (i, j, f) : 0 <= i <= j < n, f in F, f in delta^({q0}, t[i..j]) }
+ *
+ * with 0-based, inclusive ends (Fig. 2: "c" is reported at [2-2]). Empty
+ * matches are not reported (tables are epsilon-free; a final q0 does not match
+ * the empty string). Labels l: F -> L stay with the caller: results carry the
+ * final state, which the caller maps to its label.
+ *
+ * Conventions for every call:
+ *   - every function returns an int status, PFSM_OK (0) on success;
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     device memory of the context's device (for example torch tensors);
+ *   - tables passed at load are copied; the caller may free them on return;
+ *   - texts and outputs are caller-owned device memory; the library never
+ *     frees them;
+ *   - streams are the caller's (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream). Work is ordered on that stream;
+ *   - a context may be used from one host thread at a time, except that scans
+ *     on different streams may be issued from different threads;
+ *   - state ids are 0..Q-1 with Q <= 32767; symbols are the bytes 0..S-1 with
+ *     1 <= S <= 256; positions are 32-bit, so texts are shorter than 2^32.
+ */
+#ifndef PFSM_H
+#define PFSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define PFSM_OK 0
+#define PFSM_E_INVAL 1    /* bad argument, bad table, or a text symbol >= S */
+#define PFSM_E_NOMEM 2    /* device memory or the residency budget exhausted */
+#define PFSM_E_OVERFLOW 3 /* more matches than the output capacity */
+#define PFSM_E_NOENT 4    /* unknown or unloaded automaton id */
+#define PFSM_E_TIMEOUT 5  /* a bounded device wait expired */
+#define PFSM_E_CUDA 6     /* a CUDA runtime call failed */
+
+typedef struct pfsm_ctx pfsm_ctx;
+typedef int32_t pfsm_aut;
+
+/* One match: the instance started at `start` reached final state `state`
+ * after consuming t[start..end] (inclusive). */
+typedef struct {
+    uint32_t start, end, state;
+} pfsm_match;
+
+/* One match of a batch: as pfsm_match, for text number `text` of the batch. */
+typedef struct {
+    uint32_t text, start, end, state;
+} pfsm_bmatch;
+
+/* One job of a batch: scan `n` bytes at device address `text` with `aut`. */
+typedef struct {
+    pfsm_aut aut;
+    uint32_t reserved; /* must be 0 */
+    const uint8_t *text;
+    uint64_t n;
+} pfsm_job;
+
+/* Tunable launch parameters of one automaton (0 = library default). */
+typedef struct {
+    int32_t prefix_k;   /* depth of the start-prefix table: the first k steps of
+                           every instance are looked up once per k-gram;
+                           -1 = off (every instance steps from q0) */
+    int32_t tile;       /* starts owned by one CTA tile (multiple of 4096) */
+    int32_t halo;       /* text staged past the tile end (multiple of 16) */
+    int32_t threads;    /* threads per CTA: 128, 256, 512 or 1024 */
+    int32_t spt;        /* starts per thread per filter round: 4, 8 or 16 */
+    int32_t table_smem; /* delta table in shared memory: 1 yes, 0 no, -1 auto */
+    int32_t ctas_per_sm;/* persistent CTAs per SM (0 = occupancy maximum) */
+    int32_t reserved;
+} pfsm_params;
+
+/* Residency counters of a context. */
+typedef struct {
+    uint64_t resident_bytes, budget_bytes;
+    uint64_t loads, evictions, reloads;
+    int32_t resident, loaded;
+} pfsm_stats;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context on CUDA device `device`. `budget_bytes` bounds the device
+ * memory held by resident automata (0 = 8 GiB); scans reload evicted
+ * automata and evict the least recently used ones to stay inside it (the
+ * device form of the paper's treatment of insomnia, Sec. I-II). Errors:
+ * E_INVAL (bad device), E_CUDA, E_NOMEM. */
+int pfsm_ctx_create(int device, uint64_t budget_bytes, pfsm_ctx **out);
+
+/* Release every automaton and scratch buffer of the context. Waits for the
+ * context's own work to finish. NULL is accepted. */
+int pfsm_ctx_destroy(pfsm_ctx *ctx);
+
+/* ------------------------------------------------------------------ automata */
+/* Load a DFA-form machine (Sec. II: delta: Q x Sigma -> Q).
+ *   delta     host, int16 [Q][S] row-major, every entry in [0, Q)
+ *   q0        initial state
+ *   dead      an absorbing non-final state (every entry of its row is `dead`,
+ *             and it is not final); instances entering it are dropped.
+ *             -1 = no dead state: instances then live to the end of the text
+ *   is_final  host, uint8 [Q], nonzero = final
+ * The table is copied to the device (charged to the budget) along with a
+ * start-prefix table derived from it. Errors: E_INVAL (Q outside 1..32767,
+ * S outside 1..256, q0/dead out of range, an entry out of range, dead not
+ * absorbing or final), E_NOMEM. */
+int pfsm_load_dfa(pfsm_ctx *ctx, const int16_t *delta, int32_t Q, int32_t S, int32_t q0,
+                  int32_t dead, const uint8_t *is_final, pfsm_aut *out_id);
+
+/* Load an NFA-form machine, run without determinisation (Sec. II: delta:
+ * Q x Sigma -> P(Q); Sec. III.A: a PFSM's delta is NFA-like).
+ *   delta_bits  host, uint32 [Q][S][W], W = ceil(Q/32): bit (q' % 32) of word
+ *               q' / 32 of row (q, a) is set iff q' is in delta(q, a)
+ *   q0, is_final as for pfsm_load_dfa
+ * An instance whose state set becomes empty is dropped. The machine must be
+ * epsilon-free (remove epsilon edges first; the union construction of
+ * Sec. III.A is epsilon-free after that). Errors: E_INVAL, E_NOMEM. */
+int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t S, int32_t q0,
+                  const uint8_t *is_final, pfsm_aut *out_id);
+
+/* Drop the device copy of an automaton (its host copy stays); the next scan
+ * that names it reloads it. Errors: E_NOENT. */
+int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut);
+
+/* Forget an automaton entirely; its id becomes invalid. Errors: E_NOENT. */
+int pfsm_unload(pfsm_ctx *ctx, pfsm_aut aut);
+
+/* Launch parameters of an automaton (the autotuner sets them). `p` may be
+ * NULL to restore the defaults. Errors: E_NOENT, E_INVAL. */
+int pfsm_set_params(pfsm_ctx *ctx, pfsm_aut aut, const pfsm_params *p);
+int pfsm_get_params(pfsm_ctx *ctx, pfsm_aut aut, pfsm_params *out);
+
+/* ------------------------------------------------------------------ scanning */
+/* Report every match of `aut` in the text (Sec. III.B; the result is the set
+ * M above, in unspecified order).
+ *   text_dev   device, n bytes, every byte < S (a byte >= S fails with
+ *              E_INVAL after the scan; the output is then unspecified)
+ *   out_dev    device, room for `cap` pfsm_match entries
+ *   n_matches  host; receives |M| on PFSM_OK and on PFSM_E_OVERFLOW (when
+ *              |M| > cap: the first contents of out_dev are unspecified and
+ *              the caller retries with cap >= *n_matches)
+ *   stream     cudaStream_t or NULL
+ * Blocks until the scan has finished on `stream`. n = 0 yields 0 matches.
+ * Errors: E_NOENT, E_INVAL (n >= 2^32, NULL pointers with n > 0 or cap > 0,
+ * bad symbol), E_OVERFLOW, E_NOMEM (reload), E_TIMEOUT, E_CUDA. */
+int pfsm_scan(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
+              pfsm_match *out_dev, uint64_t cap, uint64_t *n_matches, void *stream);
+
+/* Asynchronous form of pfsm_scan: enqueues the scan on `stream` and returns.
+ * On completion, status_dev (device, 2 x uint64) holds { |M|, error bits }
+ * where error bit 0 = a symbol >= S, bit 1 = a device wait timed out.
+ * Capturable in a CUDA graph once the automaton is resident (a scan
+ * of a non-resident automaton reloads it, which is a host-synchronous copy).
+ * Errors detected on the host are returned directly. */
+int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
+                    pfsm_match *out_dev, uint64_t cap, uint64_t *status_dev, void *stream);
+
+/* Scan k texts, each with its own automaton, in one persistent launch (the
+ * regex and data partitioning of Sec. III.D combined: every (text, tile) is a
+ * work item).
+ *   jobs     host, k entries; texts are device pointers
+ *   out_dev  device, room for `cap` pfsm_bmatch entries (text = job index)
+ *   counts   host, k entries; receives |M| per job (may be NULL)
+ *   total    host; receives the sum (also on PFSM_E_OVERFLOW)
+ * Blocks until done. Errors: as pfsm_scan, per job. */
+int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
+                    uint64_t cap, uint64_t *counts, uint64_t *total, void *stream);
+
+/* ------------------------------------------------------------------ misc */
+int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);
+
+/* Kernel timing: when enabled, every scan records CUDA events around its
+ * tile kernel on the scan's stream; pfsm_kernel_time returns the summed
+ * milliseconds and launch count since the last reset. */
+int pfsm_set_timing(pfsm_ctx *ctx, int enable);
+int pfsm_kernel_time(pfsm_ctx *ctx, double *ms, uint64_t *launches);
+
+/* Static string for a status code. */
+const char *pfsm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFSM_H */

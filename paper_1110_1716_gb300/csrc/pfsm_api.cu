@@ -1,0 +1,790 @@
+// Host side of libpfsm: contexts, machine loading and residency, scans.
+//
+// A machine is validated and turned into its device encoding once, at load
+// (Sec. III.A: the PFSM runs on the caller's unconverted DFA or NFA table;
+// nothing is determinised or compacted). Device copies live under a byte
+// budget with least-recently-used eviction and transparent reload: the
+// device form of the paper's remedy for insomnia (Sec. I-II), where cold
+// automata leave fast memory and come back when needed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "pfsm_internal.h"
+
+using namespace pfsm;
+
+namespace {
+
+constexpr uint64_t kDefaultBudget = 8ull << 30;
+constexpr uint32_t kCarryCap = 1u << 20;     // carry entries per stream slot
+constexpr uint32_t kSmemMax = 232448;        // opt-in shared memory per CTA
+
+struct Machine {
+    int kind = 0;  // 0 DFA, 1 NFA
+    int Q = 0, S = 0, q0 = 0, dead = -1;
+    std::vector<uint8_t> fin;
+    // device encodings (host images)
+    std::vector<uint16_t> dtab;       // DFA [Q][S]
+    std::vector<uint32_t> off;        // NFA CSR [Q*S+1]
+    std::vector<uint16_t> tgt;        // NFA targets
+    // start-prefix table
+    int k = 0, sbits = 1;
+    std::vector<uint16_t> memo;
+    std::vector<uint32_t> rec_off, pool;
+    pfsm_params params{};
+    // residency
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    DevMachine dm{};
+    uint64_t last_use = 0;
+    bool was_resident = false;
+};
+
+constexpr int kEventRing = 256;   // timed launches kept in flight per stream
+
+struct Slot {   // per-stream scratch
+    unsigned long long *status = nullptr;   // device [2]
+    uint32_t *carry_n = nullptr;
+    uint32_t *carry = nullptr;
+    unsigned long long *host_status = nullptr;   // pinned [2]
+    // ring of (start, end) events around timed tile-kernel launches
+    cudaEvent_t ev[2 * kEventRing] = {};
+    int ev_head = 0, ev_pending = 0;
+};
+
+}  // namespace
+
+struct pfsm_ctx {
+    int device = 0;
+    int nsm = 0;
+    uint64_t budget = kDefaultBudget;
+    uint64_t resident_bytes = 0;
+    uint64_t clock = 0;
+    uint64_t n_loads = 0, n_evict = 0, n_reload = 0;
+    std::map<int, Machine> machines;
+    int next_id = 1;
+    std::map<cudaStream_t, Slot> slots;
+    std::mutex mu;
+    bool timing = false;
+    double time_ms = 0.0;
+    uint64_t time_launches = 0;
+    // batch state (batch.cu)
+    void *batch = nullptr;
+};
+
+namespace {
+
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int ceil_log2(int S) {
+    int b = 0;
+    while ((1 << b) < S) ++b;
+    return std::max(1, b);
+}
+
+// Default depth of the start-prefix table: the k-gram index has k * sbits
+// bits; the table holds 2^(k*sbits) uint16 entries kept in shared memory.
+int default_k(const Machine &m) {
+    if (m.sbits >= 8) return m.kind == 0 ? 2 : 1;
+    const int max_bits = m.kind == 0 ? 14 : 12;   // 32 KB / 8 KB of entries
+    int k = std::max(1, max_bits / m.sbits);
+    return std::min(k, 8);
+}
+
+// ---- start-prefix table ---------------------------------------------------
+// DFA: entry for k-gram w = outcome of stepping q0 through w.
+void build_memo_dfa(Machine &m) {
+    const int k = m.k;
+    if (k <= 0) {
+        m.memo.clear();
+        return;
+    }
+    const uint32_t nent = 1u << (k * m.sbits);
+    const uint32_t smask = (1u << m.sbits) - 1;
+    m.memo.assign(nent + (nent & 1), PT_SKIP);
+    for (uint32_t w = 0; w < nent; ++w) {
+        int s = m.q0;
+        bool fin_seen = false, died = false, bad = false;
+        for (int j = 0; j < k; ++j) {
+            const int a = (w >> (j * m.sbits)) & smask;
+            if (a >= m.S) {
+                bad = true;
+                break;
+            }
+            const uint16_t e = m.dtab[(size_t)s * m.S + a];
+            if (e == DEAD16) {
+                died = true;
+                break;
+            }
+            s = e & 0x7FFF;
+            if (e & FINAL_BIT) fin_seen = true;
+        }
+        if (bad) continue;   // such k-grams raise E_INVAL anyway
+        if (fin_seen) m.memo[w] = PT_WALK;
+        else if (died) m.memo[w] = PT_SKIP;
+        else m.memo[w] = static_cast<uint16_t>(s);
+    }
+}
+
+// NFA: entry for k-gram w = record of the matches met within the first k
+// steps from {q0} and the state set after them; equal records are shared.
+struct NfaMemoBuilder {
+    Machine &m;
+    std::map<std::vector<uint32_t>, uint32_t> recs;
+    std::vector<uint32_t> mark;
+    uint32_t stamp = 0;
+    bool ok = true;
+
+    explicit NfaMemoBuilder(Machine &mm) : m(mm), mark(mm.Q, 0) {}
+
+    uint16_t record(const std::vector<uint32_t> &matches, const std::vector<uint16_t> &set) {
+        std::vector<uint32_t> rec;
+        rec.push_back(static_cast<uint32_t>(matches.size()) |
+                      (static_cast<uint32_t>(set.size()) << 16));
+        rec.insert(rec.end(), matches.begin(), matches.end());
+        for (uint16_t q : set) rec.push_back(q);
+        auto it = recs.find(rec);
+        if (it != recs.end()) return static_cast<uint16_t>(it->second);
+        const uint32_t id = static_cast<uint32_t>(m.rec_off.size());
+        if (id >= PT_WALK || matches.size() > 0xFFFF || set.size() > 0xFFFF) {
+            ok = false;
+            return PT_SKIP;
+        }
+        recs.emplace(rec, id);
+        m.rec_off.push_back(static_cast<uint32_t>(m.pool.size()));
+        m.pool.insert(m.pool.end(), rec.begin(), rec.end());
+        return static_cast<uint16_t>(id);
+    }
+
+    // depth symbols consumed (index bits below depth*sbits fixed to prefix)
+    void dfs(int depth, uint32_t prefix, const std::vector<uint16_t> &set,
+             const std::vector<uint32_t> &matches) {
+        if (!ok) return;
+        const int k = m.k, sb = m.sbits;
+        if (depth == k) {
+            if (!matches.empty() || !set.empty()) m.memo[prefix] = record(matches, set);
+            return;
+        }
+        if (set.empty()) {
+            // nothing survives: every extension of this prefix has this record
+            if (matches.empty()) return;
+            const uint16_t id = record(matches, set);
+            const uint32_t rest = static_cast<uint32_t>(k - depth) * sb;
+            for (uint32_t hiw = 0; hiw < (1u << rest); ++hiw)
+                m.memo[prefix | (hiw << (depth * sb))] = id;
+            return;
+        }
+        for (int a = 0; a < (1 << sb); ++a) {
+            if (a >= m.S) continue;   // such k-grams raise E_INVAL anyway
+            std::vector<uint16_t> next;
+            std::vector<uint32_t> nm = matches;
+            ++stamp;
+            for (uint16_t q : set) {
+                const uint32_t lo = m.off[(size_t)q * m.S + a], hi = m.off[(size_t)q * m.S + a + 1];
+                for (uint32_t e = lo; e < hi; ++e) {
+                    const uint16_t t = m.tgt[e];
+                    const uint16_t ts = t & 0x7FFF;
+                    if (mark[ts] == stamp) continue;
+                    mark[ts] = stamp;
+                    next.push_back(ts);
+                    if (t & FINAL_BIT) nm.push_back((static_cast<uint32_t>(depth) << 16) | ts);
+                }
+            }
+            std::sort(next.begin(), next.end());
+            dfs(depth + 1, prefix | (static_cast<uint32_t>(a) << (depth * sb)), next, nm);
+        }
+    }
+};
+
+bool build_memo_nfa(Machine &m) {
+    m.rec_off.clear();
+    m.pool.clear();
+    if (m.k <= 0) {
+        m.memo.clear();
+        return true;
+    }
+    const uint32_t nent = 1u << (m.k * m.sbits);
+    m.memo.assign(nent + (nent & 1), PT_SKIP);
+    NfaMemoBuilder b(m);
+    b.dfs(0, 0, {static_cast<uint16_t>(m.q0)}, {});
+    if (!b.ok) return false;
+    if (m.pool.empty()) m.pool.push_back(0);
+    if (m.rec_off.empty()) m.rec_off.push_back(0);
+    return true;
+}
+
+bool build_memo(Machine &m) {
+    if (m.kind == 0) {
+        build_memo_dfa(m);
+        return true;
+    }
+    return build_memo_nfa(m);
+}
+
+// ---- residency --------------------------------------------------------------
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t device_bytes(const Machine &m) {
+    size_t b = align256(m.memo.size() * 2 + 4);
+    if (m.kind == 0) {
+        b += align256(m.dtab.size() * 2 + 4);
+    } else {
+        b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
+             align256(m.rec_off.size() * 4) + align256(m.pool.size() * 4);
+    }
+    return b;
+}
+
+void release(pfsm_ctx *ctx, Machine &m) {
+    if (m.dev) {
+        cudaFree(m.dev);
+        m.dev = nullptr;
+        ctx->resident_bytes -= m.dev_bytes;
+        m.dev_bytes = 0;
+    }
+}
+
+int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id) {
+    while (ctx->resident_bytes + need > ctx->budget) {
+        Machine *victim = nullptr;
+        for (auto &kv : ctx->machines) {
+            if (kv.first == keep_id || !kv.second.dev) continue;
+            if (!victim || kv.second.last_use < victim->last_use) victim = &kv.second;
+        }
+        if (!victim) return PFSM_E_NOMEM;
+        release(ctx, *victim);
+        ctx->n_evict++;
+    }
+    return PFSM_OK;
+}
+
+int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
+    m.last_use = ++ctx->clock;
+    if (m.dev) return PFSM_OK;
+    const size_t bytes = device_bytes(m);
+    int st = evict_lru(ctx, bytes, id);
+    if (st) return st;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return PFSM_E_NOMEM;
+    }
+    std::vector<uint8_t> img(bytes, 0);
+    size_t o = 0;
+    auto put = [&](const void *src, size_t n) {
+        const size_t at = o;
+        if (n) memcpy(img.data() + o, src, n);
+        o += align256(n + 4);
+        return at;
+    };
+    DevMachine dm{};
+    dm.kind = m.kind;
+    dm.Q = m.Q;
+    dm.S = m.S;
+    dm.q0 = m.q0;
+    dm.k = m.k;
+    dm.sbits = m.sbits;
+    dm.memo_n = m.k > 0 ? (1u << (m.k * m.sbits)) : 0;
+    dm.Wq = (m.Q + 31) / 32;
+    uint8_t *base = static_cast<uint8_t *>(p);
+    const size_t o_memo = put(m.memo.data(), m.memo.size() * 2);
+    dm.memo = reinterpret_cast<const uint16_t *>(base + o_memo);
+    if (m.kind == 0) {
+        const size_t o_tab = put(m.dtab.data(), m.dtab.size() * 2);
+        dm.dtab = reinterpret_cast<const uint16_t *>(base + o_tab);
+    } else {
+        o = align256(o);
+        const size_t o_off = o;
+        memcpy(img.data() + o, m.off.data(), m.off.size() * 4);
+        o += align256(m.off.size() * 4);
+        const size_t o_tgt = put(m.tgt.data(), m.tgt.size() * 2);
+        const size_t o_ro = o;
+        memcpy(img.data() + o, m.rec_off.data(), m.rec_off.size() * 4);
+        o += align256(m.rec_off.size() * 4);
+        const size_t o_pool = o;
+        memcpy(img.data() + o, m.pool.data(), m.pool.size() * 4);
+        o += align256(m.pool.size() * 4);
+        dm.off = reinterpret_cast<const uint32_t *>(base + o_off);
+        dm.tgt = reinterpret_cast<const uint16_t *>(base + o_tgt);
+        dm.rec_off = reinterpret_cast<const uint32_t *>(base + o_ro);
+        dm.pool = reinterpret_cast<const uint32_t *>(base + o_pool);
+    }
+    if (o > bytes) {   // layout and size disagree: a bug, fail loudly
+        cudaFree(p);
+        return PFSM_E_INVAL;
+    }
+    if (cudaMemcpy(p, img.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(p);
+        return PFSM_E_CUDA;
+    }
+    m.dev = p;
+    m.dev_bytes = bytes;
+    m.dm = dm;
+    ctx->resident_bytes += bytes;
+    if (m.was_resident) ctx->n_reload++;
+    m.was_resident = true;
+    return PFSM_OK;
+}
+
+Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->slots.find(s);
+    if (it != ctx->slots.end()) return &it->second;
+    Slot sl;
+    void *p = nullptr;
+    const size_t bytes = 64 + static_cast<size_t>(kCarryCap) * 12;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    sl.status = static_cast<unsigned long long *>(p);
+    sl.carry_n = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(p) + 16);
+    sl.carry = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(p) + 64);
+    if (cudaMallocHost(&sl.host_status, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return nullptr;
+    }
+    for (int i = 0; i < 2 * kEventRing; ++i) cudaEventCreate(&sl.ev[i]);
+    return &ctx->slots.emplace(s, sl).first->second;
+}
+
+void fill_defaults(const Machine &m, pfsm_params &p) {
+    if (p.prefix_k == 0) p.prefix_k = default_k(m);
+    if (p.tile == 0) p.tile = 16384;
+    if (p.halo == 0) p.halo = 2048;
+    if (p.threads == 0) p.threads = 512;
+    if (p.spt == 0) p.spt = 8;
+    if (p.table_smem == 0) p.table_smem = -1;
+}
+
+int validate_params(const Machine &m, const pfsm_params &p) {
+    if (p.prefix_k < -1 || p.prefix_k > 8) return PFSM_E_INVAL;
+    if (p.prefix_k > 0 && p.prefix_k * m.sbits > 16) return PFSM_E_INVAL;
+    if (p.tile < 4096 || p.tile > 49152 || p.tile % 4096) return PFSM_E_INVAL;
+    if (p.halo < 16 || p.halo > 16384 || p.halo % 16) return PFSM_E_INVAL;
+    if (p.threads != 128 && p.threads != 256 && p.threads != 512) return PFSM_E_INVAL;
+    if (p.spt != 8) return PFSM_E_INVAL;
+    if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
+    if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
+    return PFSM_OK;
+}
+
+// Apply the params' prefix depth to the machine (rebuilding its table).
+int apply_k(pfsm_ctx *ctx, Machine &m) {
+    const int k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
+    if (k == m.k && (k == 0 || !m.memo.empty())) return PFSM_OK;
+    const bool was_resident = m.dev != nullptr;
+    release(ctx, m);
+    m.k = k;
+    if (!build_memo(m)) return PFSM_E_INVAL;
+    (void)was_resident;
+    return PFSM_OK;
+}
+
+struct Plan {
+    ScanArgs a;
+    int threads, grid;
+    uint32_t smem;
+};
+
+// Launch geometry and shared-memory layout of one scan.
+int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, Plan &pl) {
+    const pfsm_params &p = m.params;
+    ScanArgs &a = pl.a;
+    memset(&a, 0, sizeof(a));
+    a.text = text;
+    a.n = static_cast<uint32_t>(n);
+    a.tile = p.tile;
+    a.halo = p.halo;
+    a.ntiles = static_cast<uint32_t>((n + p.tile - 1) / p.tile);
+    a.text_buf = (p.tile + p.halo + 16 + 127) & ~127u;
+    a.aligned = (reinterpret_cast<uintptr_t>(text) & 15) == 0;
+    a.Q = m.Q;
+    a.S = m.S;
+    a.q0 = m.q0;
+    a.k = m.k;
+    a.sbits = m.sbits;
+    a.memo_n = m.dm.memo_n;
+    a.memo = m.dm.memo;
+    a.dtab = m.dm.dtab;
+    a.off = m.dm.off;
+    a.tgt = m.dm.tgt;
+    a.rec_off = m.dm.rec_off;
+    a.pool = m.dm.pool;
+    a.Wq = m.kind == 1 ? m.dm.Wq : 0;
+    const uint32_t round = 8u * p.threads;
+    uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
+    // table placement: shared memory when asked, or (auto) when small
+    a.tab_smem = 0;
+    if (m.kind == 0) {
+        if (p.table_smem == 1) a.tab_smem = 1;
+        else if (p.table_smem == -1 && tab_bytes <= 48 * 1024) a.tab_smem = 1;
+    }
+    a.qcap = 2 * round;
+    uint32_t smem = layout_smem(a, m.kind, p.threads, p.spt);
+    if (smem > kSmemMax) {
+        a.qcap = round;
+        smem = layout_smem(a, m.kind, p.threads, p.spt);
+    }
+    if (smem > kSmemMax && a.tab_smem && p.table_smem == -1) {
+        a.tab_smem = 0;
+        smem = layout_smem(a, m.kind, p.threads, p.spt);
+    }
+    if (smem > kSmemMax) return PFSM_E_INVAL;
+    int occ = max_ctas_per_sm(m.kind, m.sbits, p.threads, smem, a.tab_smem != 0);
+    if (occ <= 0) return PFSM_E_INVAL;
+    if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
+    pl.threads = p.threads;
+    pl.smem = smem;
+    pl.grid = static_cast<int>(std::min<uint64_t>(a.ntiles, static_cast<uint64_t>(ctx->nsm) * occ));
+    if (pl.grid < 1) pl.grid = 1;
+    return PFSM_OK;
+}
+
+// Accumulate the durations of timed launches, oldest first; `keep` pairs
+// may stay pending (0 drains all of them, waiting for their completion).
+void collect_timing(pfsm_ctx *ctx, Slot *slot, int keep) {
+    while (slot->ev_pending > keep) {
+        const int i = (slot->ev_head - slot->ev_pending + kEventRing) % kEventRing;
+        float ms = 0.f;
+        cudaEventSynchronize(slot->ev[2 * i + 1]);
+        if (cudaEventElapsedTime(&ms, slot->ev[2 * i], slot->ev[2 * i + 1]) == cudaSuccess) {
+            ctx->time_ms += ms;
+            ctx->time_launches += 1;
+        }
+        slot->ev_pending--;
+    }
+}
+
+int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, uint32_t *out,
+                 uint64_t cap, unsigned long long *status, Slot *slot, cudaStream_t s) {
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    Machine &m = it->second;
+    int st = make_resident(ctx, aut, m);
+    if (st) return st;
+    if (cudaMemsetAsync(status, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
+        return PFSM_E_CUDA;
+    if (n == 0) return PFSM_OK;
+    Plan pl;
+    st = plan_scan(ctx, m, text, n, pl);
+    if (st) return st;
+    pl.a.out = out;
+    pl.a.cap = cap;
+    pl.a.status = status;
+    pl.a.carry = slot->carry;
+    pl.a.carry_n = slot->carry_n;
+    pl.a.carry_cap = kCarryCap;
+    if (m.kind == 0 && cudaMemsetAsync(slot->carry_n, 0, sizeof(uint32_t), s) != cudaSuccess)
+        return PFSM_E_CUDA;
+    int ev = -1;
+    if (ctx->timing) {
+        collect_timing(ctx, slot, kEventRing - 1);
+        ev = slot->ev_head;
+        cudaEventRecord(slot->ev[2 * ev], s);
+    }
+    cudaError_t e = launch_scan(pl.a, m.kind, pl.threads, pl.grid, s);
+    if (ev >= 0) {
+        cudaEventRecord(slot->ev[2 * ev + 1], s);
+        slot->ev_head = (slot->ev_head + 1) % kEventRing;
+        slot->ev_pending++;
+    }
+    if (e != cudaSuccess) return PFSM_E_CUDA;
+    if (m.kind == 0) {
+        e = launch_carry(pl.a, 2 * ctx->nsm, s);
+        if (e != cudaSuccess) return PFSM_E_CUDA;
+    }
+    return PFSM_OK;
+}
+
+int finish_status(const unsigned long long *hs, uint64_t cap, uint64_t *n_matches) {
+    if (n_matches) *n_matches = hs[0];
+    if (hs[1] & ERR_TIMEOUT) return PFSM_E_TIMEOUT;
+    if (hs[1] & ERR_SYMBOL) return PFSM_E_INVAL;
+    if (hs[0] > cap) return PFSM_E_OVERFLOW;
+    return PFSM_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int pfsm_ctx_create(int device, uint64_t budget_bytes, pfsm_ctx **out) {
+    if (!out) return PFSM_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return PFSM_E_CUDA;
+    }
+    if (device < 0 || device >= ndev) return PFSM_E_INVAL;
+    DeviceGuard g(device);
+    pfsm_ctx *c = new pfsm_ctx();
+    c->device = device;
+    c->budget = budget_bytes ? budget_bytes : kDefaultBudget;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return PFSM_E_CUDA;
+    }
+    c->nsm = prop.multiProcessorCount;
+    *out = c;
+    return PFSM_OK;
+}
+
+int pfsm_ctx_destroy(pfsm_ctx *ctx) {
+    if (!ctx) return PFSM_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->machines) release(ctx, kv.second);
+    for (auto &kv : ctx->slots) {
+        cudaFree(kv.second.status);
+        cudaFreeHost(kv.second.host_status);
+        for (int i = 0; i < 2 * kEventRing; ++i) cudaEventDestroy(kv.second.ev[i]);
+    }
+    batch_free(ctx);
+    delete ctx;
+    return PFSM_OK;
+}
+
+static int finish_load(pfsm_ctx *ctx, Machine &&m, pfsm_aut *out_id) {
+    m.sbits = ceil_log2(m.S);
+    fill_defaults(m, m.params);
+    m.k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
+    if (m.k * m.sbits > 16) m.k = 16 / m.sbits;
+    while (!build_memo(m)) {
+        if (--m.k <= 0) {
+            m.k = 0;
+            build_memo(m);
+            break;
+        }
+    }
+    m.params.prefix_k = m.k > 0 ? m.k : -1;
+    DeviceGuard g(ctx->device);
+    const int id = ctx->next_id++;
+    auto &slot = ctx->machines[id];
+    slot = std::move(m);
+    ctx->n_loads++;
+    int st = make_resident(ctx, id, slot);
+    if (st) {
+        ctx->machines.erase(id);
+        return st;
+    }
+    *out_id = id;
+    return PFSM_OK;
+}
+
+int pfsm_load_dfa(pfsm_ctx *ctx, const int16_t *delta, int32_t Q, int32_t S, int32_t q0,
+                  int32_t dead, const uint8_t *is_final, pfsm_aut *out_id) {
+    if (!ctx || !delta || !is_final || !out_id) return PFSM_E_INVAL;
+    if (Q < 1 || Q > 32767 || S < 1 || S > 256) return PFSM_E_INVAL;
+    if (q0 < 0 || q0 >= Q || dead < -1 || dead >= Q) return PFSM_E_INVAL;
+    if (dead == q0) return PFSM_E_INVAL;
+    for (size_t i = 0; i < (size_t)Q * S; ++i)
+        if (delta[i] < 0 || delta[i] >= Q) return PFSM_E_INVAL;
+    if (dead >= 0) {
+        if (is_final[dead]) return PFSM_E_INVAL;
+        for (int a = 0; a < S; ++a)
+            if (delta[(size_t)dead * S + a] != dead) return PFSM_E_INVAL;
+    }
+    Machine m;
+    m.kind = 0;
+    m.Q = Q;
+    m.S = S;
+    m.q0 = q0;
+    m.dead = dead;
+    m.fin.assign(is_final, is_final + Q);
+    m.dtab.resize((size_t)Q * S + ((size_t)Q * S & 1));
+    for (size_t i = 0; i < (size_t)Q * S; ++i) {
+        const int t = delta[i];
+        m.dtab[i] = t == dead ? DEAD16
+                              : static_cast<uint16_t>(t | (is_final[t] ? FINAL_BIT : 0));
+    }
+    return finish_load(ctx, std::move(m), out_id);
+}
+
+int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t S, int32_t q0,
+                  const uint8_t *is_final, pfsm_aut *out_id) {
+    if (!ctx || !delta_bits || !is_final || !out_id) return PFSM_E_INVAL;
+    if (Q < 1 || Q > 32767 || S < 1 || S > 256) return PFSM_E_INVAL;
+    if (q0 < 0 || q0 >= Q) return PFSM_E_INVAL;
+    const int W = (Q + 31) / 32;
+    const uint32_t lastmask = (Q % 32) ? ((1u << (Q % 32)) - 1) : 0xFFFFFFFFu;
+    Machine m;
+    m.kind = 1;
+    m.Q = Q;
+    m.S = S;
+    m.q0 = q0;
+    m.fin.assign(is_final, is_final + Q);
+    m.off.resize((size_t)Q * S + 1);
+    uint64_t e = 0;
+    for (size_t r = 0; r < (size_t)Q * S; ++r) {
+        m.off[r] = static_cast<uint32_t>(e);
+        const uint32_t *row = delta_bits + r * W;
+        if (row[W - 1] & ~lastmask) return PFSM_E_INVAL;   // a target >= Q
+        for (int w = 0; w < W; ++w) {
+            uint32_t x = row[w];
+            while (x) {
+                const int b = __builtin_ctz(x);
+                x &= x - 1;
+                const int t = w * 32 + b;
+                m.tgt.push_back(static_cast<uint16_t>(t | (is_final[t] ? FINAL_BIT : 0)));
+                ++e;
+            }
+        }
+        if (e > 0xFFFFFFFFull) return PFSM_E_INVAL;
+    }
+    m.off[(size_t)Q * S] = static_cast<uint32_t>(e);
+    if (m.tgt.empty()) m.tgt.push_back(0);
+    return finish_load(ctx, std::move(m), out_id);
+}
+
+int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut) {
+    if (!ctx) return PFSM_E_INVAL;
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    DeviceGuard g(ctx->device);
+    if (it->second.dev) {
+        release(ctx, it->second);
+        ctx->n_evict++;
+    }
+    return PFSM_OK;
+}
+
+int pfsm_unload(pfsm_ctx *ctx, pfsm_aut aut) {
+    if (!ctx) return PFSM_E_INVAL;
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    DeviceGuard g(ctx->device);
+    release(ctx, it->second);
+    ctx->machines.erase(it);
+    return PFSM_OK;
+}
+
+int pfsm_set_params(pfsm_ctx *ctx, pfsm_aut aut, const pfsm_params *p) {
+    if (!ctx) return PFSM_E_INVAL;
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    Machine &m = it->second;
+    pfsm_params np{};
+    if (p) np = *p;
+    fill_defaults(m, np);
+    int st = validate_params(m, np);
+    if (st) return st;
+    DeviceGuard g(ctx->device);
+    m.params = np;
+    st = apply_k(ctx, m);
+    if (st) {
+        m.params.prefix_k = m.k > 0 ? m.k : -1;
+        return st;
+    }
+    return PFSM_OK;
+}
+
+int pfsm_get_params(pfsm_ctx *ctx, pfsm_aut aut, pfsm_params *out) {
+    if (!ctx || !out) return PFSM_E_INVAL;
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    *out = it->second.params;
+    return PFSM_OK;
+}
+
+int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
+                    pfsm_match *out_dev, uint64_t cap, uint64_t *status_dev, void *stream) {
+    if (!ctx || !status_dev) return PFSM_E_INVAL;
+    if (n >= (1ull << 32)) return PFSM_E_INVAL;
+    if ((n > 0 && !text_dev) || (cap > 0 && !out_dev)) return PFSM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot *slot = get_slot(ctx, s);
+    if (!slot) return PFSM_E_NOMEM;
+    return scan_enqueue(ctx, aut, text_dev, n, reinterpret_cast<uint32_t *>(out_dev), cap,
+                        reinterpret_cast<unsigned long long *>(status_dev), slot, s);
+}
+
+int pfsm_scan(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
+              pfsm_match *out_dev, uint64_t cap, uint64_t *n_matches, void *stream) {
+    if (!ctx || !n_matches) return PFSM_E_INVAL;
+    if (n >= (1ull << 32)) return PFSM_E_INVAL;
+    if ((n > 0 && !text_dev) || (cap > 0 && !out_dev)) return PFSM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Slot *slot = get_slot(ctx, s);
+    if (!slot) return PFSM_E_NOMEM;
+    int st = scan_enqueue(ctx, aut, text_dev, n, reinterpret_cast<uint32_t *>(out_dev), cap,
+                          slot->status, slot, s);
+    if (st) return st;
+    if (cudaMemcpyAsync(slot->host_status, slot->status, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PFSM_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PFSM_E_CUDA;
+    return finish_status(slot->host_status, cap, n_matches);
+}
+
+int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out) {
+    if (!ctx || !out) return PFSM_E_INVAL;
+    out->resident_bytes = ctx->resident_bytes;
+    out->budget_bytes = ctx->budget;
+    out->loads = ctx->n_loads;
+    out->evictions = ctx->n_evict;
+    out->reloads = ctx->n_reload;
+    int r = 0;
+    for (auto &kv : ctx->machines) r += kv.second.dev != nullptr;
+    out->resident = r;
+    out->loaded = static_cast<int32_t>(ctx->machines.size());
+    return PFSM_OK;
+}
+
+int pfsm_set_timing(pfsm_ctx *ctx, int enable) {
+    if (!ctx) return PFSM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    for (auto &kv : ctx->slots) kv.second.ev_pending = 0;
+    ctx->timing = enable != 0;
+    ctx->time_ms = 0.0;
+    ctx->time_launches = 0;
+    return PFSM_OK;
+}
+
+int pfsm_kernel_time(pfsm_ctx *ctx, double *ms, uint64_t *launches) {
+    if (!ctx) return PFSM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    for (auto &kv : ctx->slots) collect_timing(ctx, &kv.second, 0);
+    if (ms) *ms = ctx->time_ms;
+    if (launches) *launches = ctx->time_launches;
+    return PFSM_OK;
+}
+
+const char *pfsm_strerror(int status) {
+    switch (status) {
+        case PFSM_OK: return "ok";
+        case PFSM_E_INVAL: return "invalid argument, table or text symbol";
+        case PFSM_E_NOMEM: return "out of device memory or residency budget";
+        case PFSM_E_OVERFLOW: return "more matches than the output capacity";
+        case PFSM_E_NOENT: return "unknown automaton id";
+        case PFSM_E_TIMEOUT: return "a bounded device wait expired";
+        case PFSM_E_CUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Match sets are compared as sorted (start, end, state) arrays, element by
+element (bit-exact: the scan is integer work). Sizes span several tiles and
+a ragged tail; full-size workloads are compared on sampled start windows
+(lazy data partitioning makes "matches starting in [a, b)" a well-defined
+slice the oracle computes on its own) plus properties over every match.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from conftest import read_golden
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1110_1716_gb300 as P  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = P.Pfsm(0)
+    yield p
+    p.close()
+
+
+def gpu_matches(pf, aut_id, text, cap=None):
+    return oracle.sort_matches(pf.scan_numpy(aut_id, text, cap))
+
+
+def in_window(m, lo, hi):
+    sel = (m[:, 0] >= lo) & (m[:, 0] < hi)
+    return m[sel]
+
+
+# ---------------------------------------------------------------- worked examples
+@pytest.mark.parametrize("fixture", ["fig2_aacacab.txt", "fig3_ac.txt"])
+def test_paper_examples_on_gpu(pf, fixture):
+    text, want = read_golden(fixture)
+    m = W.eps_free(W.fig1_union())
+    a = pf.load(m)
+    got = gpu_matches(pf, a, W.encode(text, W.FIG1_ALPHABET))
+    assert oracle.labelled(got, m.labels) == want
+
+
+# ---------------------------------------------------------------- small machines, ragged sizes
+SIZES = [0, 1, 2, 7, 15, 16, 17, 100, 4095, 4096, 4097, 16383, 16384, 16385, 70001]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_dfa_sizes(pf, seed):
+    d = W.dfa_random(300 + seed, Q=12, S=4, p_dead=0.25)
+    a = pf.load(d)
+    for n in SIZES:
+        t = W.text_uniform(n, 4, 1000 * seed + n)
+        assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t)), n
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_nfa_sizes(pf, seed):
+    rng = np.random.default_rng(40 + seed)
+    Q, S = 14, 4
+    edges = [(q, x, t) for q in range(Q) for x in range(S) for t in range(Q) if rng.random() < 0.12]
+    fins = [q for q in range(1, Q) if rng.random() < 0.3] or [Q - 1]
+    m = W.nfa_from_edges(Q, S, 0, edges, fins)
+    a = pf.load(m)
+    for n in SIZES:
+        t = W.text_uniform(n, 4, 77 * seed + n)
+        assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), n
+
+
+def test_byte_alphabet_and_odd_alphabets(pf):
+    for S in (2, 3, 5, 17, 200, 256):
+        d = W.dfa_random(S, Q=20, S=S, p_dead=0.2)
+        a = pf.load(d)
+        t = W.text_uniform(30011, S, S + 1)
+        assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t)), S
+
+
+# ---------------------------------------------------------------- launch parameters
+PARAMS = [
+    {"prefix_k": -1},
+    {"prefix_k": 1},
+    {"prefix_k": 3, "tile": 4096, "halo": 16},
+    {"threads": 128, "tile": 8192},
+    {"threads": 256, "table_smem": 0},
+    {"threads": 512, "tile": 32768, "halo": 4096, "ctas_per_sm": 1},
+]
+
+
+@pytest.mark.parametrize("params", PARAMS, ids=lambda p: ",".join("%s=%s" % kv for kv in p.items()))
+def test_params_do_not_change_dfa_result(pf, params):
+    d, t = W.workload_dna_dfa(1, n=300_000)
+    a = pf.load(d)
+    P.pfsm_set_params(pf.ctx, a, params)
+    assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t))
+
+
+@pytest.mark.parametrize("params", PARAMS[:4], ids=lambda p: ",".join("%s=%s" % kv for kv in p.items()))
+def test_params_do_not_change_nfa_result(pf, params):
+    nfa, t, _, _ = W.workload_motif_nfa(5, n=150_000, n_motifs=64, every=1500)
+    a = pf.load(nfa)
+    P.pfsm_set_params(pf.ctx, a, params)
+    assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(nfa, t))
+
+
+def test_nfa_warp_sets(pf):
+    """Without the prefix table the first step from q0 reaches ~85 states, more
+    than a lane holds: every instance runs on the warp-cooperative bitset path."""
+    nfa, t, _, _ = W.workload_motif_nfa(6, n=40_000, n_motifs=256, every=1000)
+    a = pf.load(nfa)
+    P.pfsm_set_params(pf.ctx, a, {"prefix_k": -1})
+    assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(nfa, t))
+
+
+# ---------------------------------------------------------------- full-size workloads
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_dna_dfa_1mib(pf, seed):
+    d, t = W.workload_dna_dfa(seed)
+    got = gpu_matches(pf, pf.load(d), t)
+    want = oracle.scan(d, t)
+    assert np.array_equal(got, want)
+
+
+def test_motif_nfa_4mib_full(pf):
+    nfa, t, _, plants = W.workload_motif_nfa(0, n=4 << 20)
+    got = gpu_matches(pf, pf.load(nfa), t)
+    assert np.array_equal(got, oracle.scan(nfa, t))
+    assert len(got) >= len(plants)
+
+
+@pytest.mark.slow
+def test_motif_nfa_64mib_sampled(pf):
+    nfa, t, motifs, plants = W.workload_motif_nfa(0)
+    got = gpu_matches(pf, pf.load(nfa), t)
+    n = len(t)
+    rng = np.random.default_rng(9)
+    wins = [0, n - (256 << 10)] + [int(x) for x in rng.integers(0, n - (256 << 10), size=6)]
+    for lo in wins:
+        hi = lo + (256 << 10)
+        assert np.array_equal(in_window(got, lo, hi), oracle.scan(nfa, t, lo, hi)), lo
+    # every match ends in a final state, inside the text, after its start
+    assert nfa.final[got[:, 2]].all()
+    assert (got[:, 0] <= got[:, 1]).all() and (got[:, 1] < n).all()
+    assert len(got) >= len(plants)
+
+
+def test_byte_trie_16mib_full(pf):
+    d, t, sigs, final_of, plants = W.workload_byte_trie(0, n=16 << 20)
+    got = gpu_matches(pf, pf.load(d), t)
+    assert np.array_equal(got, oracle.scan(d, t))
+
+
+@pytest.mark.slow
+def test_byte_trie_1gib_sampled(pf):
+    d, t, sigs, final_of, plants = W.workload_byte_trie(0)
+    got = gpu_matches(pf, pf.load(d), t)
+    n = len(t)
+    rng = np.random.default_rng(10)
+    for lo in [0, n - (4 << 20)] + [int(x) for x in rng.integers(0, n - (4 << 20), size=6)]:
+        hi = lo + (4 << 20)
+        assert np.array_equal(in_window(got, lo, hi), oracle.scan(d, t, lo, hi)), lo
+    # each reported match spells a signature ending in that final state
+    sig_of = {f: s for s, f in final_of.items()}
+    tb = memoryview(t)
+    for i, j, f in got:
+        assert bytes(tb[i:j + 1]) == sig_of[int(f)]
+    # each intact planted occurrence is reported
+    have = set(map(tuple, got.tolist()))
+    for pos, i in plants:
+        s = sigs[i]
+        if bytes(tb[pos:pos + len(s)]) == s:
+            assert (pos, pos + len(s) - 1, final_of[s]) in have
+
+
+# ---------------------------------------------------------------- protocol and errors
+def test_overflow_reports_required_count(pf):
+    d, t = W.workload_dna_dfa(1, n=100_000)
+    a = pf.load(d)
+    want = oracle.scan(d, t)
+    tt = pf.to_device(t)
+    out = torch.empty((10, 3), dtype=torch.int32, device="cuda")
+    st, cnt = P.pfsm_scan(pf.ctx, a, tt, None, out)
+    assert st == P.PFSM_E_OVERFLOW and cnt == len(want)
+    out = torch.empty((cnt, 3), dtype=torch.int32, device="cuda")
+    st, cnt2 = P.pfsm_scan(pf.ctx, a, tt, None, out)
+    assert st == P.PFSM_OK and cnt2 == cnt
+    got = oracle.sort_matches(out.cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, want)
+
+
+def test_zero_capacity_counts(pf):
+    d, t = W.workload_dna_dfa(2, n=50_000)
+    a = pf.load(d)
+    st, cnt = P.pfsm_scan(pf.ctx, a, pf.to_device(t), None, None, 0)
+    assert cnt == len(oracle.scan(d, t))
+    assert st == (P.PFSM_OK if cnt == 0 else P.PFSM_E_OVERFLOW)
+
+
+def test_bad_symbol_is_rejected(pf):
+    d = W.dfa_random(3, Q=10, S=4)
+    a = pf.load(d)
+    t = W.text_uniform(50_000, 4, 1)
+    t[33_333] = 4
+    out = torch.empty((100_000, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(P.PfsmError) as e:
+        P.pfsm_scan(pf.ctx, a, pf.to_device(t), None, out)
+    assert e.value.status == P.PFSM_E_INVAL
+
+
+def test_unknown_automaton_and_bad_tables(pf):
+    out = torch.empty((4, 3), dtype=torch.int32, device="cuda")
+    t = pf.to_device(np.zeros(8, dtype=np.uint8))
+    with pytest.raises(P.PfsmError) as e:
+        P.pfsm_scan(pf.ctx, 987654, t, None, out)
+    assert e.value.status == P.PFSM_E_NOENT
+    d = W.dfa_random(1, Q=8, S=4)
+    bad = d.delta.copy()
+    bad[2, 1] = 8
+    with pytest.raises(P.PfsmError):
+        P.pfsm_load_dfa(pf.ctx, bad, 0, d.dead, d.final)
+    nonabs = d.delta.copy()
+    nonabs[d.dead, 0] = 1
+    with pytest.raises(P.PfsmError):
+        P.pfsm_load_dfa(pf.ctx, nonabs, 0, d.dead, d.final)
+    finaldead = d.final.copy()
+    finaldead[d.dead] = 1
+    with pytest.raises(P.PfsmError):
+        P.pfsm_load_dfa(pf.ctx, d.delta, 0, d.dead, finaldead)
+
+
+def test_unaligned_text_pointer(pf):
+    d, t = W.workload_dna_dfa(2, n=100_003)
+    a = pf.load(d)
+    big = pf.to_device(np.concatenate([np.zeros(3, np.uint8), t]))
+    view = big[3:]
+    assert view.data_ptr() % 16 != 0
+    out = torch.empty((400_000, 3), dtype=torch.int32, device="cuda")
+    st, cnt = P.pfsm_scan(pf.ctx, a, view, None, out)
+    assert st == P.PFSM_OK
+    got = oracle.sort_matches(out[:cnt].cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, oracle.scan(d, t))
+
+
+def test_instances_outliving_tiles_use_the_carry_queue(pf):
+    """No dead state: every instance lives to the end of the text, so most of
+    them leave their tile's staged bytes (chained partitioning)."""
+    d = W.dfa_random(8, Q=6, S=4, dead=-1, finals=[1], p_dead=0.0)
+    a = pf.load(d)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "prefix_k": 2})
+    t = W.text_uniform(9000, 4, 3)
+    want = oracle.scan(d, t)
+    assert len(want) > 1_000_000
+    assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
+
+
+def test_eviction_and_reload(pf):
+    small = P.Pfsm(0, budget_bytes=200_000)
+    try:
+        autos = [W.dfa_random(50 + i, Q=64, S=4) for i in range(3)]
+        autos.append(W.workload_motif_nfa(3, n=10, n_motifs=40)[0])
+        ids = [small.load(x) for x in autos]
+        t = W.text_uniform(60_000, 4, 5)
+        for rnd in range(2):
+            for x, i in zip(autos, ids):
+                assert np.array_equal(gpu_matches(small, i, t), oracle.scan(x, t))
+        st = P.pfsm_get_stats(small.ctx)
+        assert st["evictions"] > 0 and st["reloads"] > 0
+        assert st["resident_bytes"] <= 200_000
+        P.pfsm_evict(small.ctx, ids[0])
+        assert np.array_equal(gpu_matches(small, ids[0], t), oracle.scan(autos[0], t))
+        P.pfsm_unload(small.ctx, ids[1])
+        with pytest.raises(P.PfsmError):
+            P.pfsm_scan(small.ctx, ids[1], small.to_device(t), None, None, 0)
+    finally:
+        small.close()
+
+
+def test_async_status_and_stream(pf):
+    d, t = W.workload_dna_dfa(2, n=200_000)
+    a = pf.load(d)
+    want = oracle.scan(d, t)
+    s = torch.cuda.Stream()
+    tt = pf.to_device(t)
+    out = torch.empty((len(want) + 5, 3), dtype=torch.int32, device="cuda")
+    status = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        P.pfsm_scan_async(pf.ctx, a, tt, None, out, status, stream=s)
+    s.synchronize()
+    cnt, err = status.tolist()
+    assert err == 0 and cnt == len(want)
+    assert np.array_equal(oracle.sort_matches(out[:cnt].cpu().numpy().view(np.uint32)), want)
