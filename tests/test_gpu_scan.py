@@ -60,25 +60,49 @@ def test_random_dfa_sizes(pf, seed):
         assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t)), n
 
 
+def forward_nfa(seed, Q=14, S=4, p=0.25):
+    """Random NFA whose edges only go to higher states (q0 excepted), so every
+    instance dies within Q steps."""
+    rng = np.random.default_rng(seed)
+    edges = [(q, x, t) for q in range(Q) for x in range(S) for t in range(Q)
+             if (t > q or q == 0) and rng.random() < p]
+    fins = [q for q in range(1, Q) if rng.random() < 0.3] or [Q - 1]
+    return W.nfa_from_edges(Q, S, 0, edges, fins)
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_random_nfa_sizes(pf, seed):
-    rng = np.random.default_rng(40 + seed)
-    Q, S = 14, 4
-    edges = [(q, x, t) for q in range(Q) for x in range(S) for t in range(Q) if rng.random() < 0.12]
-    fins = [q for q in range(1, Q) if rng.random() < 0.3] or [Q - 1]
-    m = W.nfa_from_edges(Q, S, 0, edges, fins)
+    m = forward_nfa(40 + seed)
     a = pf.load(m)
     for n in SIZES:
         t = W.text_uniform(n, 4, 77 * seed + n)
         assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), n
 
 
+def test_cyclic_nfa_long_lived_sets(pf):
+    """Cycles everywhere: state sets live to the end of the text, past every
+    tile's staged bytes (lazy partitioning reads the global text)."""
+    rng = np.random.default_rng(41)
+    Q, S = 14, 4
+    edges = [(q, x, t) for q in range(Q) for x in range(S) for t in range(Q) if rng.random() < 0.12]
+    m = W.nfa_from_edges(Q, S, 0, edges, [3, 7, 11])
+    a = pf.load(m)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16})
+    t = W.text_uniform(700, 4, 2)
+    want = oracle.scan(m, t)
+    assert len(want) > 100_000
+    assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 8), want)
+
+
 def test_byte_alphabet_and_odd_alphabets(pf):
-    for S in (2, 3, 5, 17, 200, 256):
-        d = W.dfa_random(S, Q=20, S=S, p_dead=0.2)
+    for S, seed, pdead in ((2, 22, 0.35), (3, 31, 0.3), (5, 5, 0.3), (17, 17, 0.2),
+                           (200, 200, 0.2), (256, 256, 0.2)):
+        d = W.dfa_random(seed, Q=20, S=S, p_dead=pdead)
         a = pf.load(d)
         t = W.text_uniform(30011, S, S + 1)
-        assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t)), S
+        want = oracle.scan(d, t)
+        assert len(want) > 0, S
+        assert np.array_equal(gpu_matches(pf, a, t), want), S
 
 
 # ---------------------------------------------------------------- launch parameters
