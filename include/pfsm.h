@@ -77,8 +77,8 @@ typedef struct {
                            -1 = off (every instance steps from q0) */
     int32_t tile;       /* starts owned by one CTA tile (multiple of 4096) */
     int32_t halo;       /* text staged past the tile end (multiple of 16) */
-    int32_t threads;    /* threads per CTA: 128, 256, 512 or 1024 */
-    int32_t spt;        /* starts per thread per filter round: 4, 8 or 16 */
+    int32_t threads;    /* threads per CTA: 128, 256 or 512 */
+    int32_t spt;        /* starts per thread per filter round: 8 */
     int32_t table_smem; /* delta table in shared memory: 1 yes, 0 no, -1 auto */
     int32_t ctas_per_sm;/* persistent CTAs per SM (0 = occupancy maximum) */
     int32_t reserved;
@@ -176,6 +176,14 @@ int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64
  * Blocks until done. Errors: as pfsm_scan, per job. */
 int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
                     uint64_t cap, uint64_t *counts, uint64_t *total, void *stream);
+
+/* Asynchronous form of pfsm_scan_batch: enqueues the batch on `stream` and
+ * returns. status_dev (device, k + 2 uint64) receives, when the stream
+ * reaches it: [0] total matches, [1] error bits (as pfsm_scan_async),
+ * [2 + i] matches of job i. The job array may be reused once the call
+ * returns. Errors detected on the host are returned directly. */
+int pfsm_scan_batch_async(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
+                          uint64_t cap, uint64_t *status_dev, void *stream);
 
 /* ------------------------------------------------------------------ misc */
 int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);

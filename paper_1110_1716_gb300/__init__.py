@@ -31,7 +31,7 @@ PFSM_E_CUDA = 6
 
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
-           "pfsm_scan_async", "pfsm_scan_batch", "pfsm_get_stats", "pfsm_set_timing",
+           "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_get_stats", "pfsm_set_timing",
            "pfsm_kernel_time", "pfsm_strerror")
 
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_scan": [P, I32, P, U64, P, U64, ctypes.POINTER(U64), P],
         "pfsm_scan_async": [P, I32, P, U64, P, U64, P, P],
         "pfsm_scan_batch": [P, P, I32, P, U64, P, ctypes.POINTER(U64), P],
+        "pfsm_scan_batch_async": [P, P, I32, P, U64, P, P],
         "pfsm_get_stats": [P, ctypes.POINTER(pfsm_stats)],
         "pfsm_set_timing": [P, ctypes.c_int],
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
@@ -210,16 +211,23 @@ def pfsm_scan_async(ctx: int, aut: int, text, n: Optional[int], out, status,
            "pfsm_scan_async")
 
 
-def pfsm_scan_batch(ctx: int, jobs: Sequence, out, cap: Optional[int] = None, stream=None):
-    """`jobs` = [(aut, text_tensor, n), ...]; `out` CUDA int32 [cap, 4].
-    Returns (status, counts as a numpy uint64 array, total)."""
+def _job_array(jobs: Sequence):
     k = len(jobs)
     arr = (pfsm_job * max(1, k))()
     for i, (aut, text, n) in enumerate(jobs):
         arr[i].aut = aut
         arr[i].reserved = 0
-        arr[i].text = _dev_ptr(text) if not isinstance(text, int) else text
+        arr[i].text = text if isinstance(text, int) else _dev_ptr(text)
         arr[i].n = text.numel() if n is None else n
+    return arr
+
+
+def pfsm_scan_batch(ctx: int, jobs: Sequence, out, cap: Optional[int] = None, stream=None):
+    """`jobs` = [(aut, text, n), ...] with `text` a CUDA uint8 tensor (or a
+    device address and n given); `out` CUDA int32 [cap, 4] of (text, start,
+    end, state) rows. Returns (status, per-job counts as uint64, total)."""
+    k = len(jobs)
+    arr = _job_array(jobs)
     cap = (out.shape[0] if out is not None else 0) if cap is None else cap
     counts = np.zeros(max(1, k), dtype=np.uint64)
     total = ctypes.c_uint64()
@@ -228,6 +236,17 @@ def pfsm_scan_batch(ctx: int, jobs: Sequence, out, cap: Optional[int] = None, st
     if st not in (PFSM_OK, PFSM_E_OVERFLOW):
         _check(st, "pfsm_scan_batch")
     return st, counts[:k], total.value
+
+
+def pfsm_scan_batch_async(ctx: int, jobs: Sequence, out, status, cap: Optional[int] = None,
+                          stream=None) -> None:
+    """Enqueue a batch; `status` is a CUDA int64 tensor of len(jobs) + 2
+    entries: (total, error bits, count of job 0, ...)."""
+    arr = _job_array(jobs)
+    cap = (out.shape[0] if out is not None else 0) if cap is None else cap
+    _check(load_library().pfsm_scan_batch_async(ctx, arr, len(jobs), _dev_ptr(out), cap,
+                                                _dev_ptr(status), _stream_ptr(stream)),
+           "pfsm_scan_batch_async")
 
 
 def pfsm_get_stats(ctx: int) -> dict:
@@ -308,6 +327,25 @@ class Pfsm:
             if st == PFSM_OK:
                 return out[:cnt]
             cap = int(cnt)
+
+    def scan_batch(self, jobs, cap: Optional[int] = None, stream=None):
+        """jobs = [(aut, text), ...] (numpy or CUDA texts). Returns
+        (matches as an int32 CUDA tensor of (text, start, end, state) rows,
+        per-job counts)."""
+        torch = self.torch
+        dj = []
+        for aut, text in jobs:
+            if isinstance(text, np.ndarray):
+                text = self.to_device(text)
+            dj.append((aut, text, text.numel()))
+        total_n = sum(x[2] for x in dj)
+        cap = max(1024, total_n // 2) if cap is None else cap
+        while True:
+            out = torch.empty((cap, 4), dtype=torch.int32, device="cuda:%d" % self.device)
+            st, counts, total = pfsm_scan_batch(self.ctx, dj, out, cap, stream)
+            if st == PFSM_OK:
+                return out[:total], counts
+            cap = int(total)
 
     def scan_numpy(self, aut: int, text, cap: Optional[int] = None) -> np.ndarray:
         """Matches as an (m, 3) uint32 numpy array (unordered)."""

@@ -15,84 +15,11 @@
 #include <mutex>
 #include <vector>
 
-#include "pfsm_internal.h"
+#include "pfsm_host.h"
 
 using namespace pfsm;
 
-namespace {
-
-constexpr uint64_t kDefaultBudget = 8ull << 30;
-constexpr uint32_t kCarryCap = 1u << 20;     // carry entries per stream slot
-constexpr uint32_t kSmemMax = 232448;        // opt-in shared memory per CTA
-
-struct Machine {
-    int kind = 0;  // 0 DFA, 1 NFA
-    int Q = 0, S = 0, q0 = 0, dead = -1;
-    std::vector<uint8_t> fin;
-    // device encodings (host images)
-    std::vector<uint16_t> dtab;       // DFA [Q][S]
-    std::vector<uint32_t> off;        // NFA CSR [Q*S+1]
-    std::vector<uint16_t> tgt;        // NFA targets
-    // start-prefix table
-    int k = 0, sbits = 1;
-    std::vector<uint16_t> memo;
-    std::vector<uint32_t> rec_off, pool;
-    pfsm_params params{};
-    // residency
-    void *dev = nullptr;
-    size_t dev_bytes = 0;
-    DevMachine dm{};
-    uint64_t last_use = 0;
-    bool was_resident = false;
-};
-
-constexpr int kEventRing = 256;   // timed launches kept in flight per stream
-
-struct Slot {   // per-stream scratch
-    unsigned long long *status = nullptr;   // device [2]
-    uint32_t *carry_n = nullptr;
-    uint32_t *carry = nullptr;
-    unsigned long long *host_status = nullptr;   // pinned [2]
-    // ring of (start, end) events around timed tile-kernel launches
-    cudaEvent_t ev[2 * kEventRing] = {};
-    int ev_head = 0, ev_pending = 0;
-};
-
-}  // namespace
-
-struct pfsm_ctx {
-    int device = 0;
-    int nsm = 0;
-    uint64_t budget = kDefaultBudget;
-    uint64_t resident_bytes = 0;
-    uint64_t clock = 0;
-    uint64_t n_loads = 0, n_evict = 0, n_reload = 0;
-    std::map<int, Machine> machines;
-    int next_id = 1;
-    std::map<cudaStream_t, Slot> slots;
-    std::mutex mu;
-    bool timing = false;
-    double time_ms = 0.0;
-    uint64_t time_launches = 0;
-    // batch state (batch.cu)
-    void *batch = nullptr;
-};
-
-namespace {
-
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int d) {
-        cudaGetDevice(&prev);
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
+namespace pfsm {
 
 int ceil_log2(int S) {
     int b = 0;
@@ -163,15 +90,14 @@ struct NfaMemoBuilder {
         for (uint16_t q : set) rec.push_back(q);
         auto it = recs.find(rec);
         if (it != recs.end()) return static_cast<uint16_t>(it->second);
-        const uint32_t id = static_cast<uint32_t>(m.rec_off.size());
-        if (id >= PT_WALK || matches.size() > 0xFFFF || set.size() > 0xFFFF) {
+        const uint32_t at = static_cast<uint32_t>(m.pool.size());
+        if (at >= PT_WALK || matches.size() > 0xFFFF || set.size() > 0xFFFF) {
             ok = false;
             return PT_SKIP;
         }
-        recs.emplace(rec, id);
-        m.rec_off.push_back(static_cast<uint32_t>(m.pool.size()));
+        recs.emplace(rec, at);
         m.pool.insert(m.pool.end(), rec.begin(), rec.end());
-        return static_cast<uint16_t>(id);
+        return static_cast<uint16_t>(at);
     }
 
     // depth symbols consumed (index bits below depth*sbits fixed to prefix)
@@ -215,7 +141,6 @@ struct NfaMemoBuilder {
 };
 
 bool build_memo_nfa(Machine &m) {
-    m.rec_off.clear();
     m.pool.clear();
     if (m.k <= 0) {
         m.memo.clear();
@@ -227,7 +152,6 @@ bool build_memo_nfa(Machine &m) {
     b.dfs(0, 0, {static_cast<uint16_t>(m.q0)}, {});
     if (!b.ok) return false;
     if (m.pool.empty()) m.pool.push_back(0);
-    if (m.rec_off.empty()) m.rec_off.push_back(0);
     return true;
 }
 
@@ -248,7 +172,7 @@ size_t device_bytes(const Machine &m) {
         b += align256(m.dtab.size() * 2 + 4);
     } else {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
-             align256(m.rec_off.size() * 4) + align256(m.pool.size() * 4);
+             align256(m.pool.size() * 4) + align256(m.band.size() * 8);
     }
     return b;
 }
@@ -267,6 +191,7 @@ int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id) {
         Machine *victim = nullptr;
         for (auto &kv : ctx->machines) {
             if (kv.first == keep_id || !kv.second.dev) continue;
+            if (kv.second.pin && kv.second.pin == ctx->epoch) continue;
             if (!victim || kv.second.last_use < victim->last_use) victim = &kv.second;
         }
         if (!victim) return PFSM_E_NOMEM;
@@ -316,16 +241,18 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
         memcpy(img.data() + o, m.off.data(), m.off.size() * 4);
         o += align256(m.off.size() * 4);
         const size_t o_tgt = put(m.tgt.data(), m.tgt.size() * 2);
-        const size_t o_ro = o;
-        memcpy(img.data() + o, m.rec_off.data(), m.rec_off.size() * 4);
-        o += align256(m.rec_off.size() * 4);
         const size_t o_pool = o;
         memcpy(img.data() + o, m.pool.data(), m.pool.size() * 4);
         o += align256(m.pool.size() * 4);
+        const size_t o_band = o;
+        if (!m.band.empty()) memcpy(img.data() + o, m.band.data(), m.band.size() * 8);
+        o += align256(m.band.size() * 8);
         dm.off = reinterpret_cast<const uint32_t *>(base + o_off);
         dm.tgt = reinterpret_cast<const uint16_t *>(base + o_tgt);
-        dm.rec_off = reinterpret_cast<const uint32_t *>(base + o_ro);
         dm.pool = reinterpret_cast<const uint32_t *>(base + o_pool);
+        dm.pool_n = static_cast<uint32_t>(m.pool.size());
+        dm.band = m.band.empty() ? nullptr
+                                 : reinterpret_cast<const unsigned long long *>(base + o_band);
     }
     if (o > bytes) {   // layout and size disagree: a bug, fail loudly
         cudaFree(p);
@@ -350,7 +277,7 @@ Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s) {
     if (it != ctx->slots.end()) return &it->second;
     Slot sl;
     void *p = nullptr;
-    const size_t bytes = 64 + static_cast<size_t>(kCarryCap) * 12;
+    const size_t bytes = 64 + static_cast<size_t>(kCarryCap) * 16;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -428,8 +355,9 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.dtab = m.dm.dtab;
     a.off = m.dm.off;
     a.tgt = m.dm.tgt;
-    a.rec_off = m.dm.rec_off;
     a.pool = m.dm.pool;
+    a.pool_n = m.dm.pool_n;
+    a.band = m.dm.band;
     a.Wq = m.kind == 1 ? m.dm.Wq : 0;
     const uint32_t round = 8u * p.threads;
     uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
@@ -439,17 +367,29 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         if (p.table_smem == 1) a.tab_smem = 1;
         else if (p.table_smem == -1 && tab_bytes <= 48 * 1024) a.tab_smem = 1;
     }
-    a.qcap = 2 * round;
-    uint32_t smem = layout_smem(a, m.kind, p.threads, p.spt);
-    if (smem > kSmemMax) {
+    const int kmask = m.kind == 0 ? 1 : 2;
+    a.stage_n = m.kind == 0 ? STAGE : 32;
+    SmemNeed need{};
+    need.tab_bytes = a.tab_smem ? tab_bytes : 0;
+    need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 8) : 0;
+    need.pool_bytes = (m.kind == 1 && m.pool.size() * 4 <= 64 * 1024)
+                          ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
+    uint32_t smem = 0;
+    bool fit = false;
+    for (int attempt = 0; attempt < 6 && !fit; ++attempt) {
+        a.qcap = 2 * round;
+        smem = layout_smem(a, kmask, p.threads, need);
+        if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
         a.qcap = round;
-        smem = layout_smem(a, m.kind, p.threads, p.spt);
+        smem = layout_smem(a, kmask, p.threads, need);
+        if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
+        // give up shared-memory copies, largest first
+        if (need.pool_bytes) need.pool_bytes = 0;
+        else if (need.band_bytes) need.band_bytes = 0;
+        else if (need.tab_bytes && p.table_smem == -1) { need.tab_bytes = 0; a.tab_smem = 0; }
+        else break;
     }
-    if (smem > kSmemMax && a.tab_smem && p.table_smem == -1) {
-        a.tab_smem = 0;
-        smem = layout_smem(a, m.kind, p.threads, p.spt);
-    }
-    if (smem > kSmemMax) return PFSM_E_INVAL;
+    if (!fit) return PFSM_E_INVAL;
     int occ = max_ctas_per_sm(m.kind, m.sbits, p.threads, smem, a.tab_smem != 0);
     if (occ <= 0) return PFSM_E_INVAL;
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
@@ -502,7 +442,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
         ev = slot->ev_head;
         cudaEventRecord(slot->ev[2 * ev], s);
     }
-    cudaError_t e = launch_scan(pl.a, m.kind, pl.threads, pl.grid, s);
+    cudaError_t e = launch_scan(pl.a, m.kind, pl.threads, pl.grid, pl.smem, s);
     if (ev >= 0) {
         cudaEventRecord(slot->ev[2 * ev + 1], s);
         slot->ev_head = (slot->ev_head + 1) % kEventRing;
@@ -524,7 +464,7 @@ int finish_status(const unsigned long long *hs, uint64_t cap, uint64_t *n_matche
     return PFSM_OK;
 }
 
-}  // namespace
+}  // namespace pfsm
 
 // =========================================================================
 extern "C" {
@@ -655,6 +595,28 @@ int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t 
         if (e > 0xFFFFFFFFull) return PFSM_E_INVAL;
     }
     m.off[(size_t)Q * S] = static_cast<uint32_t>(e);
+    // band rows: delta(q, a) inside q+1..q+8 for every symbol (alphabets of
+    // at most 4 symbols), with the finality of each target beside it
+    if (S <= 4) {
+        m.band.assign(Q, 0ull);
+        for (int q = 0; q < Q; ++q) {
+            unsigned long long row = 0;
+            bool fits = true;
+            for (int a = 0; a < S && fits; ++a) {
+                for (uint32_t x = m.off[(size_t)q * S + a]; x < m.off[(size_t)q * S + a + 1]; ++x) {
+                    const int t = m.tgt[x] & 0x7FFF;
+                    const int d = t - q - 1;
+                    if (d < 0 || d > 7) {
+                        fits = false;
+                        break;
+                    }
+                    row |= 1ull << (8 * a + d);
+                    if (is_final[t]) row |= 1ull << (32 + 8 * a + d);
+                }
+            }
+            m.band[q] = (fits && row != BAND_CSR) ? row : BAND_CSR;
+        }
+    }
     if (m.tgt.empty()) m.tgt.push_back(0);
     return finish_load(ctx, std::move(m), out_id);
 }

@@ -1,0 +1,101 @@
+// Host-side state of libpfsm shared by the API translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "pfsm_internal.h"
+
+namespace pfsm {
+
+constexpr uint64_t kDefaultBudget = 8ull << 30;
+constexpr uint32_t kCarryCap = 1u << 20;     // carry entries per stream slot
+constexpr uint32_t kSmemMax = 232448;        // opt-in shared memory per CTA
+constexpr uint32_t kSmemStatic = 1024;       // room left for static shared memory
+constexpr int kEventRing = 256;              // timed launches kept in flight per stream
+
+struct Machine {
+    int kind = 0;  // 0 DFA, 1 NFA
+    int Q = 0, S = 0, q0 = 0, dead = -1;
+    std::vector<uint8_t> fin;
+    // device encodings (host images)
+    std::vector<uint16_t> dtab;       // DFA [Q][S]
+    std::vector<uint32_t> off;        // NFA CSR [Q*S+1]
+    std::vector<uint16_t> tgt;        // NFA targets
+    // start-prefix table
+    int k = 0, sbits = 1;
+    std::vector<uint16_t> memo;
+    std::vector<uint32_t> pool;
+    std::vector<unsigned long long> band;   // NFA band rows (S <= 4) or empty
+    pfsm_params params{};
+    // residency
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    DevMachine dm{};
+    uint64_t last_use = 0;
+    uint64_t pin = 0;        // batch epoch that needs it resident
+    bool was_resident = false;
+};
+
+struct Slot {   // per-stream scratch
+    unsigned long long *status = nullptr;   // device [2]
+    uint32_t *carry_n = nullptr;
+    uint32_t *carry = nullptr;              // kCarryCap entries of 4 words
+    unsigned long long *host_status = nullptr;   // pinned [2]
+    // ring of (start, end) events around timed tile-kernel launches
+    cudaEvent_t ev[2 * kEventRing] = {};
+    int ev_head = 0, ev_pending = 0;
+};
+
+struct BatchState;   // batch.cu
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace pfsm
+
+struct pfsm_ctx {
+    int device = 0;
+    int nsm = 0;
+    uint64_t budget = pfsm::kDefaultBudget;
+    uint64_t resident_bytes = 0;
+    uint64_t clock = 0;
+    uint64_t epoch = 0;
+    uint64_t n_loads = 0, n_evict = 0, n_reload = 0;
+    std::map<int, pfsm::Machine> machines;
+    int next_id = 1;
+    std::map<cudaStream_t, pfsm::Slot> slots;
+    std::mutex mu;
+    bool timing = false;
+    double time_ms = 0.0;
+    uint64_t time_launches = 0;
+    // batch executors, one per stream (batch.cu)
+    std::map<cudaStream_t, pfsm::BatchState *> batch;
+};
+
+namespace pfsm {
+
+int ceil_log2(int S);
+bool build_memo(Machine &m);
+size_t align256(size_t x);
+void release(pfsm_ctx *ctx, Machine &m);
+int make_resident(pfsm_ctx *ctx, int id, Machine &m);
+Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s);
+void collect_timing(pfsm_ctx *ctx, Slot *slot, int keep);
+int finish_status(const unsigned long long *hs, uint64_t cap, uint64_t *n_matches);
+void batch_free(pfsm_ctx *ctx);
+
+}  // namespace pfsm

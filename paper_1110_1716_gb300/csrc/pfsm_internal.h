@@ -22,14 +22,20 @@ constexpr uint16_t FINAL_BIT = 0x8000;
 //   PT_SKIP  no instance survives k steps and none matches within them
 //   PT_WALK  (DFA) a final state is met within k steps: step from q0
 //   other    DFA: the state after k steps (no match on the way);
-//            NFA: a record number (record = matches within the k steps and
-//            the state set after them, see pool layout below)
+//            NFA: the word offset o of a record in `pool` holding the
+//            matches within the k steps and the state set after them:
+//              pool[o] = n_match | n_surv << 16
+//              pool[o+1 .. o+n_match]       = step << 16 | final state
+//              pool[o+1+n_match .. +n_surv] = surviving states after k steps
 constexpr uint16_t PT_SKIP = 0xFFFF;
 constexpr uint16_t PT_WALK = 0xFFFE;
-// NFA record r at word rec_off[r] of pool:
-//   pool[o] = n_match | n_surv << 16
-//   pool[o+1 .. o+n_match]       = step << 16 | final state   (step in 0..k-1)
-//   pool[o+1+n_match .. +n_surv] = surviving states after k steps
+
+// NFA band rows (alphabets of at most 4 symbols): one uint64 per state q.
+// Byte a (a < 4) is the mask of delta(q, a) within q+1..q+8 (bit d set iff
+// q+1+d is a target); byte 4+a marks which of those targets are final.
+// BAND_CSR marks a state with a target outside that window: its rows are
+// read from the CSR arrays instead.
+constexpr unsigned long long BAND_CSR = ~0ull;
 
 // Work-queue entry of the filter phase (uint32): start offset inside the
 // tile in bits 0..15, info in bits 16..31 (a prefix-table entry, or PT_WALK
@@ -41,7 +47,9 @@ constexpr unsigned long long ERR_SYMBOL = 1ull;
 constexpr unsigned long long ERR_TIMEOUT = 2ull;
 
 constexpr int NFA_SLOT = 8;       // states one lane holds for a small NFA set
-constexpr int STAGE = 128;        // staged matches per warp before a flush
+constexpr int STAGE = 128;        // largest per-warp match staging (entries)
+constexpr int NFA_INLINE = 4;     // states a filtering thread advances in registers
+constexpr int INLINE_STEPS = 24;  // symbols it advances them before handing over
 
 struct ScanArgs {
     // text
@@ -59,8 +67,11 @@ struct ScanArgs {
     const uint16_t *dtab;   // DFA: [Q][S]
     const uint32_t *off;    // NFA: [Q*S + 1] CSR offsets
     const uint16_t *tgt;    // NFA: targets
-    const uint32_t *rec_off;// NFA: record offsets
-    const uint32_t *pool;   // NFA: record words
+    const uint32_t *pool;   // NFA: prefix records
+    const unsigned long long *band;   // NFA: band rows [Q] or null
+    uint32_t pool_n;        // NFA: words of pool
+    int32_t pool_smem;      // NFA: pool staged to smem
+    int32_t band_smem;      // NFA: band rows staged to smem
     int32_t Wq;             // NFA: 32-bit words of a state bitset
     int32_t tab_smem;       // DFA table staged to smem
     // output
@@ -73,19 +84,18 @@ struct ScanArgs {
     uint32_t carry_cap;
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
+    uint32_t sm_band, sm_pool;
     uint32_t qcap;
+    uint32_t stage_n;       // staged matches per warp before a flush
 };
 
-// Per-item description for the batch kernel.
-struct BatchItem {
-    uint32_t job;     // index into the job table
-    uint32_t tile;    // tile index inside the job's text
-};
-
+// One text of a batch in the device job table (sorted by machine).
 struct BatchJob {
     const uint8_t *text;
     uint32_t n;
-    uint32_t aut;     // index into the machine table
+    uint32_t mach;        // index into the batch's machine table
+    uint32_t orig;        // caller's job index, reported with each match
+    uint32_t tile_begin;  // first work item of this text
 };
 
 struct DevMachine {
@@ -93,27 +103,49 @@ struct DevMachine {
     int32_t Q, S, q0, k, sbits;
     uint32_t memo_n;
     int32_t Wq;
+    int32_t tab_smem; // batch: DFA table staged to shared memory
+    int32_t band_smem;// batch: NFA band rows staged to shared memory
+    int32_t pool_smem;// batch: NFA prefix records staged to shared memory
+    int32_t pad;
     const uint16_t *memo;
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;
-    const uint32_t *rec_off;
     const uint32_t *pool;
+    const unsigned long long *band;
+    uint32_t pool_n;
+    int32_t pad2;
+};
+static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
+
+// Arguments of the persistent batch kernel, read from device memory so that
+// one captured graph serves every batch of the same shape.
+struct BatchArgs {
+    ScanArgs sa;              // layout, output, status, carry (text/machine unused)
+    uint32_t nitems, njobs;
+    uint32_t *item_counter;
+    const BatchJob *jobs;
+    const DevMachine *machs;
+    unsigned long long *job_counts;
 };
 
 // ---- launch helpers (scan_kernels.cu) ------------------------------------
-struct LaunchCfg {
-    int threads;
-    int ctas_per_sm;
-    uint32_t smem_bytes;
-    int spt;
+// Fill the smem offsets of `a` (kind_mask: 1 = DFA present, 2 = NFA present)
+// for `threads` threads and the table copies in `need`; returns total bytes.
+struct SmemNeed {
+    uint32_t tab_bytes;    // DFA table copy (0 = read from global)
+    uint32_t band_bytes;   // NFA band rows copy (0 = read from global)
+    uint32_t pool_bytes;   // NFA prefix records copy (0 = read from global)
 };
-
-// Fill the smem offsets of `a` for `threads` threads; returns total bytes.
-uint32_t layout_smem(ScanArgs &a, int kind, int threads, int spt);
-cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, cudaStream_t s);
+uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &need);
+cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
+                        cudaStream_t s);
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs *dev_args, int threads, int grid, uint32_t smem,
+                         cudaStream_t s);
+cudaError_t launch_carry_batch(const BatchArgs *dev_args, int grid, cudaStream_t s);
 int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem);
+int max_batch_ctas_per_sm(int threads, uint32_t smem);
 
 // Release the batch executor state of a context (batch.cu).
 void batch_free(pfsm_ctx *ctx);

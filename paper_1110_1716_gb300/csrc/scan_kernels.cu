@@ -117,51 +117,6 @@ struct Misc {
     uint32_t pad;
 };
 
-// ------------------------------------------------------------ match output
-// Per-warp staging of (start, end, state) triples; `sn` is warp-uniform.
-__device__ __forceinline__ void stage_flush(uint32_t *buf, uint32_t &sn, const ScanArgs &a,
-                                            int lane) {
-    __syncwarp();
-    if (sn == 0) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&a.status[0], (unsigned long long)sn);
-    base = __shfl_sync(FULLMASK, base, 0);
-    const uint32_t words = 3 * sn;
-    for (uint32_t w = lane; w < words; w += 32) {
-        const unsigned long long idx = base + w / 3;
-        if (idx < a.cap) a.out[base * 3 + w] = buf[w];
-    }
-    __syncwarp();
-    sn = 0;
-}
-
-__device__ __forceinline__ void warp_emit(bool has, uint32_t s, uint32_t e, uint32_t st,
-                                          uint32_t *buf, uint32_t &sn, const ScanArgs &a,
-                                          int lane) {
-    const uint32_t m = __ballot_sync(FULLMASK, has);
-    if (m == 0) return;
-    const uint32_t c = __popc(m);
-    if (sn + c > STAGE) stage_flush(buf, sn, a, lane);
-    if (has) {
-        const uint32_t i = sn + __popc(m & lanemask_lt());
-        buf[3 * i] = s;
-        buf[3 * i + 1] = e;
-        buf[3 * i + 2] = st;
-    }
-    sn += c;
-}
-
-// Direct append for the rare warp-cooperative path (divergent callers).
-__device__ __forceinline__ void emit_direct(const ScanArgs &a, uint32_t s, uint32_t e,
-                                            uint32_t st) {
-    const unsigned long long idx = atomicAdd(&a.status[0], 1ull);
-    if (idx < a.cap) {
-        a.out[3 * idx] = s;
-        a.out[3 * idx + 1] = e;
-        a.out[3 * idx + 2] = st;
-    }
-}
-
 // ------------------------------------------------------------ symbol checks
 // Byte-wise "x >= S" over a 64-bit word, high bit of each byte set on hit.
 __device__ __forceinline__ uint64_t bytes_ge(uint64_t x, uint32_t S) {
@@ -202,27 +157,117 @@ __device__ __forceinline__ uint32_t memo_index(uint64_t lo, uint64_t hi, uint32_
     }
 }
 
-// ------------------------------------------------------------ text access
-struct TileView {
-    const uint8_t *sm;   // staged bytes of [b, b + len)
-    uint32_t b, len;
+// ------------------------------------------------------------ views
+// The machine one tile runs (registers).
+struct MView {
+    int32_t Q, S, q0, k, sbits, Wq;
+    const uint16_t *dtab;
+    const uint32_t *off;
+    const uint16_t *tgt;
 };
 
-__device__ __forceinline__ uint32_t text_at(const ScanArgs &a, const TileView &tv,
-                                            uint32_t pos) {
+// Where matches and carried instances go.
+struct OView {
+    uint32_t *out;
+    uint64_t cap;
+    unsigned long long *status;       // [0] match count, [1] error bits
+    unsigned long long *job_counts;   // per-text counts (batch) or null
+    uint32_t *carry;                  // {job, start, pos, state} entries
+    uint32_t *carry_n;
+    uint32_t carry_cap;
+    uint32_t stage_n;                 // per-warp staging capacity (entries)
+};
+
+// One staged tile: bytes [b, b + len) of a text are in shared memory.
+struct TileView {
+    const uint8_t *sm;
+    const uint8_t *text;
+    uint32_t b, len, n;
+    uint32_t job;    // index into the device job table (batch), 0 otherwise
+    uint32_t orig;   // caller's text index reported with the matches
+};
+
+// Shared-memory regions of one CTA.
+struct Smem {
+    Misc *misc;
+    const uint16_t *memo;
+    const uint16_t *tab;
+    const unsigned long long *band;   // NFA band rows (shared copy, global, or null)
+    const uint32_t *pool;             // NFA prefix records (shared copy or global)
+    uint32_t *queue;
+    uint32_t *stage;   // this warp's staging buffer
+    uint16_t *slots;   // this warp's NFA slots
+    uint32_t *coop;    // this warp's two bitsets of Wq words
+};
+
+__device__ __forceinline__ uint32_t text_at(const TileView &tv, uint32_t pos) {
     const uint32_t rel = pos - tv.b;
-    return rel < tv.len ? tv.sm[rel] : __ldg(a.text + pos);
+    return rel < tv.len ? tv.sm[rel] : __ldg(tv.text + pos);
+}
+
+// ------------------------------------------------------------ match output
+// Per-warp staging of matches (OUTW words each: [text,] start, end, state);
+// `sn` is warp-uniform. A flush reserves room with one global atomic.
+template <int OUTW>
+__device__ __forceinline__ void stage_flush(uint32_t *buf, uint32_t &sn, const OView &ov,
+                                            uint32_t orig, int lane) {
+    __syncwarp();
+    if (sn == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&ov.status[0], (unsigned long long)sn);
+        if (ov.job_counts) atomicAdd(&ov.job_counts[orig], (unsigned long long)sn);
+    }
+    base = __shfl_sync(FULLMASK, base, 0);
+    const uint32_t words = OUTW * sn;
+    for (uint32_t w = lane; w < words; w += 32) {
+        const unsigned long long idx = base + w / OUTW;
+        if (idx < ov.cap) ov.out[base * OUTW + w] = buf[w];
+    }
+    __syncwarp();
+    sn = 0;
+}
+
+template <int OUTW>
+__device__ __forceinline__ void warp_emit(bool has, uint32_t s, uint32_t e, uint32_t st,
+                                          uint32_t *buf, uint32_t &sn, const OView &ov,
+                                          const TileView &tv, int lane) {
+    const uint32_t m = __ballot_sync(FULLMASK, has);
+    if (m == 0) return;
+    const uint32_t c = __popc(m);
+    if (sn + c > ov.stage_n) stage_flush<OUTW>(buf, sn, ov, tv.orig, lane);
+    if (has) {
+        uint32_t *p = buf + OUTW * (sn + __popc(m & lanemask_lt()));
+        if (OUTW == 4) *p++ = tv.orig;
+        p[0] = s;
+        p[1] = e;
+        p[2] = st;
+    }
+    sn += c;
+}
+
+// Direct append for divergent callers (warp-cooperative sets, carried runs).
+template <int OUTW>
+__device__ __forceinline__ void emit_direct(const OView &ov, uint32_t orig, uint32_t s,
+                                            uint32_t e, uint32_t st) {
+    const unsigned long long idx = atomicAdd(&ov.status[0], 1ull);
+    if (ov.job_counts) atomicAdd(&ov.job_counts[orig], 1ull);
+    if (idx < ov.cap) {
+        uint32_t *p = ov.out + idx * OUTW;
+        if (OUTW == 4) *p++ = orig;
+        p[0] = s;
+        p[1] = e;
+        p[2] = st;
+    }
 }
 
 // ------------------------------------------------------------ continuation: DFA
-// Drains the work queue: lane-refill loop, one symbol per lane per iteration.
-template <bool TAB_SMEM>
-__device__ void drain_dfa(const ScanArgs &a, const TileView &tv, Misc *misc,
-                          const uint32_t *queue, const uint16_t *tab_sm, uint32_t *stage,
+// Drains the work queue with lane refill: one symbol per lane per iteration.
+template <bool TAB_SMEM, int OUTW>
+__device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
                           uint32_t &sn, int lane, uint64_t pol_keep) {
-    const uint32_t qn = misc->q_count;
-    const uint32_t S = a.S;
-    const uint32_t n = a.n;
+    const uint32_t qn = sm.misc->q_count;
+    const uint32_t S = mv.S, n = tv.n;
     const uint32_t tile_end = tv.b + tv.len;
     bool act = false;
     bool gmode = false;   // past the staged text and the carry queue is full
@@ -232,20 +277,20 @@ __device__ void drain_dfa(const ScanArgs &a, const TileView &tv, Misc *misc,
         const uint32_t m = __ballot_sync(FULLMASK, need);
         if (m) {
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&misc->q_head, __popc(m));
+            if (lane == 0) base = atomicAdd(&sm.misc->q_head, __popc(m));
             base = __shfl_sync(FULLMASK, base, 0);
             if (need) {
                 const uint32_t qi = base + __popc(m & lanemask_lt());
                 if (qi < qn) {
-                    const uint32_t e = queue[qi];
+                    const uint32_t e = sm.queue[qi];
                     start = tv.b + (e & 0xFFFFu);
                     const uint32_t info = e >> 16;
                     if (info == PT_WALK) {
-                        s = a.q0;
+                        s = mv.q0;
                         pos = start;
                     } else {
                         s = info;
-                        pos = start + a.k;
+                        pos = start + mv.k;
                     }
                     act = true;
                     gmode = false;
@@ -259,22 +304,24 @@ __device__ void drain_dfa(const ScanArgs &a, const TileView &tv, Misc *misc,
             if (pos >= n) {
                 act = false;
             } else if (pos >= tile_end && !gmode) {
-                const uint32_t ci = atomicAdd(a.carry_n, 1u);
-                if (ci < a.carry_cap) {
-                    a.carry[3 * ci] = start;
-                    a.carry[3 * ci + 1] = pos;
-                    a.carry[3 * ci + 2] = s;
+                const uint32_t ci = atomicAdd(ov.carry_n, 1u);
+                if (ci < ov.carry_cap) {
+                    uint32_t *c = ov.carry + 4 * ci;
+                    c[0] = tv.job;
+                    c[1] = start;
+                    c[2] = pos;
+                    c[3] = s;
                     act = false;
                 } else {
                     gmode = true;
                 }
             }
             if (act) {
-                const uint32_t c = text_at(a, tv, pos);
+                const uint32_t c = text_at(tv, pos);
                 uint16_t e = DEAD16;
                 if (c < S) {
                     const uint32_t ix = s * S + c;
-                    e = TAB_SMEM ? tab_sm[ix] : ldg_u16_keep(a.dtab + ix, pol_keep);
+                    e = TAB_SMEM ? sm.tab[ix] : ldg_u16_keep(mv.dtab + ix, pol_keep);
                 }
                 if (e == DEAD16) {
                     act = false;
@@ -286,36 +333,114 @@ __device__ void drain_dfa(const ScanArgs &a, const TileView &tv, Misc *misc,
                 }
             }
         }
-        warp_emit(hit, start, hend, s, stage, sn, a, lane);
+        warp_emit<OUTW>(hit, start, hend, s, sm.stage, sn, ov, tv, lane);
     }
+}
+
+// ------------------------------------------------------------ NFA rows
+// Visits delta(q, c) as (state | FINAL_BIT) values: from the band row of q
+// when it has one, otherwise from the CSR arrays.
+template <class F>
+__device__ __forceinline__ void nfa_targets(const MView &mv, const unsigned long long *band,
+                                            uint32_t q, uint32_t c, uint64_t pol_keep, F &&f) {
+    if (band) {
+        const unsigned long long row = band[q];
+        if (row != BAND_CSR) {
+            uint32_t m = static_cast<uint32_t>(row >> (8 * c)) & 0xFFu;
+            const uint32_t fm = static_cast<uint32_t>(row >> (32 + 8 * c)) & 0xFFu;
+            while (m) {
+                const uint32_t d = __ffs(m) - 1;
+                m &= m - 1;
+                f((q + 1 + d) | (((fm >> d) & 1u) << 15));
+            }
+            return;
+        }
+    }
+    const uint32_t lo = ldg_u32_keep(mv.off + q * mv.S + c, pol_keep);
+    const uint32_t hi = ldg_u32_keep(mv.off + q * mv.S + c + 1, pol_keep);
+    for (uint32_t e = lo; e < hi; ++e) f(static_cast<uint32_t>(ldg_u16_keep(mv.tgt + e, pol_keep)));
+}
+
+// Advances the state set of a prefix record in registers through band rows.
+// True when the instance provably reports nothing: its set empties before any
+// final state is reached, or the text ends. False hands it to the exact path
+// (a final target, a set larger than the registers, a row outside the band,
+// or the staged text runs out), which redoes it from its record.
+__device__ __forceinline__ bool nfa_settle(const MView &mv, const Smem &sm, const TileView &tv,
+                                           uint32_t start, uint32_t rec) {
+    const uint32_t hdr = sm.pool[rec];
+    const uint32_t ns = hdr >> 16;
+    if ((hdr & 0xFFFFu) != 0 || ns > static_cast<uint32_t>(NFA_INLINE)) return false;
+    uint32_t s[NFA_INLINE];
+#pragma unroll
+    for (int i = 0; i < NFA_INLINE; ++i) s[i] = static_cast<uint32_t>(i) < ns ? sm.pool[rec + 1 + i] : 0u;
+    uint32_t cnt = ns;
+    uint32_t pos = start + mv.k;
+    const uint32_t tile_end = tv.b + tv.len;
+    for (int step = 0; step < INLINE_STEPS; ++step) {
+        if (cnt == 0 || pos >= tv.n) return true;
+        if (pos >= tile_end) return false;
+        const uint32_t c = tv.sm[pos - tv.b];
+        if (c >= static_cast<uint32_t>(mv.S)) return true;   // the scan fails with E_INVAL
+        uint32_t t[NFA_INLINE];
+#pragma unroll
+        for (int j = 0; j < NFA_INLINE; ++j) t[j] = 0;
+        uint32_t tc = 0;
+#pragma unroll
+        for (int i = 0; i < NFA_INLINE; ++i) {
+            if (static_cast<uint32_t>(i) < cnt) {
+                const unsigned long long row = sm.band[s[i]];
+                if (row == BAND_CSR) return false;
+                uint32_t m = static_cast<uint32_t>(row >> (8 * c)) & 0xFFu;
+                if (m & static_cast<uint32_t>(row >> (32 + 8 * c))) return false;
+                while (m) {
+                    const uint32_t tt = s[i] + __ffs(m);
+                    m &= m - 1;
+                    bool dup = false;
+#pragma unroll
+                    for (int j = 0; j < NFA_INLINE; ++j) dup |= (static_cast<uint32_t>(j) < tc) && t[j] == tt;
+                    if (!dup) {
+                        if (tc == static_cast<uint32_t>(NFA_INLINE)) return false;
+#pragma unroll
+                        for (int j = 0; j < NFA_INLINE; ++j)
+                            if (static_cast<uint32_t>(j) == tc) t[j] = tt;
+                        ++tc;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NFA_INLINE; ++j) s[j] = t[j];
+        cnt = tc;
+        ++pos;
+    }
+    return cnt == 0;
 }
 
 // ------------------------------------------------------------ continuation: NFA
 // Warp-cooperative advance of one instance as a bitset over Q (lazy data
 // partitioning: reads the global text once past the staged bytes).
-__device__ void coop_run(const ScanArgs &a, const TileView &tv, uint32_t *bits0,
-                         uint32_t *bits1, uint32_t start, uint32_t pos, int lane,
-                         uint64_t pol_keep) {
-    const uint32_t Wq = a.Wq, S = a.S, n = a.n;
+template <int OUTW>
+__device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
+                                      const unsigned long long *band, const TileView &tv,
+                                      uint32_t *bits0, uint32_t *bits1, uint32_t start,
+                                      uint32_t pos, int lane, uint64_t pol_keep) {
+    const uint32_t Wq = mv.Wq, S = mv.S, n = tv.n;
     uint32_t *cur = bits0, *nxt = bits1;
     while (pos < n) {
-        const uint32_t c = text_at(a, tv, pos);
+        const uint32_t c = text_at(tv, pos);
         if (c >= S) break;
         for (uint32_t w = lane; w < Wq; w += 32) {
             uint32_t x = cur[w];
             while (x) {
                 const uint32_t bit = __ffs(x) - 1;
                 x &= x - 1;
-                const uint32_t q = w * 32 + bit;
-                const uint32_t lo = ldg_u32_keep(a.off + q * S + c, pol_keep);
-                const uint32_t hi = ldg_u32_keep(a.off + q * S + c + 1, pol_keep);
-                for (uint32_t e = lo; e < hi; ++e) {
-                    const uint32_t t = ldg_u16_keep(a.tgt + e, pol_keep);
+                nfa_targets(mv, band, w * 32 + bit, c, pol_keep, [&](uint32_t t) {
                     const uint32_t ts = t & 0x7FFFu;
                     const uint32_t mb = 1u << (ts & 31);
                     const uint32_t old = atomicOr(&nxt[ts >> 5], mb);
-                    if ((t & FINAL_BIT) && !(old & mb)) emit_direct(a, start, pos, ts);
-                }
+                    if ((t & FINAL_BIT) && !(old & mb)) emit_direct<OUTW>(ov, tv.orig, start, pos, ts);
+                });
             }
         }
         __syncwarp();
@@ -336,12 +461,15 @@ __device__ void coop_run(const ScanArgs &a, const TileView &tv, uint32_t *bits0,
 
 enum : uint32_t { MODE_LANE = 0, MODE_COOP_SLOT = 1, MODE_COOP_POOL = 2 };
 
-__device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
-                          const uint32_t *queue, uint16_t *slots, uint32_t *coop,
-                          uint32_t *stage, uint32_t &sn, int lane, uint64_t pol_keep) {
-    const uint32_t qn = misc->q_count;
-    const uint32_t S = a.S, n = a.n;
+// Drains the work queue for an NFA: each lane holds one instance's state set
+// (up to NFA_SLOT states) and advances it one symbol per iteration.
+template <int OUTW>
+__device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
+                          uint32_t &sn, int lane, uint64_t pol_keep) {
+    const uint32_t qn = sm.misc->q_count;
+    const uint32_t S = mv.S, n = tv.n;
     constexpr int C = NFA_SLOT;
+    uint16_t *slots = sm.slots;
 #define SLOT(sel, i) slots[((sel) * C + (i)) * 32 + lane]
     bool act = false;
     uint32_t start = 0, pos = 0, cnt = 0, cb = 0, mode = MODE_LANE;
@@ -351,37 +479,35 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
         const uint32_t m = __ballot_sync(FULLMASK, need);
         if (m) {
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&misc->q_head, __popc(m));
+            if (lane == 0) base = atomicAdd(&sm.misc->q_head, __popc(m));
             base = __shfl_sync(FULLMASK, base, 0);
             if (need) {
                 const uint32_t qi = base + __popc(m & lanemask_lt());
                 if (qi < qn) {
-                    const uint32_t e = queue[qi];
+                    const uint32_t e = sm.queue[qi];
                     start = tv.b + (e & 0xFFFFu);
                     const uint32_t info = e >> 16;
                     act = true;
                     mode = MODE_LANE;
                     pm_left = 0;
                     if (info == PT_WALK) {
-                        SLOT(cb, 0) = static_cast<uint16_t>(a.q0);
+                        SLOT(cb, 0) = static_cast<uint16_t>(mv.q0);
                         cnt = 1;
                         pos = start;
                     } else {
-                        const uint32_t ro = ldg_u32_keep(a.rec_off + info, pol_keep);
-                        const uint32_t w0 = ldg_u32_keep(a.pool + ro, pol_keep);
+                        const uint32_t ro = info;
+                        const uint32_t w0 = sm.pool[ro];
                         const uint32_t nm = w0 & 0xFFFFu, ns = w0 >> 16;
                         pm_left = nm;
                         pm_ptr = ro + 1;
-                        pos = start + a.k;
+                        pos = start + mv.k;
+                        cnt = ns;
                         if (ns > static_cast<uint32_t>(C)) {
                             mode = MODE_COOP_POOL;
                             cptr = ro + 1 + nm;
-                            cnt = ns;
                         } else {
                             for (uint32_t i = 0; i < ns; ++i)
-                                SLOT(cb, i) = static_cast<uint16_t>(
-                                    ldg_u32_keep(a.pool + ro + 1 + nm + i, pol_keep));
-                            cnt = ns;
+                                SLOT(cb, i) = static_cast<uint16_t>(sm.pool[ro + 1 + nm + i]);
                         }
                     }
                 }
@@ -394,13 +520,13 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
             const bool has = pm_left > 0;
             uint32_t o = 0, f = 0;
             if (has) {
-                const uint32_t w = ldg_u32_keep(a.pool + pm_ptr, pol_keep);
+                const uint32_t w = sm.pool[pm_ptr];
                 o = w >> 16;
                 f = w & 0xFFFFu;
                 ++pm_ptr;
                 --pm_left;
             }
-            warp_emit(has, start, start + o, f, stage, sn, a, lane);
+            warp_emit<OUTW>(has, start, start + o, f, sm.stage, sn, ov, tv, lane);
         }
         if (act && mode == MODE_LANE && cnt == 0) act = false;
 
@@ -410,7 +536,7 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
             if (pos >= n) {
                 act = false;
             } else {
-                const uint32_t c = text_at(a, tv, pos);
+                const uint32_t c = text_at(tv, pos);
                 if (c >= S) {
                     act = false;
                 } else {
@@ -418,26 +544,19 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
                     bool ovf = false;
                     for (uint32_t i = 0; i < cnt && !ovf; ++i) {
                         const uint32_t q = SLOT(cb, i) & 0x7FFFu;
-                        const uint32_t lo = ldg_u32_keep(a.off + q * S + c, pol_keep);
-                        const uint32_t hi = ldg_u32_keep(a.off + q * S + c + 1, pol_keep);
-                        for (uint32_t e = lo; e < hi; ++e) {
-                            const uint16_t t = ldg_u16_keep(a.tgt + e, pol_keep);
+                        nfa_targets(mv, sm.band, q, c, pol_keep, [&](uint32_t t) {
+                            if (ovf) return;
                             const uint32_t ts = t & 0x7FFFu;
-                            bool dup = false;
                             for (uint32_t j = 0; j < ncnt; ++j)
-                                if ((SLOT(cb ^ 1, j) & 0x7FFFu) == ts) {
-                                    dup = true;
-                                    break;
-                                }
-                            if (dup) continue;
+                                if ((SLOT(cb ^ 1, j) & 0x7FFFu) == ts) return;
                             if (ncnt == static_cast<uint32_t>(C)) {
                                 ovf = true;
-                                break;
+                                return;
                             }
-                            SLOT(cb ^ 1, ncnt) = t;
+                            SLOT(cb ^ 1, ncnt) = static_cast<uint16_t>(t);
                             ++ncnt;
                             anyfin |= (t & FINAL_BIT) != 0;
-                        }
+                        });
                     }
                     if (ovf) {
                         mode = MODE_COOP_SLOT;   // redo this symbol on the warp
@@ -452,8 +571,8 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
         if (__any_sync(FULLMASK, anyfin)) {
             for (uint32_t j = 0; j < static_cast<uint32_t>(C); ++j) {
                 const bool has = anyfin && j < cnt && (SLOT(cb, j) & FINAL_BIT);
-                warp_emit(has, start, pos, has ? (SLOT(cb, j) & 0x7FFFu) : 0u, stage, sn, a,
-                          lane);
+                warp_emit<OUTW>(has, start, pos, has ? (SLOT(cb, j) & 0x7FFFu) : 0u, sm.stage,
+                                sn, ov, tv, lane);
             }
         }
         if (act && mode == MODE_LANE) {
@@ -472,8 +591,8 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
             const uint32_t ccnt = __shfl_sync(FULLMASK, cnt, src);
             const uint32_t ccb = __shfl_sync(FULLMASK, cb, src);
             const uint32_t cpt = __shfl_sync(FULLMASK, cptr, src);
-            uint32_t *b0 = coop, *b1 = coop + a.Wq;
-            for (uint32_t w = lane; w < static_cast<uint32_t>(a.Wq); w += 32) {
+            uint32_t *b0 = sm.coop, *b1 = sm.coop + mv.Wq;
+            for (uint32_t w = lane; w < static_cast<uint32_t>(mv.Wq); w += 32) {
                 b0[w] = 0;
                 b1[w] = 0;
             }
@@ -485,12 +604,12 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
                 }
             } else {
                 for (uint32_t i = lane; i < ccnt; i += 32) {
-                    const uint32_t q = ldg_u32_keep(a.pool + cpt + i, pol_keep);
+                    const uint32_t q = sm.pool[cpt + i];
                     atomicOr(&b0[q >> 5], 1u << (q & 31));
                 }
             }
             __syncwarp();
-            coop_run(a, tv, b0, b1, cs, cp, lane, pol_keep);
+            coop_run<OUTW>(ov, mv, sm.band, tv, b0, b1, cs, cp, lane, pol_keep);
             if (lane == src) {
                 act = false;
                 mode = MODE_LANE;
@@ -500,37 +619,193 @@ __device__ void drain_nfa(const ScanArgs &a, const TileView &tv, Misc *misc,
 #undef SLOT
 }
 
-// ------------------------------------------------------------ the tile kernel
-template <int KIND, int SB, bool TAB_SMEM>
-__global__ void __launch_bounds__(512) scan_tiles(const ScanArgs a) {
-    extern __shared__ __align__(128) uint8_t sm[];
+template <int KIND, bool TAB_SMEM, int OUTW>
+__device__ __forceinline__ void drain(const OView &ov, const MView &mv, const TileView &tv,
+                                      const Smem &sm, uint32_t &sn, int lane, uint64_t pol_keep) {
+    if (KIND == 0)
+        drain_dfa<TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+    else
+        drain_nfa<OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+}
+
+// ------------------------------------------------------------ one tile
+// Filter phase over the tile's own starts [b, own_end), then the
+// continuation of every queued instance. All threads of the CTA call this.
+template <int KIND, int SB, bool TAB_SMEM, int OUTW>
+__device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
+                             const Smem &sm, uint32_t own_end, uint32_t qcap, uint32_t &sn,
+                             bool &bad_symbol, uint64_t pol_keep) {
     constexpr int SPT = 8;   // starts per thread per filter round
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int NT = blockDim.x;
+    const uint32_t n = tv.n, b = tv.b;
+    const uint32_t kk = static_cast<uint32_t>(mv.k);
+    const uint32_t kbits = static_cast<uint32_t>(mv.k * mv.sbits);
+    const uint32_t mask = kbits >= 32 ? 0xFFFFFFFFu : ((1u << kbits) - 1);
+    const uint32_t round = SPT * NT;
+    for (uint32_t r0 = b; r0 < own_end; r0 += round) {
+        if (sm.misc->q_count + round > qcap) {
+            drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+            __syncthreads();
+            if (tid == 0) {
+                sm.misc->q_count = 0;
+                sm.misc->q_head = 0;
+            }
+            __syncthreads();
+        }
+        const uint32_t i0 = r0 + SPT * tid;
+        uint32_t pm = 0;
+        uint32_t ent[SPT];
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) ent[r] = 0;
+        if (KIND == 1) {
+            // NFA: settle small sets in registers; queue the rest directly
+            if (i0 < own_end) {
+                const uint8_t *tp = tv.sm + (i0 - b);
+                const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
+                if (mv.S < 256) {
+                    uint64_t badm = bytes_ge(lo, mv.S);
+                    if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
+                    if (badm) bad_symbol = true;
+                }
+                const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+#pragma unroll 1
+                for (uint32_t r = 0; r < nown; ++r) {
+                    const uint32_t i = i0 + r;
+                    uint32_t e;
+                    if (kk == 0 || i + kk > n) {
+                        e = PT_WALK;
+                    } else {
+                        e = sm.memo[memo_index<SB>(lo, hi, p2, r, mv.k, mv.sbits, mask)];
+                        if (e == PT_SKIP) continue;
+                        if (sm.band && nfa_settle(mv, sm, tv, i, e)) continue;
+                    }
+                    const uint32_t p = atomicAdd(&sm.misc->q_count, 1u);
+                    sm.queue[p] = (i - b) | (e << 16);
+                }
+            }
+        } else {
+            if (i0 < own_end) {
+                const uint8_t *tp = tv.sm + (i0 - b);
+                const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
+                if (mv.S < 256) {
+                    uint64_t badm = bytes_ge(lo, mv.S);
+                    if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
+                    if (badm) bad_symbol = true;
+                }
+                const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+    #pragma unroll
+                for (int r = 0; r < SPT; ++r) {
+                    if (static_cast<uint32_t>(r) < nown) {
+                        const uint32_t i = i0 + r;
+                        if (kk == 0 || i + kk > n) {
+                            ent[r] = PT_WALK;
+                            pm |= 1u << r;
+                        } else {
+                            const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mv.k, mv.sbits, mask);
+                            const uint16_t e = sm.memo[idx];
+                            if (e != PT_SKIP) {
+                                ent[r] = e;
+                                pm |= 1u << r;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // warp-aggregated append to the CTA work queue
+        const uint32_t c = __popc(pm);
+        if (KIND == 0 && __ballot_sync(FULLMASK, c != 0)) {
+            uint32_t incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const uint32_t wtot = __shfl_sync(FULLMASK, incl, 31);
+            uint32_t wbase = 0;
+            if (lane == 31) wbase = atomicAdd(&sm.misc->q_count, wtot);
+            wbase = __shfl_sync(FULLMASK, wbase, 31);
+            uint32_t p = wbase + incl - c;
+#pragma unroll
+            for (int r = 0; r < SPT; ++r)
+                if (pm >> r & 1u) sm.queue[p++] = (i0 + r - b) | (ent[r] << 16);
+        }
+        __syncthreads();
+    }
+    drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+    __syncthreads();
+    if (tid == 0) {
+        sm.misc->q_count = 0;
+        sm.misc->q_head = 0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid) {
+    Smem s;
+    s.misc = reinterpret_cast<Misc *>(base + a.sm_misc);
+    s.memo = reinterpret_cast<const uint16_t *>(base + a.sm_memo);
+    s.tab = reinterpret_cast<const uint16_t *>(base + a.sm_tab);
+    s.queue = reinterpret_cast<uint32_t *>(base + a.sm_queue);
+    s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
+    s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
+    s.coop = reinterpret_cast<uint32_t *>(base + a.sm_coop) + wid * (2 * a.Wq);
+    s.band = a.band_smem ? reinterpret_cast<const unsigned long long *>(base + a.sm_band) : a.band;
+    s.pool = a.pool_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_pool) : a.pool;
+    return s;
+}
+
+__device__ __forceinline__ void stage_u16(uint16_t *dst, const uint16_t *src, uint32_t count,
+                                          int tid, int nt) {
+    const uint32_t words = (count + 1) / 2;
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = tid; i < words; i += nt) d[i] = __ldg(s + i);
+}
+
+// Copies an NFA's band rows and prefix records into shared memory (either
+// source may be null: that table is then read from global memory).
+__device__ __forceinline__ void stage_nfa(uint8_t *base, uint32_t sm_band, uint32_t sm_pool,
+                                          const unsigned long long *band, int32_t Q,
+                                          const uint32_t *pool, uint32_t pool_n, int tid,
+                                          int nt) {
+    if (band) {
+        unsigned long long *d = reinterpret_cast<unsigned long long *>(base + sm_band);
+        for (int32_t i = tid; i < Q; i += nt) d[i] = __ldg(band + i);
+    }
+    if (pool) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(base + sm_pool);
+        for (uint32_t i = tid; i < pool_n; i += nt) d[i] = __ldg(pool + i);
+    }
+}
+
+// ------------------------------------------------------------ single-text kernel
+template <int KIND, int SB, bool TAB_SMEM>
+__global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int NT = blockDim.x;
-    Misc *misc = reinterpret_cast<Misc *>(sm + a.sm_misc);
-    uint16_t *memo_sm = reinterpret_cast<uint16_t *>(sm + a.sm_memo);
-    uint16_t *tab_sm = reinterpret_cast<uint16_t *>(sm + a.sm_tab);
-    uint8_t *text_sm = sm + a.sm_text;
-    uint32_t *queue = reinterpret_cast<uint32_t *>(sm + a.sm_queue);
-    uint32_t *stage = reinterpret_cast<uint32_t *>(sm + a.sm_stage) + wid * (3 * STAGE);
-    uint16_t *slots = reinterpret_cast<uint16_t *>(sm + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
-    uint32_t *coop = reinterpret_cast<uint32_t *>(sm + a.sm_coop) + wid * (2 * a.Wq);
+    const Smem sm = smem_regions(smem, a, wid);
+    Misc *misc = sm.misc;
+    uint8_t *text_sm = smem + a.sm_text;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
+    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
+    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.dtab, a.off, a.tgt};
 
-    // tables into shared memory
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.memo);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(memo_sm);
-        const uint32_t words = (a.memo_n + 1) / 2;
-        for (uint32_t i = tid; i < words; i += NT) dst[i] = __ldg(src + i);
-        if (TAB_SMEM) {
-            const uint32_t tw = (static_cast<uint32_t>(a.Q) * a.S + 1) / 2;
-            const uint32_t *ts = reinterpret_cast<const uint32_t *>(a.dtab);
-            uint32_t *td = reinterpret_cast<uint32_t *>(tab_sm);
-            for (uint32_t i = tid; i < tw; i += NT) td[i] = __ldg(ts + i);
-        }
-    }
+    stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
+    if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
+    if (KIND == 1) stage_nfa(smem, a.sm_band, a.sm_pool, a.band_smem ? a.band : nullptr, a.Q,
+                             a.pool_smem ? a.pool : nullptr, a.pool_n, tid, NT);
     if (tid == 0) {
         mbar_init(&misc->bar[0], 1);
         mbar_init(&misc->bar[1], 1);
@@ -541,10 +816,9 @@ __global__ void __launch_bounds__(512) scan_tiles(const ScanArgs a) {
     }
     __syncthreads();
 
-    uint32_t sn = 0;   // staged matches of this warp
+    uint32_t sn = 0;
     bool bad_symbol = false;
     const uint32_t n = a.n;
-
     auto issue = [&](uint32_t tile, int buf) {
         const uint32_t b = tile * a.tile;
         const uint32_t len = min(a.tile + a.halo, n - b);
@@ -566,8 +840,6 @@ __global__ void __launch_bounds__(512) scan_tiles(const ScanArgs a) {
         const uint32_t len = min(a.tile + a.halo, n - b);
         const uint32_t len16 = len & ~15u;
         uint8_t *tsm = text_sm + buf * a.text_buf;
-        // prefetch the next tile into the other buffer (freed at the end of
-        // the previous iteration)
         if (tid == 0 && tile + gridDim.x < a.ntiles) issue(tile + gridDim.x, buf ^ 1);
         if (a.aligned && len16) {
             if (!mbar_wait_bounded(&misc->bar[buf], parity)) misc->abort = 1;
@@ -577,131 +849,222 @@ __global__ void __launch_bounds__(512) scan_tiles(const ScanArgs a) {
         }
         __syncthreads();
         if (misc->abort) break;
-        const TileView tv{tsm, b, len};
+        const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
+        process_tile<KIND, SB, TAB_SMEM, 3>(ov, mv, tv, sm, min(b + a.tile, n), a.qcap, sn,
+                                            bad_symbol, pol_keep);
+    }
+    stage_flush<3>(sm.stage, sn, ov, 0u, lane);
+    if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
+    if (tid == 0 && misc->abort) {
+        atomicOr(&a.status[1], ERR_TIMEOUT);
+        // a copy may still be in flight: wait for it (bounded) before exit
+        mbar_wait_bounded(&misc->bar[0], 0);
+        mbar_wait_bounded(&misc->bar[1], 0);
+    }
+}
 
-        // ---------------- filter phase over the tile's own starts
-        const uint32_t own_end = min(b + a.tile, n);
-        const uint32_t kk = static_cast<uint32_t>(a.k);
-        const uint32_t mask = (a.k * a.sbits >= 32) ? 0xFFFFFFFFu : ((1u << (a.k * a.sbits)) - 1);
-        const uint32_t round = SPT * NT;
-        for (uint32_t r0 = b; r0 < own_end; r0 += round) {
-            if (misc->q_count + round > a.qcap) {
-                if (KIND == 0)
-                    drain_dfa<TAB_SMEM>(a, tv, misc, queue, tab_sm, stage, sn, lane, pol_keep);
-                else
-                    drain_nfa(a, tv, misc, queue, slots, coop, stage, sn, lane, pol_keep);
-                __syncthreads();
-                if (tid == 0) {
-                    misc->q_count = 0;
-                    misc->q_head = 0;
-                }
-                __syncthreads();
-            }
-            const uint32_t i0 = r0 + SPT * tid;
-            uint32_t pm = 0;
-            uint32_t ent[SPT];
-#pragma unroll
-            for (int r = 0; r < SPT; ++r) ent[r] = 0;
-            if (i0 < own_end) {
-                const uint8_t *tp = tsm + (i0 - b);
-                const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-                const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-                const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-                const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
-                const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
-                if (a.S < 256) {
-                    uint64_t badm = bytes_ge(lo, a.S);
-                    if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
-                    if (badm) bad_symbol = true;
-                }
-                const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
-#pragma unroll
-                for (int r = 0; r < SPT; ++r) {
-                    if (static_cast<uint32_t>(r) < nown) {
-                        const uint32_t i = i0 + r;
-                        if (kk == 0 || i + kk > n) {
-                            ent[r] = PT_WALK;
-                            pm |= 1u << r;
-                        } else {
-                            const uint32_t idx = memo_index<SB>(lo, hi, p2, r, a.k, a.sbits, mask);
-                            const uint16_t e = memo_sm[idx];
-                            if (e != PT_SKIP) {
-                                ent[r] = e;
-                                pm |= 1u << r;
-                            }
-                        }
-                    }
-                }
-            }
-            // warp-aggregated append to the CTA work queue
-            const uint32_t c = __popc(pm);
-            if (__ballot_sync(FULLMASK, c != 0)) {
-                uint32_t incl = c;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
-                    if (lane >= d) incl += v;
-                }
-                const uint32_t wtot = __shfl_sync(FULLMASK, incl, 31);
-                uint32_t wbase = 0;
-                if (lane == 31) wbase = atomicAdd(&misc->q_count, wtot);
-                wbase = __shfl_sync(FULLMASK, wbase, 31);
-                uint32_t p = wbase + incl - c;
-#pragma unroll
-                for (int r = 0; r < SPT; ++r)
-                    if (pm >> r & 1u) queue[p++] = (i0 + r - b) | (ent[r] << 16);
-            }
-            __syncthreads();
+// ------------------------------------------------------------ batch kernel
+// Persistent CTAs pull (text, tile) work items from a global counter. Items
+// are ordered by machine, so a CTA usually keeps its machine's tables in
+// shared memory from one item to the next.
+struct ItemDesc {
+    const uint8_t *text;
+    uint32_t item, job, orig, mach, b, len, n, tma, parity, pad;
+};
+
+__device__ __forceinline__ uint32_t find_job(const BatchJob *jobs, uint32_t njobs, uint32_t item) {
+    uint32_t lo = 0, hi = njobs;   // last job with tile_begin <= item
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].tile_begin <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ MView mview_of(const DevMachine &m) {
+    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.dtab, m.off, m.tgt};
+}
+
+__global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict__ gargs) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ BatchArgs A;
+    __shared__ ItemDesc desc[2];
+    __shared__ int32_t cur_mach;
+    __shared__ uint32_t tma_uses[2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int NT = blockDim.x;
+    if (tid == 0) {
+        A = *gargs;
+        cur_mach = -1;
+        tma_uses[0] = tma_uses[1] = 0;
+    }
+    __syncthreads();
+    const Smem sm = smem_regions(smem, A.sa, wid);
+    Misc *misc = sm.misc;
+    uint8_t *text_sm = smem + A.sa.sm_text;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const OView ov{A.sa.out, A.sa.cap, A.sa.status, A.job_counts, A.sa.carry, A.sa.carry_n,
+                   A.sa.carry_cap, A.sa.stage_n};
+    if (tid == 0) {
+        mbar_init(&misc->bar[0], 1);
+        mbar_init(&misc->bar[1], 1);
+        misc->q_count = 0;
+        misc->q_head = 0;
+        misc->abort = 0;
+        fence_mbar_init();
+    }
+
+    // tid 0: claim the next item and start its copy into buffer `buf`
+    auto claim = [&](int buf) {
+        ItemDesc &d = desc[buf];
+        d.item = atomicAdd(A.item_counter, 1u);
+        if (d.item >= A.nitems) return;
+        d.job = find_job(A.jobs, A.njobs, d.item);
+        const BatchJob &J = A.jobs[d.job];
+        d.text = J.text;
+        d.n = J.n;
+        d.orig = J.orig;
+        d.mach = J.mach;
+        d.b = (d.item - J.tile_begin) * A.sa.tile;
+        d.len = min(A.sa.tile + A.sa.halo, d.n - d.b);
+        const uint32_t len16 = d.len & ~15u;
+        d.tma = (((reinterpret_cast<uintptr_t>(d.text) & 15) == 0) && len16) ? 1u : 0u;
+        if (d.tma) {
+            d.parity = tma_uses[buf] & 1;
+            tma_uses[buf]++;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&misc->bar[buf], len16);
+            tma_load_1d(text_sm + buf * A.sa.text_buf, d.text + d.b, len16, &misc->bar[buf],
+                        pol_stream);
         }
-        // ---------------- continuation phase
-        if (KIND == 0)
-            drain_dfa<TAB_SMEM>(a, tv, misc, queue, tab_sm, stage, sn, lane, pol_keep);
-        else
-            drain_nfa(a, tv, misc, queue, slots, coop, stage, sn, lane, pol_keep);
+    };
+    if (tid == 0) claim(0);
+    __syncthreads();
+
+    uint32_t sn = 0;
+    bool bad_symbol = false;
+    for (uint32_t it = 0;; ++it) {
+        const int buf = it & 1;
+        if (desc[buf].item >= A.nitems) break;
+        const ItemDesc d = desc[buf];
+        if (tid == 0) claim(buf ^ 1);   // prefetch the next item
+        const DevMachine &M = A.machs[d.mach];
+        if (static_cast<int32_t>(d.mach) != cur_mach) {
+            stage_u16(const_cast<uint16_t *>(sm.memo), M.memo, M.memo_n, tid, NT);
+            if (M.tab_smem) stage_u16(const_cast<uint16_t *>(sm.tab), M.dtab, M.Q * M.S, tid, NT);
+            if (M.kind == 1)
+                stage_nfa(smem, A.sa.sm_band, A.sa.sm_pool, M.band_smem ? M.band : nullptr, M.Q,
+                          M.pool_smem ? M.pool : nullptr, M.pool_n, tid, NT);
+        }
+        Smem smi = sm;
+        smi.band = M.band_smem ? reinterpret_cast<const unsigned long long *>(smem + A.sa.sm_band)
+                               : M.band;
+        smi.pool = M.pool_smem ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_pool) : M.pool;
+        uint8_t *tsm = text_sm + buf * A.sa.text_buf;
+        if (d.tma) {
+            if (!mbar_wait_bounded(&misc->bar[buf], d.parity)) misc->abort = 1;
+            for (uint32_t i = (d.len & ~15u) + tid; i < d.len; i += NT) tsm[i] = d.text[d.b + i];
+        } else {
+            for (uint32_t i = tid; i < d.len; i += NT) tsm[i] = d.text[d.b + i];
+        }
         __syncthreads();
-        if (tid == 0) {
-            misc->q_count = 0;
-            misc->q_head = 0;
+        if (tid == 0) cur_mach = static_cast<int32_t>(d.mach);
+        if (misc->abort) break;
+        const MView mv = mview_of(M);
+        const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
+        const uint32_t own_end = min(d.b + A.sa.tile, d.n);
+        const uint32_t qcap = A.sa.qcap;
+        if (M.kind == 0) {
+            if (M.tab_smem) {
+                if (M.sbits == 2 && M.k > 0)
+                    process_tile<0, 2, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                else
+                    process_tile<0, 0, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+            } else {
+                if (M.sbits == 8 && M.k > 0)
+                    process_tile<0, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                else if (M.sbits == 2 && M.k > 0)
+                    process_tile<0, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                else
+                    process_tile<0, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+            }
+        } else {
+            if (M.sbits == 2 && M.k > 0)
+                process_tile<1, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+            else if (M.sbits == 8 && M.k > 0)
+                process_tile<1, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+            else
+                process_tile<1, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
         }
+        // per-text counts: the staged matches all belong to this item's text
+        stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
         __syncthreads();
     }
-    stage_flush(stage, sn, a, lane);
-    if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
-    if (tid == 0 && misc->abort) atomicOr(&a.status[1], ERR_TIMEOUT);
-    // a tile whose copy timed out may still have one in flight: wait for it
-    // (bounded) before the CTA's shared memory is released
+    if (bad_symbol) atomicOr(&A.sa.status[1], ERR_SYMBOL);
     if (tid == 0 && misc->abort) {
+        atomicOr(&A.sa.status[1], ERR_TIMEOUT);
         mbar_wait_bounded(&misc->bar[0], 0);
         mbar_wait_bounded(&misc->bar[1], 0);
     }
 }
 
 // ------------------------------------------------------------ DFA carry queue
-// Continues instances that outlived their tile's staged text, reading the
-// text from global memory (chained data partitioning).
+// Continues DFA instances that outlived their tile's staged text, reading the
+// text from global memory (chained data partitioning, Sec. III.D.2). Entries
+// are {job, start, pos, state}.
 __global__ void __launch_bounds__(256) carry_dfa(const ScanArgs a) {
     const uint32_t nc = min(*a.carry_n, a.carry_cap);
     const uint64_t pol_keep = policy_evict_last();
+    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
          idx += gridDim.x * blockDim.x) {
-        const uint32_t start = a.carry[3 * idx];
-        uint32_t pos = a.carry[3 * idx + 1];
-        uint32_t s = a.carry[3 * idx + 2];
+        const uint32_t *c = a.carry + 4 * idx;
+        const uint32_t start = c[1];
+        uint32_t pos = c[2], s = c[3];
         while (pos < a.n) {
-            const uint32_t c = __ldg(a.text + pos);
-            if (c >= static_cast<uint32_t>(a.S)) break;
-            const uint16_t e = ldg_u16_keep(a.dtab + s * a.S + c, pol_keep);
+            const uint32_t ch = __ldg(a.text + pos);
+            if (ch >= static_cast<uint32_t>(a.S)) break;
+            const uint16_t e = ldg_u16_keep(a.dtab + s * a.S + ch, pol_keep);
             if (e == DEAD16) break;
             s = e & 0x7FFFu;
-            if (e & FINAL_BIT) emit_direct(a, start, pos, s);
+            if (e & FINAL_BIT) emit_direct<3>(ov, 0u, start, pos, s);
+            ++pos;
+        }
+    }
+}
+
+// Batch form of the carry continuation; arguments come from device memory.
+__global__ void __launch_bounds__(256) carry_batch(const BatchArgs *__restrict__ g) {
+    const uint32_t nc = min(*g->sa.carry_n, g->sa.carry_cap);
+    const uint64_t pol_keep = policy_evict_last();
+    const OView ov{g->sa.out, g->sa.cap, g->sa.status, g->job_counts, g->sa.carry,
+                   g->sa.carry_n, g->sa.carry_cap, g->sa.stage_n};
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
+         idx += gridDim.x * blockDim.x) {
+        const uint32_t *c = g->sa.carry + 4 * idx;
+        const uint32_t start = c[1];
+        uint32_t pos = c[2], s = c[3];
+        const BatchJob &J = g->jobs[c[0]];
+        const DevMachine &M = g->machs[J.mach];
+        const uint32_t S = M.S;
+        while (pos < J.n) {
+            const uint32_t ch = __ldg(J.text + pos);
+            if (ch >= S) break;
+            const uint16_t e = ldg_u16_keep(M.dtab + s * S + ch, pol_keep);
+            if (e == DEAD16) break;
+            s = e & 0x7FFFu;
+            if (e & FINAL_BIT) emit_direct<4>(ov, J.orig, start, pos, s);
             ++pos;
         }
     }
 }
 
 // ------------------------------------------------------------ host helpers
-uint32_t layout_smem(ScanArgs &a, int kind, int threads, int spt) {
+uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &need) {
     const int nw = threads / 32;
+    const bool has_nfa = (kind_mask & 2) != 0;
     uint32_t o = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
         o = (o + align - 1) & ~(align - 1);
@@ -709,15 +1072,19 @@ uint32_t layout_smem(ScanArgs &a, int kind, int threads, int spt) {
         o += bytes;
         return r;
     };
+    if (a.stage_n == 0) a.stage_n = STAGE;
     a.sm_misc = take(sizeof(Misc), 16);
     a.sm_memo = take(((a.memo_n + 1) / 2) * 4 + 4, 16);
-    a.sm_tab = take(a.tab_smem ? ((static_cast<uint32_t>(a.Q) * a.S + 1) / 2) * 4 : 0, 16);
+    a.sm_tab = take(need.tab_bytes, 16);
+    a.sm_band = take(need.band_bytes, 16);
+    a.sm_pool = take(need.pool_bytes, 16);
+    a.band_smem = need.band_bytes > 0;
+    a.pool_smem = need.pool_bytes > 0;
     a.sm_text = take(2 * a.text_buf, 128);
     a.sm_queue = take(a.qcap * 4, 16);
-    a.sm_stage = take(nw * STAGE * 12, 16);
-    a.sm_slots = take(kind == 1 ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
-    a.sm_coop = take(kind == 1 ? nw * 2 * a.Wq * 4 : 0, 16);
-    (void)spt;
+    a.sm_stage = take(nw * a.stage_n * 16, 16);
+    a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
+    a.sm_coop = take(has_nfa ? nw * 2 * a.Wq * 4 : 0, 16);
     return (o + 127) & ~127u;
 }
 
@@ -739,18 +1106,31 @@ static cudaError_t launch_sb(const ScanArgs &a, int threads, int grid, uint32_t 
     return launch_t<KIND, 0, TAB>(a, threads, grid, smem, s);
 }
 
-cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, cudaStream_t s) {
-    ScanArgs c = a;
-    const uint32_t smem = layout_smem(c, kind, threads, 8);
+cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
+                        cudaStream_t s) {
     if (kind == 0) {
-        if (c.tab_smem) return launch_sb<0, true>(c, threads, grid, smem, s);
-        return launch_sb<0, false>(c, threads, grid, smem, s);
+        if (a.tab_smem) return launch_sb<0, true>(a, threads, grid, smem, s);
+        return launch_sb<0, false>(a, threads, grid, smem, s);
     }
-    return launch_sb<1, false>(c, threads, grid, smem, s);
+    return launch_sb<1, false>(a, threads, grid, smem, s);
 }
 
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s) {
     carry_dfa<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs *dev_args, int threads, int grid, uint32_t smem,
+                         cudaStream_t s) {
+    cudaError_t e =
+        cudaFuncSetAttribute(scan_items, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    scan_items<<<grid, threads, smem, s>>>(dev_args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_carry_batch(const BatchArgs *dev_args, int grid, cudaStream_t s) {
+    carry_batch<<<grid, 256, 0, s>>>(dev_args);
     return cudaGetLastError();
 }
 
@@ -780,6 +1160,15 @@ int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_sm
     if (sb == 2) return occ_t<1, 2, false>(threads, smem);
     if (sb == 8) return occ_t<1, 8, false>(threads, smem);
     return occ_t<1, 0, false>(threads, smem);
+}
+
+int max_batch_ctas_per_sm(int threads, uint32_t smem) {
+    int nb = 0;
+    cudaFuncSetAttribute(scan_items, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_items, threads, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
 }
 
 }  // namespace pfsm

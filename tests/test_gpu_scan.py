@@ -283,7 +283,7 @@ def test_instances_outliving_tiles_use_the_carry_queue(pf):
 
 
 def test_eviction_and_reload(pf):
-    small = P.Pfsm(0, budget_bytes=200_000)
+    small = P.Pfsm(0, budget_bytes=80_000)
     try:
         autos = [W.dfa_random(50 + i, Q=64, S=4) for i in range(3)]
         autos.append(W.workload_motif_nfa(3, n=10, n_motifs=40)[0])
@@ -294,7 +294,7 @@ def test_eviction_and_reload(pf):
                 assert np.array_equal(gpu_matches(small, i, t), oracle.scan(x, t))
         st = P.pfsm_get_stats(small.ctx)
         assert st["evictions"] > 0 and st["reloads"] > 0
-        assert st["resident_bytes"] <= 200_000
+        assert st["resident_bytes"] <= 80_000
         P.pfsm_evict(small.ctx, ids[0])
         assert np.array_equal(gpu_matches(small, ids[0], t), oracle.scan(autos[0], t))
         P.pfsm_unload(small.ctx, ids[1])
