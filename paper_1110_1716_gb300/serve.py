@@ -1,0 +1,239 @@
+"""Continuous-batching scan server on one GPU.
+
+Requests (machine, text) arrive at any time. A scheduler thread admits them
+into batch slots as device memory and slots free up: each slot owns a CUDA
+stream, a device text arena, a device match buffer and pinned host mirrors.
+Admitted requests are packed into the slot's arena, copied to the device and
+scanned with one ``pfsm_scan_batch_async`` call (one persistent launch replayed
+from a CUDA graph); while a slot's batch runs, newly arrived requests fill
+the next free slot, so batches from several slots overlap on the device.
+
+Machines stay resident on the device under the context's byte budget; the
+library evicts the least recently used ones and reloads them when a batch
+names them again (cold machines leave fast memory, Sec. I-II's insomnia).
+
+Each request's result is its own match set, bit-identical to a scan of that
+text alone; latency is measured from arrival to the moment its matches are
+on the host.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import (PFSM_OK, Pfsm, pfsm_get_stats, pfsm_scan_batch, pfsm_scan_batch_async)
+
+
+class Request:
+    __slots__ = ("rid", "aut", "text", "arrival", "future", "t_done")
+
+    def __init__(self, rid, aut, text, arrival):
+        self.rid = rid
+        self.aut = aut
+        self.text = text
+        self.arrival = arrival
+        self.future = Future()
+        self.t_done = None
+
+
+class _Slot:
+    def __init__(self, torch, dev, text_bytes, out_rows, max_jobs):
+        self.stream = torch.cuda.Stream(device=dev)
+        self.text_dev = torch.empty(text_bytes, dtype=torch.uint8, device=dev)
+        self.text_host = torch.empty(text_bytes, dtype=torch.uint8).pin_memory()
+        self.out_dev = torch.empty((out_rows, 4), dtype=torch.int32, device=dev)
+        self.out_host = torch.empty((out_rows, 4), dtype=torch.int32).pin_memory()
+        self.status_dev = torch.zeros(max_jobs + 2, dtype=torch.int64, device=dev)
+        self.status_host = torch.zeros(max_jobs + 2, dtype=torch.int64).pin_memory()
+        self.done = torch.cuda.Event()
+        self.reqs: List[Request] = []
+        self.busy = False
+        self.text_bytes = text_bytes
+        self.out_rows = out_rows
+        self.max_jobs = max_jobs
+
+
+class Server:
+    """Scan server over a ``Pfsm`` context.
+
+    automata     machines (``workloads.Dfa``/``Nfa``-shaped); request.aut
+                 indexes this list
+    slots        batch slots = CUDA streams with their own buffers
+    slot_bytes   text arena per slot (the largest request must fit)
+    out_rows     match capacity per slot (a batch that overflows is rerun
+                 synchronously with the exact capacity)
+    max_jobs     requests per batch
+    """
+
+    def __init__(self, pf: Pfsm, automata, slots: int = 3, slot_bytes: int = 64 << 20,
+                 out_rows: int = 4 << 20, max_jobs: int = 1024):
+        import torch
+        self.torch = torch
+        self.pf = pf
+        self.ids = [pf.load(a) for a in automata]
+        dev = torch.device("cuda", pf.device)
+        self.slots = [_Slot(torch, dev, slot_bytes, out_rows, max_jobs) for _ in range(slots)]
+        self.pending = collections.deque()
+        self.lock = threading.Condition()
+        self.running = False
+        self.thread = None
+        self.done: List[Request] = []
+        self.batches = 0
+        self.overflow_reruns = 0
+        self.bytes_scanned = 0
+        self.next_rid = 0
+
+    # -------------------------------------------------------------- client side
+    def submit(self, aut: int, text: np.ndarray, arrival: Optional[float] = None) -> Future:
+        text = np.ascontiguousarray(text, dtype=np.uint8)
+        if len(text) > self.slots[0].text_bytes:
+            raise ValueError("request larger than a slot's text arena")
+        with self.lock:
+            r = Request(self.next_rid, aut, text, time.perf_counter() if arrival is None else arrival)
+            self.next_rid += 1
+            self.pending.append(r)
+            self.lock.notify()
+        return r.future
+
+    def start(self):
+        self.running = True
+        self.thread = threading.Thread(target=self._loop, name="pfsm-serve", daemon=True)
+        self.thread.start()
+        return self
+
+    def stop(self):
+        with self.lock:
+            self.running = False
+            self.lock.notify()
+        if self.thread:
+            self.thread.join()
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *exc):
+        self.stop()
+        return False
+
+    # -------------------------------------------------------------- scheduler
+    def _admit(self, slot: _Slot) -> bool:
+        """Pack pending requests into a free slot and launch its batch."""
+        reqs, used = [], 0
+        with self.lock:
+            while self.pending and len(reqs) < slot.max_jobs:
+                r = self.pending[0]
+                if used + len(r.text) > slot.text_bytes:
+                    break
+                self.pending.popleft()
+                reqs.append(r)
+                used += (len(r.text) + 15) & ~15
+        if not reqs:
+            return False
+        torch = self.torch
+        host = slot.text_host.numpy()
+        jobs, off = [], 0
+        base = slot.text_dev.data_ptr()
+        for r in reqs:
+            n = len(r.text)
+            host[off:off + n] = r.text
+            jobs.append((self.ids[r.aut], base + off, n))
+            off += (n + 15) & ~15
+        with torch.cuda.stream(slot.stream):
+            slot.text_dev[:off].copy_(slot.text_host[:off], non_blocking=True)
+            pfsm_scan_batch_async(self.pf.ctx, jobs, slot.out_dev, slot.status_dev[:len(jobs) + 2],
+                                  stream=slot.stream)
+            slot.status_host[:len(jobs) + 2].copy_(slot.status_dev[:len(jobs) + 2],
+                                                   non_blocking=True)
+            slot.done.record(slot.stream)
+        slot.reqs = reqs
+        slot.jobs = jobs
+        slot.busy = True
+        self.batches += 1
+        self.bytes_scanned += used
+        return True
+
+    def _complete(self, slot: _Slot):
+        st = slot.status_host.numpy()
+        k = len(slot.reqs)
+        total, err = int(st[0]), int(st[1])
+        counts = st[2:2 + k].astype(np.int64)
+        if err:
+            exc = RuntimeError("scan error bits %d" % err)
+            for r in slot.reqs:
+                r.future.set_exception(exc)
+        else:
+            torch = self.torch
+            if total > slot.out_rows:
+                # overflow: rerun this batch synchronously with room for all
+                self.overflow_reruns += 1
+                out = torch.empty((total, 4), dtype=torch.int32, device=slot.out_dev.device)
+                s2, counts2, total2 = pfsm_scan_batch(self.pf.ctx, slot.jobs, out, total,
+                                                      stream=slot.stream)
+                m = out[:total2].cpu().numpy().view(np.uint32)
+            else:
+                with torch.cuda.stream(slot.stream):
+                    slot.out_host[:total].copy_(slot.out_dev[:total], non_blocking=True)
+                slot.stream.synchronize()
+                m = slot.out_host[:total].numpy().view(np.uint32)
+            order = np.argsort(m[:, 0], kind="stable")
+            m = m[order]
+            bounds = np.searchsorted(m[:, 0], np.arange(k + 1))
+            now = time.perf_counter()
+            for i, r in enumerate(slot.reqs):
+                r.t_done = now
+                r.future.set_result(m[bounds[i]:bounds[i + 1], 1:])
+                self.done.append(r)
+        slot.reqs = []
+        slot.busy = False
+
+    def _loop(self):
+        while True:
+            progressed = False
+            for slot in self.slots:
+                if slot.busy and slot.done.query():
+                    self._complete(slot)
+                    progressed = True
+            for slot in self.slots:
+                if not slot.busy:
+                    if self._admit(slot):
+                        progressed = True
+            with self.lock:
+                if not self.running and not self.pending and not any(s.busy for s in self.slots):
+                    return
+                if not progressed and not any(s.busy for s in self.slots):
+                    self.lock.wait(timeout=0.001)
+            if not progressed:
+                time.sleep(20e-6)
+
+    # -------------------------------------------------------------- reporting
+    def latency_stats(self) -> Dict[str, float]:
+        lat = np.array([r.t_done - r.arrival for r in self.done if r.t_done is not None])
+        if len(lat) == 0:
+            return {}
+        return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "batches": self.batches,
+                "overflow_reruns": self.overflow_reruns, **{
+                    "residency_" + k: v for k, v in pfsm_get_stats(self.pf.ctx).items()}}
+
+
+def replay(server: Server, arrivals: np.ndarray, auts: np.ndarray, texts, t0: Optional[float] = None):
+    """Submit requests at their arrival offsets (seconds) in real time;
+    returns the futures. `texts[i]` is request i's text."""
+    t0 = time.perf_counter() if t0 is None else t0
+    futs = []
+    for i in range(len(arrivals)):
+        due = t0 + float(arrivals[i])
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            if due - now > 2e-4:
+                time.sleep((due - now) * 0.5)
+        futs.append(server.submit(int(auts[i]), texts[i], arrival=due))
+    return futs
