@@ -52,16 +52,36 @@ WORKLOADS = {
 }
 
 
-def make_workload(name, seed):
+def make_workload(name, seed, n=None):
+    """The named workload; `n` overrides the text length (smaller probes)."""
+    kw = {} if n is None else {"n": n}
     if name == "motif_nfa_64mib":
-        a, t, _, _ = W.workload_motif_nfa(seed)
+        a, t, _, _ = W.workload_motif_nfa(seed, **kw)
     elif name == "dna_dfa_1mib":
-        a, t = W.workload_dna_dfa(seed if seed else 1)
+        a, t = W.workload_dna_dfa(seed if seed else 1, **kw)
     elif name == "byte_trie_1gib":
-        a, t, _, _, _ = W.workload_byte_trie(seed)
+        a, t, _, _, _ = W.workload_byte_trie(seed, **kw)
     else:
         raise ValueError(name)
     return a, t
+
+
+def run_probe(args):
+    """Two scans of one workload (optionally resized with --bytes): the
+    command profiles are taken on."""
+    import torch
+    import paper_1110_1716_gb300 as P
+    aut, text = make_workload(args.workload, args.seed, args.bytes or None)
+    with P.Pfsm(0) as pf:
+        aid = pf.load(aut)
+        if args.params:
+            P.pfsm_set_params(pf.ctx, aid, json.loads(args.params))
+        t = pf.to_device(text)
+        for _ in range(2):
+            r = pf.scan(aid, t, cap=max(1 << 20, len(text) // 2))
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": args.workload, "bytes": len(text), "matches": int(r.shape[0]),
+                          "params": P.pfsm_get_params(pf.ctx, aid)}))
 
 
 def measured_peaks():
@@ -254,6 +274,10 @@ def run_ours(args, rank, world, local_rank):
 
     main = measure(args.workload, args.steps, args.warmup, args.seed)
     others = {}
+    if not args.only and not args.no_batch:
+        others["batch_10k_texts"] = measure_batch(P, pf, torch, dev)
+    if not args.only and not args.no_serve:
+        others["serving"] = measure_serving(P, pf, torch, dev)
     if not args.only:
         for name in WORKLOADS:
             if name == args.workload:
@@ -287,6 +311,116 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(main["aut"], main["text"])
     return line
+
+
+def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
+    """Batched form (one persistent launch over every text) against the plain
+    form (one pfsm_scan per text) on the mixed many-texts workload."""
+    t0 = time.perf_counter()
+    w = W.batch_workload(seed=0, n_texts=n_texts)
+    gen_s = time.perf_counter() - t0
+    ids = [pf.load(a) for a in w.automata]
+    data = pf.to_device(w.data)
+    jobs = [(ids[int(w.job_aut[i])], data[int(w.offsets[i]):int(w.offsets[i + 1])],
+             int(w.offsets[i + 1] - w.offsets[i])) for i in range(len(w.job_aut))]
+    total_bytes = int(w.offsets[-1])
+    st, counts, total = P.pfsm_scan_batch(pf.ctx, jobs, None, 0)
+    out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
+    status = torch.zeros(len(jobs) + 2, dtype=torch.int64, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    P.pfsm_scan_batch_async(pf.ctx, jobs, out, status, stream=s)   # warm (graph capture)
+    s.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        P.pfsm_scan_batch_async(pf.ctx, jobs, out, status, stream=s)
+        e1.record(s)
+        s.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    assert int(status[0].item()) == total and int(status[1].item()) == 0
+    batch_ms = float(np.median(ms))
+    # plain form: one scan per text, back to back on one stream
+    out1 = torch.empty((max(1, int(counts.max())) + 1024, 3), dtype=torch.int32, device=dev)
+    st1 = torch.zeros(2, dtype=torch.int64, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for aid, tt, n in jobs:
+        P.pfsm_scan_async(pf.ctx, aid, tt, n, out1, st1, stream=s)
+    e1.record(s)
+    s.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for a in ids:
+        P.pfsm_unload(pf.ctx, a)
+    return {"desc": "10,000 texts, log-uniform 100 B-1 MiB, 8 motif NFAs + 8 byte tries",
+            "bytes": total_bytes, "matches": int(total), "texts": len(jobs),
+            "batch_ms": batch_ms, "gbps": total_bytes / (batch_ms * 1e-3) / 1e9,
+            "plain_loop_ms": plain_ms, "plain_gbps": total_bytes / (plain_ms * 1e-3) / 1e9,
+            "speedup_vs_plain": plain_ms / batch_ms, "generate_s": gen_s}
+
+
+def serve_texts(w, seed=0):
+    """Request texts as slices of two seeded pools (DNA and bytes)."""
+    dna = W.text_dna(64 << 20, seed + 11)
+    byt = W.text_uniform(64 << 20, 256, seed + 12)
+    rng = np.random.default_rng(seed + 13)
+    texts = []
+    for i in range(len(w.lengths)):
+        n = int(w.lengths[i])
+        pool = dna if w.alphabet[int(w.req_aut[i])] == 4 else byt
+        o = int(rng.integers(0, len(pool) - n))
+        texts.append(pool[o:o + n])
+    return texts
+
+
+def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
+    """Continuous batching under Poisson arrivals at `load` x the burst
+    capacity, against the plain form (one synchronous scan per request)."""
+    from paper_1110_1716_gb300.serve import Server, replay
+    w = W.serve_workload(seed=0, n_req=n_req)
+    texts = serve_texts(w)
+    nbytes = int(sum(len(t) for t in texts))
+    res = {"desc": "Poisson arrivals, lognormal lengths (median 4 KiB, sigma 1.5, max 4 MiB), "
+                   "Zipf(1.1) over 64 machines of 64-16,384 states", "requests": n_req,
+           "bytes": nbytes}
+    with P.Pfsm(dev.index, budget_bytes=8 << 30) as pf:
+        srv = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
+                     max_jobs=1024)
+        # plain form: one request at a time through pfsm_scan
+        k = min(2000, n_req)
+        t0 = time.perf_counter()
+        for i in range(k):
+            pf.scan(srv.ids[int(w.req_aut[i])], texts[i], cap=max(1024, len(texts[i])))
+        plain_s = time.perf_counter() - t0
+        res["plain_req_per_s"] = k / plain_s
+        res["plain_gbps"] = sum(len(t) for t in texts[:k]) / plain_s / 1e9
+        # burst: every request at once, to find the served capacity
+        with srv:
+            t0 = time.perf_counter()
+            futs = [srv.submit(int(w.req_aut[i]), texts[i], arrival=t0) for i in range(n_req)]
+            for f in futs:
+                f.result()
+            burst_s = time.perf_counter() - t0
+        cap_rps = n_req / burst_s
+        res["burst_req_per_s"] = cap_rps
+        res["burst_gbps"] = nbytes / burst_s / 1e9
+        # Poisson arrivals at a fraction of that capacity
+        srv2 = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
+                      max_jobs=1024)
+        gaps = np.random.default_rng(1).exponential(1.0 / (load * cap_rps), size=n_req)
+        with srv2:
+            t0 = time.perf_counter()
+            futs = replay(srv2, np.cumsum(gaps), w.req_aut, texts, t0=t0)
+            m = sum(len(f.result()) for f in futs)
+            el = time.perf_counter() - t0
+        st = srv2.latency_stats()
+        res.update({"offered_load": load, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                    "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9,
+                    "matches_per_s": m / el, "batches": st["batches"],
+                    "evictions": st["residency_evictions"], "reloads": st["residency_reloads"]})
+    return res
 
 
 def run_reference(args):
@@ -340,6 +474,10 @@ def main():
     ap.add_argument("--params", default="", help="JSON pfsm_params overrides")
     ap.add_argument("--only", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", action="store_true", help="two scans of one workload (profiling)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--bytes", type=int, default=0, help="text length for --probe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -355,6 +493,9 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
+    if args.probe:
+        run_probe(args)
+        return
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")

@@ -75,7 +75,9 @@ typedef struct {
     int32_t prefix_k;   /* depth of the start-prefix table: the first k steps of
                            every instance are looked up once per k-gram;
                            -1 = off (every instance steps from q0) */
-    int32_t tile;       /* starts owned by one CTA tile (multiple of 4096) */
+    int32_t tile;       /* starts owned by one CTA tile (multiple of 4096, at
+                           most 49152; 0 = automatic: 16384, smaller for short
+                           texts) */
     int32_t halo;       /* text staged past the tile end (multiple of 16) */
     int32_t threads;    /* threads per CTA: 128, 256 or 512 */
     int32_t spt;        /* starts per thread per filter round: 8 */

@@ -33,6 +33,8 @@ struct BatchState {
     unsigned long long *status = nullptr;       // device: total, errors, per-job counts
     unsigned long long *host_status = nullptr;  // pinned copy of status
     uint32_t *carry = nullptr;
+    uint32_t *coop = nullptr;         // warp-wide NFA bitsets
+    size_t coop_words = 0;
     cudaEvent_t staged = nullptr;     // previous staging copy has been consumed
     bool staged_pending = false;
     cudaGraphExec_t exec = nullptr;
@@ -47,6 +49,7 @@ static void state_free(BatchState *b) {
     if (b->capture) cudaStreamDestroy(b->capture);
     cudaFree(b->dev);
     cudaFree(b->ctr);
+    cudaFree(b->coop);
     cudaFreeHost(b->host);
     cudaFreeHost(b->host_status);
     delete b;
@@ -138,7 +141,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
         int st = make_resident(ctx, id, ctx->machines[id]);
         if (st) return st;
     }
-    uint32_t memo_max = 0, tab_max = 0, band_max = 0, pool_max = 0;
+    uint32_t memo_max = 0, tab_max = 0, band_max = 0, pool_max = 0, surv_max = 0;
     int32_t wq_max = 0;
     int kmask = 0;
     for (int id : ids) {
@@ -147,13 +150,14 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
         const uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
         d.tab_smem = (m.kind == 0 && tab_bytes <= kBatchTabMax) ? 1 : 0;
         if (d.tab_smem) tab_max = std::max(tab_max, tab_bytes);
-        const uint32_t band_bytes = static_cast<uint32_t>(m.band.size() * 8);
+        const uint32_t band_bytes = static_cast<uint32_t>(m.band.size() * 4);
         const uint32_t pool_bytes = m.kind == 1 ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
         d.band_smem = band_bytes > 0 && band_bytes <= kBatchTabMax * 2;
         d.pool_smem = pool_bytes > 0 && pool_bytes <= kBatchTabMax * 2;
         if (d.band_smem) band_max = std::max(band_max, band_bytes);
         if (d.pool_smem) pool_max = std::max(pool_max, pool_bytes);
         memo_max = std::max(memo_max, d.memo_n);
+        surv_max = std::max(surv_max, static_cast<uint32_t>(m.surv.size() * 4));
         if (m.kind == 1) wq_max = std::max(wq_max, d.Wq);
         kmask |= m.kind == 0 ? 1 : 2;
         pl.machs.push_back(d);
@@ -174,18 +178,19 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     int threads = 256;
     uint32_t smem = 0;
     bool fit = false;
-    for (int attempt = 0; attempt < 10 && !fit; ++attempt) {
+    a.qcap = 2 * 8u * threads;
+    for (int attempt = 0; attempt < 12 && !fit; ++attempt) {
         a.tile = tile;
         a.halo = kBatchHalo;
         a.text_buf = (tile + kBatchHalo + 16 + 127) & ~127u;
-        const SmemNeed need{tab_max, band_max, pool_max};
-        a.qcap = 2 * 8u * threads;
+        const SmemNeed need{tab_max, band_max, pool_max, surv_max};
         smem = layout_smem(a, kmask, threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        a.qcap = 8u * threads;
-        smem = layout_smem(a, kmask, threads, need);
-        if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        if (pool_max) {
+        if (a.stage_n > 32) {
+            a.stage_n = 32;
+        } else if (a.qcap > 8u * threads) {
+            a.qcap = 8u * threads;
+        } else if (pool_max) {
             pool_max = 0;
             for (auto &d : pl.machs) d.pool_smem = 0;
         } else if (tile > 8192) {
@@ -198,6 +203,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
             for (auto &d : pl.machs) d.tab_smem = 0;
         } else if (threads > 128) {
             threads /= 2;
+            a.qcap = 2 * 8u * threads;
         } else {
             break;
         }
@@ -286,6 +292,11 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
     args.jobs = reinterpret_cast<const BatchJob *>(b->dev + b->off_jobs);
     args.machs = reinterpret_cast<const DevMachine *>(b->dev + b->off_machs);
     args.job_counts = b->status + 2;
+    if (pl.sa.Wq > 0) {
+        const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * pl.sa.Wq;
+        if (ensure_words(&b->coop, &b->coop_words, need)) return PFSM_E_NOMEM;
+        args.sa.coop_g = b->coop;
+    }
     memcpy(b->host, &args, sizeof(args));
     if (!pl.jobs.empty())
         memcpy(b->host + b->off_jobs, pl.jobs.data(), pl.jobs.size() * sizeof(BatchJob));

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -163,16 +164,100 @@ bool build_memo(Machine &m) {
     return build_memo_nfa(m);
 }
 
+// ---- survival bitmap ----------------------------------------------------
+// One bit per m-gram w (index sum_j w[j] << (j * sbits)): set when an instance
+// started at q0 either reaches a final state within the m symbols of w or
+// still holds a state after them. A clear bit proves that a start whose next
+// m symbols are w reports nothing, so the filter drops it with one bit test.
+// Kept only when it clears at least half of the m-grams.
+void build_survival(Machine &m) {
+    m.surv.clear();
+    m.sm_m = 0;
+    int mm = std::min(9, 18 / m.sbits);
+    if (mm < 1) return;
+    const uint32_t nbits = 1u << (mm * m.sbits);
+    std::vector<uint32_t> bits((nbits + 31) / 32, 0);
+    const uint32_t smask = (1u << m.sbits) - 1;
+    uint64_t ones = 0;
+    if (m.kind == 0) {
+        for (uint32_t w = 0; w < nbits; ++w) {
+            int s = m.q0;
+            bool live = true, hit = false;
+            for (int j = 0; j < mm; ++j) {
+                const int a = (w >> (j * m.sbits)) & smask;
+                if (a >= m.S) { live = false; break; }
+                const uint16_t e = m.dtab[(size_t)s * m.S + a];
+                if (e == DEAD16) { live = false; break; }
+                s = e & 0x7FFF;
+                if (e & FINAL_BIT) { hit = true; break; }
+            }
+            if (live || hit) {
+                bits[w >> 5] |= 1u << (w & 31);
+                ++ones;
+            }
+        }
+    } else {
+        std::vector<uint32_t> mark(m.Q, 0);
+        uint32_t stamp = 0;
+        // depth-first over m-grams; a subtree is settled as soon as its set
+        // empties (all clear) or a final state is met (all set)
+        struct Frame { std::vector<uint16_t> set; };
+        std::vector<Frame> lv(mm + 1);
+        std::function<void(int, uint32_t)> dfs = [&](int depth, uint32_t prefix) {
+            const std::vector<uint16_t> &S = lv[depth].set;
+            if (depth == mm) {
+                if (!S.empty()) { bits[prefix >> 5] |= 1u << (prefix & 31); ++ones; }
+                return;
+            }
+            if (S.empty()) return;
+            for (int a = 0; a < (1 << m.sbits); ++a) {
+                if (a >= m.S) continue;
+                std::vector<uint16_t> &N = lv[depth + 1].set;
+                N.clear();
+                bool hit = false;
+                ++stamp;
+                for (uint16_t q : S) {
+                    const uint32_t lo = m.off[(size_t)q * m.S + a], hi = m.off[(size_t)q * m.S + a + 1];
+                    for (uint32_t e = lo; e < hi; ++e) {
+                        const uint16_t t = m.tgt[e];
+                        const uint16_t ts = t & 0x7FFF;
+                        if (t & FINAL_BIT) hit = true;
+                        if (mark[ts] == stamp) continue;
+                        mark[ts] = stamp;
+                        N.push_back(ts);
+                    }
+                }
+                const uint32_t p = prefix | (static_cast<uint32_t>(a) << (depth * m.sbits));
+                if (hit) {
+                    const uint32_t rest = static_cast<uint32_t>(mm - depth - 1) * m.sbits;
+                    for (uint32_t hw = 0; hw < (1u << rest); ++hw) {
+                        const uint32_t w = p | (hw << ((depth + 1) * m.sbits));
+                        bits[w >> 5] |= 1u << (w & 31);
+                        ++ones;
+                    }
+                    continue;
+                }
+                dfs(depth + 1, p);
+            }
+        };
+        lv[0].set = {static_cast<uint16_t>(m.q0)};
+        dfs(0, 0);
+    }
+    if (ones * 2 > nbits) return;   // does not prune enough to pay for itself
+    m.surv = std::move(bits);
+    m.sm_m = mm;
+}
+
 // ---- residency --------------------------------------------------------------
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t device_bytes(const Machine &m) {
-    size_t b = align256(m.memo.size() * 2 + 4);
+    size_t b = align256(m.memo.size() * 2 + 4) + align256(m.surv.size() * 4 + 4);
     if (m.kind == 0) {
         b += align256(m.dtab.size() * 2 + 4);
     } else {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
-             align256(m.pool.size() * 4) + align256(m.band.size() * 8);
+             align256(m.pool.size() * 4) + align256(m.band.size() * 4);
     }
     return b;
 }
@@ -232,6 +317,10 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
     uint8_t *base = static_cast<uint8_t *>(p);
     const size_t o_memo = put(m.memo.data(), m.memo.size() * 2);
     dm.memo = reinterpret_cast<const uint16_t *>(base + o_memo);
+    const size_t o_surv = put(m.surv.data(), m.surv.size() * 4);
+    dm.surv = m.surv.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv);
+    dm.surv_m = m.sm_m;
+    dm.surv_words = static_cast<uint32_t>(m.surv.size());
     if (m.kind == 0) {
         const size_t o_tab = put(m.dtab.data(), m.dtab.size() * 2);
         dm.dtab = reinterpret_cast<const uint16_t *>(base + o_tab);
@@ -245,14 +334,13 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
         memcpy(img.data() + o, m.pool.data(), m.pool.size() * 4);
         o += align256(m.pool.size() * 4);
         const size_t o_band = o;
-        if (!m.band.empty()) memcpy(img.data() + o, m.band.data(), m.band.size() * 8);
-        o += align256(m.band.size() * 8);
+        if (!m.band.empty()) memcpy(img.data() + o, m.band.data(), m.band.size() * 4);
+        o += align256(m.band.size() * 4);
         dm.off = reinterpret_cast<const uint32_t *>(base + o_off);
         dm.tgt = reinterpret_cast<const uint16_t *>(base + o_tgt);
         dm.pool = reinterpret_cast<const uint32_t *>(base + o_pool);
         dm.pool_n = static_cast<uint32_t>(m.pool.size());
-        dm.band = m.band.empty() ? nullptr
-                                 : reinterpret_cast<const unsigned long long *>(base + o_band);
+        dm.band = m.band.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_band);
     }
     if (o > bytes) {   // layout and size disagree: a bug, fail loudly
         cudaFree(p);
@@ -268,6 +356,26 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
     ctx->resident_bytes += bytes;
     if (m.was_resident) ctx->n_reload++;
     m.was_resident = true;
+    return PFSM_OK;
+}
+
+// Grows a device scratch buffer to at least `need` words (synchronises the
+// device when it has to reallocate, which happens once per size class).
+int ensure_words(uint32_t **buf, size_t *have, size_t need) {
+    if (need <= *have) return PFSM_OK;
+    size_t n = std::max(need, 2 * *have);
+    if (*buf) {
+        cudaDeviceSynchronize();
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    if (cudaMalloc(buf, n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return PFSM_E_NOMEM;
+    }
+    *have = n;
     return PFSM_OK;
 }
 
@@ -296,7 +404,7 @@ Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s) {
 
 void fill_defaults(const Machine &m, pfsm_params &p) {
     if (p.prefix_k == 0) p.prefix_k = default_k(m);
-    if (p.tile == 0) p.tile = 16384;
+    // tile 0 = automatic: 16 KiB, smaller for texts too short to fill the GPU
     if (p.halo == 0) p.halo = 2048;
     if (p.threads == 0) p.threads = 512;
     if (p.spt == 0) p.spt = 8;
@@ -306,7 +414,7 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
 int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.prefix_k < -1 || p.prefix_k > 8) return PFSM_E_INVAL;
     if (p.prefix_k > 0 && p.prefix_k * m.sbits > 16) return PFSM_E_INVAL;
-    if (p.tile < 4096 || p.tile > 49152 || p.tile % 4096) return PFSM_E_INVAL;
+    if (p.tile != 0 && (p.tile < 4096 || p.tile > 49152 || p.tile % 4096)) return PFSM_E_INVAL;
     if (p.halo < 16 || p.halo > 16384 || p.halo % 16) return PFSM_E_INVAL;
     if (p.threads != 128 && p.threads != 256 && p.threads != 512) return PFSM_E_INVAL;
     if (p.spt != 8) return PFSM_E_INVAL;
@@ -340,10 +448,16 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     memset(&a, 0, sizeof(a));
     a.text = text;
     a.n = static_cast<uint32_t>(n);
-    a.tile = p.tile;
+    uint32_t tile = static_cast<uint32_t>(p.tile);
+    if (tile == 0) {
+        // at least two tiles per SM when the text allows it
+        const uint64_t want = n / (2ull * ctx->nsm);
+        tile = static_cast<uint32_t>(std::min<uint64_t>(16384, std::max<uint64_t>(4096, (want + 4095) & ~4095ull)));
+    }
+    a.tile = tile;
     a.halo = p.halo;
-    a.ntiles = static_cast<uint32_t>((n + p.tile - 1) / p.tile);
-    a.text_buf = (p.tile + p.halo + 16 + 127) & ~127u;
+    a.ntiles = static_cast<uint32_t>((n + tile - 1) / tile);
+    a.text_buf = (tile + p.halo + 16 + 127) & ~127u;
     a.aligned = (reinterpret_cast<uintptr_t>(text) & 15) == 0;
     a.Q = m.Q;
     a.S = m.S;
@@ -358,6 +472,9 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.pool = m.dm.pool;
     a.pool_n = m.dm.pool_n;
     a.band = m.dm.band;
+    a.surv = m.dm.surv;
+    a.surv_m = m.dm.surv_m;
+    a.surv_words = m.dm.surv_words;
     a.Wq = m.kind == 1 ? m.dm.Wq : 0;
     const uint32_t round = 8u * p.threads;
     uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
@@ -371,20 +488,21 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.stage_n = m.kind == 0 ? STAGE : 32;
     SmemNeed need{};
     need.tab_bytes = a.tab_smem ? tab_bytes : 0;
-    need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 8) : 0;
+    need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 4) : 0;
     need.pool_bytes = (m.kind == 1 && m.pool.size() * 4 <= 64 * 1024)
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
+    need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
     uint32_t smem = 0;
     bool fit = false;
-    for (int attempt = 0; attempt < 6 && !fit; ++attempt) {
-        a.qcap = 2 * round;
+    a.qcap = 2 * round;
+    for (int attempt = 0; attempt < 8 && !fit; ++attempt) {
         smem = layout_smem(a, kmask, p.threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        a.qcap = round;
-        smem = layout_smem(a, kmask, p.threads, need);
-        if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        // give up shared-memory copies, largest first
-        if (need.pool_bytes) need.pool_bytes = 0;
+        // shrink, cheapest loss first: match staging, queue depth, then
+        // table copies (largest first)
+        if (a.stage_n > 32) a.stage_n = 32;
+        else if (a.qcap > round) a.qcap = round;
+        else if (need.pool_bytes) need.pool_bytes = 0;
         else if (need.band_bytes) need.band_bytes = 0;
         else if (need.tab_bytes && p.table_smem == -1) { need.tab_bytes = 0; a.tab_smem = 0; }
         else break;
@@ -434,6 +552,11 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     pl.a.carry = slot->carry;
     pl.a.carry_n = slot->carry_n;
     pl.a.carry_cap = kCarryCap;
+    if (m.kind == 1) {
+        const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * m.dm.Wq;
+        if (ensure_words(&slot->coop, &slot->coop_words, need)) return PFSM_E_NOMEM;
+        pl.a.coop_g = slot->coop;
+    }
     if (m.kind == 0 && cudaMemsetAsync(slot->carry_n, 0, sizeof(uint32_t), s) != cudaSuccess)
         return PFSM_E_CUDA;
     int ev = -1;
@@ -498,6 +621,7 @@ int pfsm_ctx_destroy(pfsm_ctx *ctx) {
     cudaDeviceSynchronize();
     for (auto &kv : ctx->machines) release(ctx, kv.second);
     for (auto &kv : ctx->slots) {
+        cudaFree(kv.second.coop);
         cudaFree(kv.second.status);
         cudaFreeHost(kv.second.host_status);
         for (int i = 0; i < 2 * kEventRing; ++i) cudaEventDestroy(kv.second.ev[i]);
@@ -520,6 +644,7 @@ static int finish_load(pfsm_ctx *ctx, Machine &&m, pfsm_aut *out_id) {
         }
     }
     m.params.prefix_k = m.k > 0 ? m.k : -1;
+    build_survival(m);
     DeviceGuard g(ctx->device);
     const int id = ctx->next_id++;
     auto &slot = ctx->machines[id];
@@ -598,9 +723,9 @@ int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t 
     // band rows: delta(q, a) inside q+1..q+8 for every symbol (alphabets of
     // at most 4 symbols), with the finality of each target beside it
     if (S <= 4) {
-        m.band.assign(Q, 0ull);
+        m.band.assign(static_cast<size_t>(Q) + W, 0u);
         for (int q = 0; q < Q; ++q) {
-            unsigned long long row = 0;
+            uint32_t row = 0;
             bool fits = true;
             for (int a = 0; a < S && fits; ++a) {
                 for (uint32_t x = m.off[(size_t)q * S + a]; x < m.off[(size_t)q * S + a + 1]; ++x) {
@@ -610,12 +735,13 @@ int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t 
                         fits = false;
                         break;
                     }
-                    row |= 1ull << (8 * a + d);
-                    if (is_final[t]) row |= 1ull << (32 + 8 * a + d);
+                    row |= 1u << (8 * a + d);
                 }
             }
             m.band[q] = (fits && row != BAND_CSR) ? row : BAND_CSR;
         }
+        for (int q = 0; q < Q; ++q)
+            if (is_final[q]) m.band[Q + (q >> 5)] |= 1u << (q & 31);
     }
     if (m.tgt.empty()) m.tgt.push_back(0);
     return finish_load(ctx, std::move(m), out_id);

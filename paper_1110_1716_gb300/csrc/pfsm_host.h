@@ -29,7 +29,10 @@ struct Machine {
     int k = 0, sbits = 1;
     std::vector<uint16_t> memo;
     std::vector<uint32_t> pool;
-    std::vector<unsigned long long> band;   // NFA band rows (S <= 4) or empty
+    std::vector<uint32_t> band;   // NFA band image (S <= 4) or empty
+    // survival bitmap over m-grams (m = 0: none)
+    int sm_m = 0;
+    std::vector<uint32_t> surv;
     pfsm_params params{};
     // residency
     void *dev = nullptr;
@@ -45,6 +48,8 @@ struct Slot {   // per-stream scratch
     uint32_t *carry_n = nullptr;
     uint32_t *carry = nullptr;              // kCarryCap entries of 4 words
     unsigned long long *host_status = nullptr;   // pinned [2]
+    uint32_t *coop = nullptr;               // warp-wide NFA bitsets
+    size_t coop_words = 0;
     // ring of (start, end) events around timed tile-kernel launches
     cudaEvent_t ev[2 * kEventRing] = {};
     int ev_head = 0, ev_pending = 0;
@@ -90,10 +95,12 @@ namespace pfsm {
 
 int ceil_log2(int S);
 bool build_memo(Machine &m);
+void build_survival(Machine &m);
 size_t align256(size_t x);
 void release(pfsm_ctx *ctx, Machine &m);
 int make_resident(pfsm_ctx *ctx, int id, Machine &m);
 Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s);
+int ensure_words(uint32_t **buf, size_t *have, size_t need);
 void collect_timing(pfsm_ctx *ctx, Slot *slot, int keep);
 int finish_status(const unsigned long long *hs, uint64_t cap, uint64_t *n_matches);
 void batch_free(pfsm_ctx *ctx);

@@ -30,12 +30,16 @@ constexpr uint16_t FINAL_BIT = 0x8000;
 constexpr uint16_t PT_SKIP = 0xFFFF;
 constexpr uint16_t PT_WALK = 0xFFFE;
 
-// NFA band rows (alphabets of at most 4 symbols): one uint64 per state q.
-// Byte a (a < 4) is the mask of delta(q, a) within q+1..q+8 (bit d set iff
-// q+1+d is a target); byte 4+a marks which of those targets are final.
-// BAND_CSR marks a state with a target outside that window: its rows are
-// read from the CSR arrays instead.
-constexpr unsigned long long BAND_CSR = ~0ull;
+// NFA band image (alphabets of at most 4 symbols): Q uint32 rows followed by
+// a final-state bitmap of ceil(Q/32) words. Byte a of row q is the mask of
+// delta(q, a) within q+1..q+8 (bit d set iff q+1+d is a target). BAND_CSR
+// marks a state with a target outside that window: its rows are read from
+// the CSR arrays instead.
+constexpr uint32_t BAND_CSR = 0xFFFFFFFFu;
+
+// Survival bitmap (optional): one bit per m-gram, set when an instance
+// started at q0 meets a final state within those m symbols or still holds a
+// state after them; a clear bit settles the start without a lookup.
 
 // Work-queue entry of the filter phase (uint32): start offset inside the
 // tile in bits 0..15, info in bits 16..31 (a prefix-table entry, or PT_WALK
@@ -48,7 +52,7 @@ constexpr unsigned long long ERR_TIMEOUT = 2ull;
 
 constexpr int NFA_SLOT = 8;       // states one lane holds for a small NFA set
 constexpr int STAGE = 128;        // largest per-warp match staging (entries)
-constexpr int NFA_INLINE = 4;     // states a filtering thread advances in registers
+constexpr int NFA_INLINE = 8;     // states a filtering thread advances in registers
 constexpr int INLINE_STEPS = 24;  // symbols it advances them before handing over
 
 struct ScanArgs {
@@ -68,12 +72,16 @@ struct ScanArgs {
     const uint32_t *off;    // NFA: [Q*S + 1] CSR offsets
     const uint16_t *tgt;    // NFA: targets
     const uint32_t *pool;   // NFA: prefix records
-    const unsigned long long *band;   // NFA: band rows [Q] or null
+    const uint32_t *band;   // NFA: band image (rows, then final bitmap) or null
     uint32_t pool_n;        // NFA: words of pool
     int32_t pool_smem;      // NFA: pool staged to smem
     int32_t band_smem;      // NFA: band rows staged to smem
+    const uint32_t *surv;   // survival bitmap over m-grams, or null
+    int32_t surv_m;         // m (0: no bitmap)
+    uint32_t surv_words;
     int32_t Wq;             // NFA: 32-bit words of a state bitset
     int32_t tab_smem;       // DFA table staged to smem
+    uint32_t *coop_g;       // NFA: global scratch for warp-wide state bitsets
     // output
     uint32_t *out;          // pfsm_match[cap] as words, or pfsm_bmatch
     uint64_t cap;
@@ -84,7 +92,7 @@ struct ScanArgs {
     uint32_t carry_cap;
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
-    uint32_t sm_band, sm_pool;
+    uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t qcap;
     uint32_t stage_n;       // staged matches per warp before a flush
 };
@@ -112,9 +120,12 @@ struct DevMachine {
     const uint32_t *off;
     const uint16_t *tgt;
     const uint32_t *pool;
-    const unsigned long long *band;
+    const uint32_t *band;
     uint32_t pool_n;
-    int32_t pad2;
+    int32_t surv_m;
+    const uint32_t *surv;
+    uint32_t surv_words;
+    int32_t pad3;
 };
 static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
 
@@ -134,8 +145,9 @@ struct BatchArgs {
 // for `threads` threads and the table copies in `need`; returns total bytes.
 struct SmemNeed {
     uint32_t tab_bytes;    // DFA table copy (0 = read from global)
-    uint32_t band_bytes;   // NFA band rows copy (0 = read from global)
+    uint32_t band_bytes;   // NFA band image copy (0 = read from global)
     uint32_t pool_bytes;   // NFA prefix records copy (0 = read from global)
+    uint32_t surv_bytes;   // survival bitmap (always in shared memory when used)
 };
 uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &need);
 cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,

@@ -157,10 +157,25 @@ __device__ __forceinline__ uint32_t memo_index(uint64_t lo, uint64_t hi, uint32_
     }
 }
 
+// Prefix-table index of the start at offset `off` of the staged tile (k
+// symbols read from three aligned words; k <= 8).
+template <int SB>
+__device__ __forceinline__ uint32_t kgram_at(const uint8_t *tsm, uint32_t off, int k, int sbits,
+                                             uint32_t mask) {
+    const uint32_t a4 = off & ~3u, r = off & 3u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t *>(tsm + a4);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t *>(tsm + a4 + 4);
+    const uint32_t w2 = *reinterpret_cast<const uint32_t *>(tsm + a4 + 8);
+    const uint64_t lo = w0 | (static_cast<uint64_t>(w1) << 32);
+    const uint64_t hi = w2;
+    const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+    return memo_index<SB>(lo, hi, p2, static_cast<int>(r), k, sbits, mask);
+}
+
 // ------------------------------------------------------------ views
 // The machine one tile runs (registers).
 struct MView {
-    int32_t Q, S, q0, k, sbits, Wq;
+    int32_t Q, S, q0, k, sbits, Wq, surv_m;
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;
@@ -192,8 +207,10 @@ struct Smem {
     Misc *misc;
     const uint16_t *memo;
     const uint16_t *tab;
-    const unsigned long long *band;   // NFA band rows (shared copy, global, or null)
+    const uint32_t *band;             // NFA band image (shared copy, global, or null)
     const uint32_t *pool;             // NFA prefix records (shared copy or global)
+    const uint32_t *surv;             // survival bitmap (shared copy) or null
+    uint16_t *list;                   // this warp's list of surviving starts
     uint32_t *queue;
     uint32_t *stage;   // this warp's staging buffer
     uint16_t *slots;   // this warp's NFA slots
@@ -341,17 +358,17 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
 // Visits delta(q, c) as (state | FINAL_BIT) values: from the band row of q
 // when it has one, otherwise from the CSR arrays.
 template <class F>
-__device__ __forceinline__ void nfa_targets(const MView &mv, const unsigned long long *band,
-                                            uint32_t q, uint32_t c, uint64_t pol_keep, F &&f) {
+__device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *band, uint32_t q,
+                                            uint32_t c, uint64_t pol_keep, F &&f) {
     if (band) {
-        const unsigned long long row = band[q];
+        const uint32_t row = band[q];
         if (row != BAND_CSR) {
-            uint32_t m = static_cast<uint32_t>(row >> (8 * c)) & 0xFFu;
-            const uint32_t fm = static_cast<uint32_t>(row >> (32 + 8 * c)) & 0xFFu;
+            const uint32_t *fin = band + mv.Q;
+            uint32_t m = (row >> (8 * c)) & 0xFFu;
             while (m) {
-                const uint32_t d = __ffs(m) - 1;
+                const uint32_t t = q + __ffs(m);
                 m &= m - 1;
-                f((q + 1 + d) | (((fm >> d) & 1u) << 15));
+                f(t | (((fin[t >> 5] >> (t & 31)) & 1u) << 15));
             }
             return;
         }
@@ -377,6 +394,7 @@ __device__ __forceinline__ bool nfa_settle(const MView &mv, const Smem &sm, cons
     uint32_t cnt = ns;
     uint32_t pos = start + mv.k;
     const uint32_t tile_end = tv.b + tv.len;
+    const uint32_t *fin = sm.band + mv.Q;
     for (int step = 0; step < INLINE_STEPS; ++step) {
         if (cnt == 0 || pos >= tv.n) return true;
         if (pos >= tile_end) return false;
@@ -389,13 +407,13 @@ __device__ __forceinline__ bool nfa_settle(const MView &mv, const Smem &sm, cons
 #pragma unroll
         for (int i = 0; i < NFA_INLINE; ++i) {
             if (static_cast<uint32_t>(i) < cnt) {
-                const unsigned long long row = sm.band[s[i]];
+                const uint32_t row = sm.band[s[i]];
                 if (row == BAND_CSR) return false;
-                uint32_t m = static_cast<uint32_t>(row >> (8 * c)) & 0xFFu;
-                if (m & static_cast<uint32_t>(row >> (32 + 8 * c))) return false;
+                uint32_t m = (row >> (8 * c)) & 0xFFu;
                 while (m) {
                     const uint32_t tt = s[i] + __ffs(m);
                     m &= m - 1;
+                    if ((fin[tt >> 5] >> (tt & 31)) & 1u) return false;
                     bool dup = false;
 #pragma unroll
                     for (int j = 0; j < NFA_INLINE; ++j) dup |= (static_cast<uint32_t>(j) < tc) && t[j] == tt;
@@ -422,7 +440,7 @@ __device__ __forceinline__ bool nfa_settle(const MView &mv, const Smem &sm, cons
 // partitioning: reads the global text once past the staged bytes).
 template <int OUTW>
 __device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
-                                      const unsigned long long *band, const TileView &tv,
+                                      const uint32_t *band, const TileView &tv,
                                       uint32_t *bits0, uint32_t *bits1, uint32_t start,
                                       uint32_t pos, int lane, uint64_t pol_keep) {
     const uint32_t Wq = mv.Wq, S = mv.S, n = tv.n;
@@ -643,6 +661,9 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
     const uint32_t kbits = static_cast<uint32_t>(mv.k * mv.sbits);
     const uint32_t mask = kbits >= 32 ? 0xFFFFFFFFu : ((1u << kbits) - 1);
     const uint32_t round = SPT * NT;
+    const uint32_t mm = static_cast<uint32_t>(mv.surv_m);
+    const uint32_t mbits = mm * static_cast<uint32_t>(mv.sbits);
+    const uint32_t mmask = mbits >= 32 ? 0xFFFFFFFFu : ((1u << mbits) - 1);
     for (uint32_t r0 = b; r0 < own_end; r0 += round) {
         if (sm.misc->q_count + round > qcap) {
             drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
@@ -653,92 +674,73 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             }
             __syncthreads();
         }
+        // 1. this thread's SPT starts: symbol check and survival-bitmap test
         const uint32_t i0 = r0 + SPT * tid;
-        uint32_t pm = 0;
-        uint32_t ent[SPT];
-#pragma unroll
-        for (int r = 0; r < SPT; ++r) ent[r] = 0;
-        if (KIND == 1) {
-            // NFA: settle small sets in registers; queue the rest directly
-            if (i0 < own_end) {
-                const uint8_t *tp = tv.sm + (i0 - b);
-                const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-                const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-                const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-                const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
-                const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
-                if (mv.S < 256) {
-                    uint64_t badm = bytes_ge(lo, mv.S);
-                    if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
-                    if (badm) bad_symbol = true;
-                }
-                const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
-#pragma unroll 1
-                for (uint32_t r = 0; r < nown; ++r) {
-                    const uint32_t i = i0 + r;
-                    uint32_t e;
-                    if (kk == 0 || i + kk > n) {
-                        e = PT_WALK;
-                    } else {
-                        e = sm.memo[memo_index<SB>(lo, hi, p2, r, mv.k, mv.sbits, mask)];
-                        if (e == PT_SKIP) continue;
-                        if (sm.band && nfa_settle(mv, sm, tv, i, e)) continue;
-                    }
-                    const uint32_t p = atomicAdd(&sm.misc->q_count, 1u);
-                    sm.queue[p] = (i - b) | (e << 16);
-                }
+        uint32_t live = 0;
+        if (i0 < own_end) {
+            const uint8_t *tp = tv.sm + (i0 - b);
+            const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+            const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+            const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+            const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+            const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
+            if (mv.S < 256) {
+                uint64_t badm = bytes_ge(lo, mv.S);
+                if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
+                if (badm) bad_symbol = true;
             }
-        } else {
-            if (i0 < own_end) {
-                const uint8_t *tp = tv.sm + (i0 - b);
-                const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-                const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-                const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-                const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
-                const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
-                if (mv.S < 256) {
-                    uint64_t badm = bytes_ge(lo, mv.S);
-                    if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
-                    if (badm) bad_symbol = true;
-                }
+            live = (1u << nown) - 1;
+            if (sm.surv) {
                 const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
-    #pragma unroll
+#pragma unroll
                 for (int r = 0; r < SPT; ++r) {
-                    if (static_cast<uint32_t>(r) < nown) {
-                        const uint32_t i = i0 + r;
-                        if (kk == 0 || i + kk > n) {
-                            ent[r] = PT_WALK;
-                            pm |= 1u << r;
-                        } else {
-                            const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mv.k, mv.sbits, mask);
-                            const uint16_t e = sm.memo[idx];
-                            if (e != PT_SKIP) {
-                                ent[r] = e;
-                                pm |= 1u << r;
-                            }
-                        }
+                    if (static_cast<uint32_t>(r) < nown && i0 + r + mm <= n) {
+                        const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
+                        if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << r);
                     }
                 }
             }
         }
-        // warp-aggregated append to the CTA work queue
-        const uint32_t c = __popc(pm);
-        if (KIND == 0 && __ballot_sync(FULLMASK, c != 0)) {
-            uint32_t incl = c;
+        // 2. compact the surviving starts into this warp's list
+        const uint32_t c = __popc(live);
+        uint32_t incl = c;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
-                if (lane >= d) incl += v;
-            }
-            const uint32_t wtot = __shfl_sync(FULLMASK, incl, 31);
-            uint32_t wbase = 0;
-            if (lane == 31) wbase = atomicAdd(&sm.misc->q_count, wtot);
-            wbase = __shfl_sync(FULLMASK, wbase, 31);
-            uint32_t p = wbase + incl - c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
+        {
+            uint32_t p = incl - c;
 #pragma unroll
             for (int r = 0; r < SPT; ++r)
-                if (pm >> r & 1u) sm.queue[p++] = (i0 + r - b) | (ent[r] << 16);
+                if (live >> r & 1u) sm.list[p++] = static_cast<uint16_t>(i0 + r - b);
         }
+        __syncwarp();
+        // 3. every lane takes list entries: prefix table, settling, queue
+        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool push = false;
+            uint32_t qe = 0;
+            if (j < total) {
+                const uint32_t off = sm.list[j];
+                const uint32_t i = b + off;
+                uint32_t e = PT_WALK;
+                if (kk != 0 && i + kk <= n) e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                push = e != PT_SKIP;
+                if (KIND == 1 && push && e != PT_WALK && sm.band && nfa_settle(mv, sm, tv, i, e))
+                    push = false;
+                qe = off | (e << 16);
+            }
+            const uint32_t pmask = __ballot_sync(FULLMASK, push);
+            if (pmask) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&sm.misc->q_count, __popc(pmask));
+                base = __shfl_sync(FULLMASK, base, 0);
+                if (push) sm.queue[base + __popc(pmask & lanemask_lt())] = qe;
+            }
+        }
+        __syncwarp();
         __syncthreads();
     }
     drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
@@ -758,8 +760,11 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
     s.queue = reinterpret_cast<uint32_t *>(base + a.sm_queue);
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
     s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
-    s.coop = reinterpret_cast<uint32_t *>(base + a.sm_coop) + wid * (2 * a.Wq);
-    s.band = a.band_smem ? reinterpret_cast<const unsigned long long *>(base + a.sm_band) : a.band;
+    s.coop = a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
+                      : nullptr;
+    s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
+    s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;
+    s.list = reinterpret_cast<uint16_t *>(base + a.sm_list) + wid * (8 * 32);
     s.pool = a.pool_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_pool) : a.pool;
     return s;
 }
@@ -775,12 +780,13 @@ __device__ __forceinline__ void stage_u16(uint16_t *dst, const uint16_t *src, ui
 // Copies an NFA's band rows and prefix records into shared memory (either
 // source may be null: that table is then read from global memory).
 __device__ __forceinline__ void stage_nfa(uint8_t *base, uint32_t sm_band, uint32_t sm_pool,
-                                          const unsigned long long *band, int32_t Q,
+                                          const uint32_t *band, int32_t Q,
                                           const uint32_t *pool, uint32_t pool_n, int tid,
                                           int nt) {
     if (band) {
-        unsigned long long *d = reinterpret_cast<unsigned long long *>(base + sm_band);
-        for (int32_t i = tid; i < Q; i += nt) d[i] = __ldg(band + i);
+        uint32_t *d = reinterpret_cast<uint32_t *>(base + sm_band);
+        const int32_t words = Q + (Q + 31) / 32;
+        for (int32_t i = tid; i < words; i += nt) d[i] = __ldg(band + i);
     }
     if (pool) {
         uint32_t *d = reinterpret_cast<uint32_t *>(base + sm_pool);
@@ -800,12 +806,16 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
-    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.dtab, a.off, a.tgt};
+    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.dtab, a.off, a.tgt};
 
     stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
     if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
     if (KIND == 1) stage_nfa(smem, a.sm_band, a.sm_pool, a.band_smem ? a.band : nullptr, a.Q,
                              a.pool_smem ? a.pool : nullptr, a.pool_n, tid, NT);
+    if (a.surv) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(smem + a.sm_surv);
+        for (uint32_t i = tid; i < a.surv_words; i += NT) d[i] = __ldg(a.surv + i);
+    }
     if (tid == 0) {
         mbar_init(&misc->bar[0], 1);
         mbar_init(&misc->bar[1], 1);
@@ -883,7 +893,7 @@ __device__ __forceinline__ uint32_t find_job(const BatchJob *jobs, uint32_t njob
 }
 
 __device__ __forceinline__ MView mview_of(const DevMachine &m) {
-    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.dtab, m.off, m.tgt};
+    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.dtab, m.off, m.tgt};
 }
 
 __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict__ gargs) {
@@ -957,11 +967,15 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
             if (M.kind == 1)
                 stage_nfa(smem, A.sa.sm_band, A.sa.sm_pool, M.band_smem ? M.band : nullptr, M.Q,
                           M.pool_smem ? M.pool : nullptr, M.pool_n, tid, NT);
+            if (M.surv) {
+                uint32_t *dst = reinterpret_cast<uint32_t *>(smem + A.sa.sm_surv);
+                for (uint32_t i = tid; i < M.surv_words; i += NT) dst[i] = __ldg(M.surv + i);
+            }
         }
         Smem smi = sm;
-        smi.band = M.band_smem ? reinterpret_cast<const unsigned long long *>(smem + A.sa.sm_band)
-                               : M.band;
+        smi.band = M.band_smem ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_band) : M.band;
         smi.pool = M.pool_smem ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_pool) : M.pool;
+        smi.surv = M.surv ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_surv) : nullptr;
         uint8_t *tsm = text_sm + buf * A.sa.text_buf;
         if (d.tma) {
             if (!mbar_wait_bounded(&misc->bar[buf], d.parity)) misc->abort = 1;
@@ -1078,13 +1092,15 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     a.sm_tab = take(need.tab_bytes, 16);
     a.sm_band = take(need.band_bytes, 16);
     a.sm_pool = take(need.pool_bytes, 16);
+    a.sm_surv = take(need.surv_bytes, 16);
     a.band_smem = need.band_bytes > 0;
     a.pool_smem = need.pool_bytes > 0;
+    a.sm_list = take(nw * 8 * 32 * 2, 16);
     a.sm_text = take(2 * a.text_buf, 128);
     a.sm_queue = take(a.qcap * 4, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
-    a.sm_coop = take(has_nfa ? nw * 2 * a.Wq * 4 : 0, 16);
+    a.sm_coop = 0;   // warp-wide bitsets live in global scratch (coop_g)
     return (o + 127) & ~127u;
 }
 

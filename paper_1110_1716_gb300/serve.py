@@ -26,7 +26,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import (PFSM_OK, Pfsm, pfsm_get_stats, pfsm_scan_batch, pfsm_scan_batch_async)
+from . import (PFSM_E_NOMEM, PFSM_OK, Pfsm, PfsmError, pfsm_get_stats, pfsm_scan_batch,
+               pfsm_scan_batch_async)
 
 
 class Request:
@@ -85,6 +86,7 @@ class Server:
         self.done: List[Request] = []
         self.batches = 0
         self.overflow_reruns = 0
+        self.nomem_splits = 0
         self.bytes_scanned = 0
         self.next_rid = 0
 
@@ -121,17 +123,26 @@ class Server:
         return False
 
     # -------------------------------------------------------------- scheduler
-    def _admit(self, slot: _Slot) -> bool:
-        """Pack pending requests into a free slot and launch its batch."""
-        reqs, used = [], 0
+    def _admit(self, slot: _Slot, one_machine: bool = False) -> bool:
+        """Pack pending requests into a free slot and launch its batch. With
+        `one_machine`, only requests for the first pending request's machine
+        are taken (used when the machines of a mixed batch do not fit the
+        residency budget together)."""
+        reqs, used, skipped = [], 0, []
         with self.lock:
+            first = self.pending[0].aut if self.pending else None
             while self.pending and len(reqs) < slot.max_jobs:
                 r = self.pending[0]
                 if used + len(r.text) > slot.text_bytes:
                     break
                 self.pending.popleft()
+                if one_machine and r.aut != first:
+                    skipped.append(r)
+                    continue
                 reqs.append(r)
                 used += (len(r.text) + 15) & ~15
+            for r in reversed(skipped):
+                self.pending.appendleft(r)
         if not reqs:
             return False
         torch = self.torch
@@ -143,13 +154,27 @@ class Server:
             host[off:off + n] = r.text
             jobs.append((self.ids[r.aut], base + off, n))
             off += (n + 15) & ~15
-        with torch.cuda.stream(slot.stream):
-            slot.text_dev[:off].copy_(slot.text_host[:off], non_blocking=True)
-            pfsm_scan_batch_async(self.pf.ctx, jobs, slot.out_dev, slot.status_dev[:len(jobs) + 2],
-                                  stream=slot.stream)
-            slot.status_host[:len(jobs) + 2].copy_(slot.status_dev[:len(jobs) + 2],
-                                                   non_blocking=True)
-            slot.done.record(slot.stream)
+        try:
+            with torch.cuda.stream(slot.stream):
+                slot.text_dev[:off].copy_(slot.text_host[:off], non_blocking=True)
+                pfsm_scan_batch_async(self.pf.ctx, jobs, slot.out_dev,
+                                      slot.status_dev[:len(jobs) + 2], stream=slot.stream)
+                slot.status_host[:len(jobs) + 2].copy_(slot.status_dev[:len(jobs) + 2],
+                                                       non_blocking=True)
+                slot.done.record(slot.stream)
+        except PfsmError as e:
+            slot.stream.synchronize()
+            if e.status == PFSM_E_NOMEM and not one_machine:
+                # the batch's machines exceed the budget together: requeue
+                # and retry with one machine per batch
+                with self.lock:
+                    for r in reversed(reqs):
+                        self.pending.appendleft(r)
+                self.nomem_splits += 1
+                return self._admit(slot, one_machine=True)
+            for r in reqs:
+                r.future.set_exception(e)
+            return True
         slot.reqs = reqs
         slot.jobs = jobs
         slot.busy = True
@@ -192,6 +217,18 @@ class Server:
         slot.busy = False
 
     def _loop(self):
+        try:
+            self._run()
+        except BaseException as e:   # never leave futures hanging
+            with self.lock:
+                pend = list(self.pending)
+                self.pending.clear()
+            for r in pend + [r for s in self.slots for r in s.reqs]:
+                if not r.future.done():
+                    r.future.set_exception(e)
+            raise
+
+    def _run(self):
         while True:
             progressed = False
             for slot in self.slots:
@@ -218,7 +255,7 @@ class Server:
         return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "batches": self.batches,
-                "overflow_reruns": self.overflow_reruns, **{
+                "overflow_reruns": self.overflow_reruns, "nomem_splits": self.nomem_splits, **{
                     "residency_" + k: v for k, v in pfsm_get_stats(self.pf.ctx).items()}}
 
 

@@ -145,9 +145,17 @@ def test_batch_errors(pf):
 
 
 def test_batch_under_small_budget_reloads(pf):
-    small = P.Pfsm(0, budget_bytes=120_000)
+    autos = [W.dfa_random(60 + i, Q=64, S=4) for i in range(6)]
+    sizes = []
+    for x in autos:
+        before = P.pfsm_get_stats(pf.ctx)["resident_bytes"]
+        a = pf.load(x)
+        sizes.append(P.pfsm_get_stats(pf.ctx)["resident_bytes"] - before)
+        P.pfsm_unload(pf.ctx, a)
+    budget = int(3.5 * max(sizes))     # any three fit together, all six do not
+    assert budget < sum(sizes)
+    small = P.Pfsm(0, budget_bytes=budget)
     try:
-        autos = [W.dfa_random(60 + i, Q=64, S=4) for i in range(6)]
         ids = [small.load(x) for x in autos]
         texts = [W.text_uniform(20_000, 4, 70 + i) for i in range(6)]
         for rnd in range(2):

@@ -68,10 +68,24 @@ def test_mix_equals_alone_burst(fleet):
         assert st["requests"] == len(texts) and st["p99_ms"] >= st["p50_ms"] > 0
 
 
+def fleet_bytes(autos):
+    """Device bytes of each machine, read from the residency counters."""
+    sizes = []
+    with P.Pfsm(0) as pf:
+        for a in autos:
+            before = P.pfsm_get_stats(pf.ctx)["resident_bytes"]
+            pf.load(a)
+            sizes.append(P.pfsm_get_stats(pf.ctx)["resident_bytes"] - before)
+    return sizes
+
+
 def test_mix_equals_alone_poisson_with_evictions(fleet):
     autos, alph = fleet
     auts, texts = requests(autos, alph, 400, 12, median=1024)
-    with P.Pfsm(0, budget_bytes=1 << 20) as pf:
+    sizes = fleet_bytes(autos)
+    budget = max(2 * max(sizes), sum(sizes) // 2)
+    assert budget < sum(sizes)
+    with P.Pfsm(0, budget_bytes=budget) as pf:
         srv = Server(pf, autos, slots=3, slot_bytes=1 << 20, out_rows=1 << 18, max_jobs=32)
         arrivals = np.cumsum(np.random.default_rng(5).exponential(1 / 4000.0, size=len(texts)))
         with srv:
