@@ -187,6 +187,32 @@ int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch 
 int pfsm_scan_batch_async(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
                           uint64_t cap, uint64_t *status_dev, void *stream);
 
+/* Allocation-free DFA scan. The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory (a plugin that is only
+ * handed buffers, a process whose device memory belongs to another
+ * allocator, a loop that must never stall on cudaMalloc/cudaFree). It needs
+ * no context and allocates nothing; its working memory is one 4 MiB array
+ * of device memory that every GPU loading the library holds until exit.
+ *   delta_dev     device, int16 [Q][S] row-major (entries in [0, Q))
+ *   is_final_dev  device, uint8 [Q]
+ *   q0, dead      as for pfsm_load_dfa (dead = -1: none)
+ *   text_dev, n   device text, n < 2^32, every byte < S
+ *   out_dev, cap  device, room for `cap` pfsm_match entries
+ *   status_dev    device, 2 x uint64: { |M|, error bits } when the stream
+ *                 reaches the end of the scan (bit 0: a symbol >= S or a
+ *                 malformed table; |M| > cap means the output was truncated)
+ * Limits: Q * S <= 524288 (the encoded table must fit 1 MiB of the array);
+ * larger tables fail with E_INVAL. The result is the same match set as
+ * pfsm_scan. Asynchronous on `stream`. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture. Calls share the array: two calls whose
+ * work overlaps on the GPU race, so issue them on one stream or wait in
+ * between. Errors detected on the host are returned directly. */
+int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_t S, int32_t q0,
+                          int32_t dead, const uint8_t *is_final_dev, const uint8_t *text_dev,
+                          uint64_t n, pfsm_match *out_dev, uint64_t cap, uint64_t *status_dev,
+                          void *stream);
+
 /* ------------------------------------------------------------------ misc */
 int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);
 

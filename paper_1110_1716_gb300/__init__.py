@@ -32,7 +32,7 @@ PFSM_E_CUDA = 6
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_get_stats", "pfsm_set_timing",
-           "pfsm_kernel_time", "pfsm_strerror")
+           "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc")
 
 
 class pfsm_params(ctypes.Structure):
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_set_timing": [P, ctypes.c_int],
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
         "pfsm_strerror": [ctypes.c_int],
+        "pfsm_scan_dfa_noalloc": [P, I32, I32, I32, I32, P, P, U64, P, U64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +270,21 @@ def pfsm_kernel_time(ctx: int):
 
 def pfsm_strerror(status: int) -> str:
     return strerror(status)
+
+
+def pfsm_scan_dfa_noalloc(delta, q0: int, dead: int, is_final, text, n: Optional[int], out,
+                          status, cap: Optional[int] = None, stream=None) -> None:
+    """Allocation-free DFA scan on caller buffers: `delta` CUDA int16 [Q, S],
+    `is_final` CUDA uint8 [Q], `text` CUDA uint8, `out` CUDA int32 [cap, 3],
+    `status` CUDA int64 [2] receiving (match count, error bits)."""
+    Q, S = delta.shape
+    n = text.numel() if n is None else n
+    cap = (out.shape[0] if out is not None else 0) if cap is None else cap
+    _check(load_library().pfsm_scan_dfa_noalloc(_dev_ptr(delta), Q, S, q0, dead,
+                                                _dev_ptr(is_final), _dev_ptr(text), n,
+                                                _dev_ptr(out), cap, _dev_ptr(status),
+                                                _stream_ptr(stream)),
+           "pfsm_scan_dfa_noalloc")
 
 
 # ---------------------------------------------------------------- convenience
