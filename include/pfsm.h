@@ -83,7 +83,9 @@ typedef struct {
     int32_t spt;        /* starts per thread per filter round: 8 */
     int32_t table_smem; /* delta table in shared memory: 1 yes, 0 no, -1 auto */
     int32_t ctas_per_sm;/* persistent CTAs per SM (0 = occupancy maximum) */
-    int32_t reserved;
+    int32_t settle;     /* NFA: steps a surviving instance is advanced in the
+                           filter before it is queued for the exact path
+                           (0 = library default, -1 = queue at once) */
 } pfsm_params;
 
 /* Residency counters of a context. */

@@ -39,10 +39,10 @@ class pfsm_params(ctypes.Structure):
     _fields_ = [("prefix_k", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("halo", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("spt", ctypes.c_int32), ("table_smem", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("settle", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class pfsm_stats(ctypes.Structure):

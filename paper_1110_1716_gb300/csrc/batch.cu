@@ -156,7 +156,9 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
         d.pool_smem = pool_bytes > 0 && pool_bytes <= kBatchTabMax * 2;
         if (d.band_smem) band_max = std::max(band_max, band_bytes);
         if (d.pool_smem) pool_max = std::max(pool_max, pool_bytes);
-        memo_max = std::max(memo_max, d.memo_n);
+        d.memo_smem = m.surv2.empty() && d.memo_n > 0;
+        if (d.memo_smem) memo_max = std::max(memo_max, d.memo_n);
+        if (!m.surv2.empty()) d.pool_smem = 0;
         surv_max = std::max(surv_max, static_cast<uint32_t>(m.surv.size() * 4));
         if (m.kind == 1) wq_max = std::max(wq_max, d.Wq);
         kmask |= m.kind == 0 ? 1 : 2;
@@ -174,22 +176,22 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     a.memo_n = memo_max;
     a.Wq = wq_max;
     a.stage_n = (kmask & 1) ? STAGE : 32;
+    a.settle_steps = 8;
     uint32_t tile = kBatchTile;
     int threads = 256;
     uint32_t smem = 0;
     bool fit = false;
-    a.qcap = 2 * 8u * threads;
+    a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
     for (int attempt = 0; attempt < 12 && !fit; ++attempt) {
         a.tile = tile;
         a.halo = kBatchHalo;
         a.text_buf = (tile + kBatchHalo + 16 + 127) & ~127u;
-        const SmemNeed need{tab_max, band_max, pool_max, surv_max};
+        const SmemNeed need{memo_max ? ((memo_max + 1) / 2) * 4 + 4 : 0u, tab_max, band_max,
+                            pool_max, surv_max};
         smem = layout_smem(a, kmask, threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
         if (a.stage_n > 32) {
             a.stage_n = 32;
-        } else if (a.qcap > 8u * threads) {
-            a.qcap = 8u * threads;
         } else if (pool_max) {
             pool_max = 0;
             for (auto &d : pl.machs) d.pool_smem = 0;
@@ -203,7 +205,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
             for (auto &d : pl.machs) d.tab_smem = 0;
         } else if (threads > 128) {
             threads /= 2;
-            a.qcap = 2 * 8u * threads;
+            a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
         } else {
             break;
         }
@@ -272,6 +274,10 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
                          uint64_t cap, cudaStream_t s, BatchState **bs) {
     BatchPlan pl;
     int st = plan_batch(ctx, jobs, k, pl);
+    // the pins protect this batch's machines while it is planned; once its
+    // pointers are recorded they may be evicted again (an eviction frees
+    // device memory with cudaFree, which waits for work in flight)
+    ctx->epoch++;
     if (st) return st;
     BatchState *b = nullptr;
     st = state_reserve(ctx, s, std::max<size_t>(1, pl.jobs.size()), std::max<size_t>(1, pl.machs.size()), &b);

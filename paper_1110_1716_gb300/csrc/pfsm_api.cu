@@ -164,55 +164,55 @@ bool build_memo(Machine &m) {
     return build_memo_nfa(m);
 }
 
-// ---- survival bitmap ----------------------------------------------------
+// ---- survival bitmaps ---------------------------------------------------
 // One bit per m-gram w (index sum_j w[j] << (j * sbits)): set when an instance
 // started at q0 either reaches a final state within the m symbols of w or
 // still holds a state after them. A clear bit proves that a start whose next
 // m symbols are w reports nothing, so the filter drops it with one bit test.
-// Kept only when it clears at least half of the m-grams.
-void build_survival(Machine &m) {
-    m.surv.clear();
-    m.sm_m = 0;
-    int mm = std::min(9, 18 / m.sbits);
-    if (mm < 1) return;
+// Built depth-first; a subtree is settled as soon as the set empties (all
+// clear) or a final state is met (all set). Returns false (and no bitmap)
+// when fewer than half of the m-grams are clear.
+static bool survival_bits(const Machine &m, int mm, std::vector<uint32_t> &bits) {
     const uint32_t nbits = 1u << (mm * m.sbits);
-    std::vector<uint32_t> bits((nbits + 31) / 32, 0);
-    const uint32_t smask = (1u << m.sbits) - 1;
+    bits.assign((nbits + 31) / 32, 0);
     uint64_t ones = 0;
-    if (m.kind == 0) {
-        for (uint32_t w = 0; w < nbits; ++w) {
-            int s = m.q0;
-            bool live = true, hit = false;
-            for (int j = 0; j < mm; ++j) {
-                const int a = (w >> (j * m.sbits)) & smask;
-                if (a >= m.S) { live = false; break; }
-                const uint16_t e = m.dtab[(size_t)s * m.S + a];
-                if (e == DEAD16) { live = false; break; }
-                s = e & 0x7FFF;
-                if (e & FINAL_BIT) { hit = true; break; }
-            }
-            if (live || hit) {
-                bits[w >> 5] |= 1u << (w & 31);
-                ++ones;
-            }
+    auto set_range = [&](uint32_t p, int depth) {   // all extensions of a depth-long prefix
+        const uint32_t rest = static_cast<uint32_t>(mm - depth) * m.sbits;
+        for (uint32_t hw = 0; hw < (1u << rest); ++hw) {
+            const uint32_t w = p | (hw << (depth * m.sbits));
+            bits[w >> 5] |= 1u << (w & 31);
         }
+        ones += 1ull << rest;
+    };
+    if (m.kind == 0) {
+        std::function<void(int, uint32_t, int)> dfs = [&](int depth, uint32_t prefix, int s) {
+            if (depth == mm) {
+                bits[prefix >> 5] |= 1u << (prefix & 31);
+                ++ones;
+                return;
+            }
+            for (int a = 0; a < (1 << m.sbits) && a < m.S; ++a) {
+                const uint16_t e = m.dtab[(size_t)s * m.S + a];
+                if (e == DEAD16) continue;
+                const uint32_t p = prefix | (static_cast<uint32_t>(a) << (depth * m.sbits));
+                if (e & FINAL_BIT) set_range(p, depth + 1);
+                else dfs(depth + 1, p, e & 0x7FFF);
+            }
+        };
+        dfs(0, 0, m.q0);
     } else {
         std::vector<uint32_t> mark(m.Q, 0);
         uint32_t stamp = 0;
-        // depth-first over m-grams; a subtree is settled as soon as its set
-        // empties (all clear) or a final state is met (all set)
-        struct Frame { std::vector<uint16_t> set; };
-        std::vector<Frame> lv(mm + 1);
+        std::vector<std::vector<uint16_t>> lv(mm + 1);
         std::function<void(int, uint32_t)> dfs = [&](int depth, uint32_t prefix) {
-            const std::vector<uint16_t> &S = lv[depth].set;
+            const std::vector<uint16_t> &S = lv[depth];
             if (depth == mm) {
-                if (!S.empty()) { bits[prefix >> 5] |= 1u << (prefix & 31); ++ones; }
+                bits[prefix >> 5] |= 1u << (prefix & 31);
+                ++ones;
                 return;
             }
-            if (S.empty()) return;
-            for (int a = 0; a < (1 << m.sbits); ++a) {
-                if (a >= m.S) continue;
-                std::vector<uint16_t> &N = lv[depth + 1].set;
+            for (int a = 0; a < (1 << m.sbits) && a < m.S; ++a) {
+                std::vector<uint16_t> &N = lv[depth + 1];
                 N.clear();
                 bool hit = false;
                 ++stamp;
@@ -228,31 +228,40 @@ void build_survival(Machine &m) {
                     }
                 }
                 const uint32_t p = prefix | (static_cast<uint32_t>(a) << (depth * m.sbits));
-                if (hit) {
-                    const uint32_t rest = static_cast<uint32_t>(mm - depth - 1) * m.sbits;
-                    for (uint32_t hw = 0; hw < (1u << rest); ++hw) {
-                        const uint32_t w = p | (hw << ((depth + 1) * m.sbits));
-                        bits[w >> 5] |= 1u << (w & 31);
-                        ++ones;
-                    }
-                    continue;
-                }
-                dfs(depth + 1, p);
+                if (hit) set_range(p, depth + 1);
+                else if (!N.empty()) dfs(depth + 1, p);
             }
         };
-        lv[0].set = {static_cast<uint16_t>(m.q0)};
+        lv[0] = {static_cast<uint16_t>(m.q0)};
         dfs(0, 0);
     }
-    if (ones * 2 > nbits) return;   // does not prune enough to pay for itself
-    m.surv = std::move(bits);
-    m.sm_m = mm;
+    if (ones * 2 > nbits) {
+        bits.clear();
+        return false;
+    }
+    return true;
+}
+
+// Two filters: a shallow one kept in shared memory (<= 32 KB) and a deep
+// one read from global memory / L2 (<= 2 MB) for the starts that pass the
+// first.
+void build_survival(Machine &m) {
+    m.surv.clear();
+    m.surv2.clear();
+    m.sm_m = 0;
+    m.sm_m2 = 0;
+    const int m1 = std::min(9, 18 / m.sbits);
+    if (m1 >= 1 && survival_bits(m, m1, m.surv)) m.sm_m = m1;
+    const int m2 = std::min(12, 24 / m.sbits);
+    if (m2 > m1 && survival_bits(m, m2, m.surv2)) m.sm_m2 = m2;
 }
 
 // ---- residency --------------------------------------------------------------
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t device_bytes(const Machine &m) {
-    size_t b = align256(m.memo.size() * 2 + 4) + align256(m.surv.size() * 4 + 4);
+    size_t b = align256(m.memo.size() * 2 + 4) + align256(m.surv.size() * 4 + 4) +
+               align256(m.surv2.size() * 4 + 4);
     if (m.kind == 0) {
         b += align256(m.dtab.size() * 2 + 4);
     } else {
@@ -321,6 +330,9 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
     dm.surv = m.surv.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv);
     dm.surv_m = m.sm_m;
     dm.surv_words = static_cast<uint32_t>(m.surv.size());
+    const size_t o_surv2 = put(m.surv2.data(), m.surv2.size() * 4);
+    dm.surv2 = m.surv2.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv2);
+    dm.surv2_m = m.sm_m2;
     if (m.kind == 0) {
         const size_t o_tab = put(m.dtab.data(), m.dtab.size() * 2);
         dm.dtab = reinterpret_cast<const uint16_t *>(base + o_tab);
@@ -409,6 +421,7 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
     if (p.threads == 0) p.threads = 512;
     if (p.spt == 0) p.spt = 8;
     if (p.table_smem == 0) p.table_smem = -1;
+    if (p.settle == 0) p.settle = 8;
 }
 
 int validate_params(const Machine &m, const pfsm_params &p) {
@@ -420,6 +433,7 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.spt != 8) return PFSM_E_INVAL;
     if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
+    if (p.settle < -1 || p.settle > 63) return PFSM_E_INVAL;
     return PFSM_OK;
 }
 
@@ -475,8 +489,10 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.surv = m.dm.surv;
     a.surv_m = m.dm.surv_m;
     a.surv_words = m.dm.surv_words;
+    a.surv2 = m.dm.surv2;
+    a.surv2_m = m.dm.surv2_m;
     a.Wq = m.kind == 1 ? m.dm.Wq : 0;
-    const uint32_t round = 8u * p.threads;
+    const uint32_t round = static_cast<uint32_t>(FILTER_SPT) * p.threads;
     uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
     // table placement: shared memory when asked, or (auto) when small
     a.tab_smem = 0;
@@ -487,22 +503,28 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     const int kmask = m.kind == 0 ? 1 : 2;
     a.stage_n = m.kind == 0 ? STAGE : 32;
     SmemNeed need{};
+    // with a deep filter few starts reach the prefix table: leave it (and the
+    // NFA records) in global memory and keep shared memory for occupancy
+    const bool deep = !m.surv2.empty();
+    need.memo_bytes = deep ? 0u : static_cast<uint32_t>(((m.memo.size() + 1) / 2) * 4 + 4);
+    if (m.memo.empty()) need.memo_bytes = 0;
     need.tab_bytes = a.tab_smem ? tab_bytes : 0;
     need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 4) : 0;
-    need.pool_bytes = (m.kind == 1 && m.pool.size() * 4 <= 64 * 1024)
+    need.pool_bytes = (m.kind == 1 && !deep && m.pool.size() * 4 <= 64 * 1024)
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
+    a.settle_steps = m.params.settle > 0 ? m.params.settle : 0;
     need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
     uint32_t smem = 0;
     bool fit = false;
-    a.qcap = 2 * round;
+    a.qcap = round;   // a filter round may queue every start it owns
     for (int attempt = 0; attempt < 8 && !fit; ++attempt) {
         smem = layout_smem(a, kmask, p.threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        // shrink, cheapest loss first: match staging, queue depth, then
-        // table copies (largest first)
+        // shrink, cheapest loss first: match staging, then table copies
+        // (largest first)
         if (a.stage_n > 32) a.stage_n = 32;
-        else if (a.qcap > round) a.qcap = round;
         else if (need.pool_bytes) need.pool_bytes = 0;
+        else if (need.memo_bytes) need.memo_bytes = 0;
         else if (need.band_bytes) need.band_bytes = 0;
         else if (need.tab_bytes && p.table_smem == -1) { need.tab_bytes = 0; a.tab_smem = 0; }
         else break;

@@ -31,8 +31,8 @@ struct Machine {
     std::vector<uint32_t> pool;
     std::vector<uint32_t> band;   // NFA band image (S <= 4) or empty
     // survival bitmap over m-grams (m = 0: none)
-    int sm_m = 0;
-    std::vector<uint32_t> surv;
+    int sm_m = 0, sm_m2 = 0;
+    std::vector<uint32_t> surv, surv2;   // shallow (shared memory) and deep (global) bitmaps
     pfsm_params params{};
     // residency
     void *dev = nullptr;

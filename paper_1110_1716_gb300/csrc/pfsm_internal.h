@@ -52,8 +52,12 @@ constexpr unsigned long long ERR_TIMEOUT = 2ull;
 
 constexpr int NFA_SLOT = 8;       // states one lane holds for a small NFA set
 constexpr int STAGE = 128;        // largest per-warp match staging (entries)
-constexpr int NFA_INLINE = 8;     // states a filtering thread advances in registers
-constexpr int INLINE_STEPS = 24;  // symbols it advances them before handing over
+constexpr int SETTLE_PAIRS = 128; // per-warp pool of (start, state) pairs being settled
+constexpr int WARP_LIST = 1024;   // surviving starts a warp lists per round (32 lanes x 32)
+// per-warp list area: the start offsets (uint16), the settling pool, the mark
+// bits and the pool count
+constexpr int WARP_LIST_BYTES = 2 * WARP_LIST + 4 * SETTLE_PAIRS + WARP_LIST / 8 + 16;
+constexpr int FILTER_SPT = 32;    // starts per thread per filter round
 
 struct ScanArgs {
     // text
@@ -79,6 +83,8 @@ struct ScanArgs {
     const uint32_t *surv;   // survival bitmap over m-grams, or null
     int32_t surv_m;         // m (0: no bitmap)
     uint32_t surv_words;
+    const uint32_t *surv2;  // deep survival bitmap (global memory), or null
+    int32_t surv2_m;
     int32_t Wq;             // NFA: 32-bit words of a state bitset
     int32_t tab_smem;       // DFA table staged to smem
     uint32_t *coop_g;       // NFA: global scratch for warp-wide state bitsets
@@ -95,6 +101,8 @@ struct ScanArgs {
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t qcap;
     uint32_t stage_n;       // staged matches per warp before a flush
+    int32_t memo_smem;      // prefix table staged to smem (else read from global)
+    int32_t settle_steps;   // NFA: settling step cap (0 = no settling)
 };
 
 // One text of a batch in the device job table (sorted by machine).
@@ -114,7 +122,7 @@ struct DevMachine {
     int32_t tab_smem; // batch: DFA table staged to shared memory
     int32_t band_smem;// batch: NFA band rows staged to shared memory
     int32_t pool_smem;// batch: NFA prefix records staged to shared memory
-    int32_t pad;
+    int32_t memo_smem;// batch: prefix table staged to shared memory
     const uint16_t *memo;
     const uint16_t *dtab;
     const uint32_t *off;
@@ -125,7 +133,8 @@ struct DevMachine {
     int32_t surv_m;
     const uint32_t *surv;
     uint32_t surv_words;
-    int32_t pad3;
+    int32_t surv2_m;
+    const uint32_t *surv2;
 };
 static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
 
@@ -144,6 +153,7 @@ struct BatchArgs {
 // Fill the smem offsets of `a` (kind_mask: 1 = DFA present, 2 = NFA present)
 // for `threads` threads and the table copies in `need`; returns total bytes.
 struct SmemNeed {
+    uint32_t memo_bytes;   // prefix table copy (0 = read from global)
     uint32_t tab_bytes;    // DFA table copy (0 = read from global)
     uint32_t band_bytes;   // NFA band image copy (0 = read from global)
     uint32_t pool_bytes;   // NFA prefix records copy (0 = read from global)

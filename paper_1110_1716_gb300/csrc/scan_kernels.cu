@@ -157,6 +157,32 @@ __device__ __forceinline__ uint32_t memo_index(uint64_t lo, uint64_t hi, uint32_
     }
 }
 
+// m-gram index (m <= 12) of the start at offset `off` of the staged tile,
+// read from four aligned words.
+template <int SB>
+__device__ __forceinline__ uint32_t gram_at16(const uint8_t *tsm, uint32_t off, int m, int sbits,
+                                              uint32_t mask) {
+    const uint32_t a4 = off & ~3u, r = off & 3u;
+    const uint4 w = *reinterpret_cast<const uint4 *>(tsm + (a4 & ~15u));
+    // realign to a4 (a4 may sit 4, 8 or 12 bytes into the 16-byte block)
+    const uint32_t sh = (a4 & 15u) >> 2;
+    const uint32_t x0 = sh == 0 ? w.x : sh == 1 ? w.y : sh == 2 ? w.z : w.w;
+    const uint32_t x1 = sh == 0 ? w.y : sh == 1 ? w.z : sh == 2 ? w.w : 0u;
+    const uint32_t x2 = sh == 0 ? w.z : sh == 1 ? w.w : 0u;
+    const uint32_t x3 = sh == 0 ? w.w : 0u;
+    uint32_t y1 = x1, y2 = x2, y3 = x3;
+    if (sh) {   // the missing words come from the next 16-byte block
+        const uint4 v = *reinterpret_cast<const uint4 *>(tsm + (a4 & ~15u) + 16);
+        if (sh == 1) y3 = v.x;
+        if (sh == 2) { y2 = v.x; y3 = v.y; }
+        if (sh == 3) { y1 = v.x; y2 = v.y; y3 = v.z; }
+    }
+    const uint64_t lo = x0 | (static_cast<uint64_t>(y1) << 32);
+    const uint64_t hi = y2 | (static_cast<uint64_t>(y3) << 32);
+    const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+    return memo_index<SB>(lo, hi, p2, static_cast<int>(r), m, sbits, mask);
+}
+
 // Prefix-table index of the start at offset `off` of the staged tile (k
 // symbols read from three aligned words; k <= 8).
 template <int SB>
@@ -175,7 +201,8 @@ __device__ __forceinline__ uint32_t kgram_at(const uint8_t *tsm, uint32_t off, i
 // ------------------------------------------------------------ views
 // The machine one tile runs (registers).
 struct MView {
-    int32_t Q, S, q0, k, sbits, Wq, surv_m;
+    int32_t Q, S, q0, k, sbits, Wq, surv_m, surv2_m;
+    const uint32_t *surv2;
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;
@@ -211,6 +238,9 @@ struct Smem {
     const uint32_t *pool;             // NFA prefix records (shared copy or global)
     const uint32_t *surv;             // survival bitmap (shared copy) or null
     uint16_t *list;                   // this warp's list of surviving starts
+    uint32_t *pairs;                  // this warp's settling pool (SETTLE_PAIRS)
+    uint32_t *pcount;                 // its fill count
+    uint32_t *marks;                  // WARP_LIST bits: entries sent to the exact path
     uint32_t *queue;
     uint32_t *stage;   // this warp's staging buffer
     uint16_t *slots;   // this warp's NFA slots
@@ -378,61 +408,141 @@ __device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *ban
     for (uint32_t e = lo; e < hi; ++e) f(static_cast<uint32_t>(ldg_u16_keep(mv.tgt + e, pol_keep)));
 }
 
-// Advances the state set of a prefix record in registers through band rows.
-// True when the instance provably reports nothing: its set empties before any
-// final state is reached, or the text ends. False hands it to the exact path
-// (a final target, a set larger than the registers, a row outside the band,
-// or the staged text runs out), which redoes it from its record.
-__device__ __forceinline__ bool nfa_settle(const MView &mv, const Smem &sm, const TileView &tv,
-                                           uint32_t start, uint32_t rec) {
-    const uint32_t hdr = sm.pool[rec];
-    const uint32_t ns = hdr >> 16;
-    if ((hdr & 0xFFFFu) != 0 || ns > static_cast<uint32_t>(NFA_INLINE)) return false;
-    uint32_t s[NFA_INLINE];
-#pragma unroll
-    for (int i = 0; i < NFA_INLINE; ++i) s[i] = static_cast<uint32_t>(i) < ns ? sm.pool[rec + 1 + i] : 0u;
-    uint32_t cnt = ns;
-    uint32_t pos = start + mv.k;
-    const uint32_t tile_end = tv.b + tv.len;
+// Settling of surviving NFA starts, one warp at a time. The instances of a
+// chunk of <= 32 list entries are split into (start, state) pairs, one per
+// state of their prefix record; lanes advance one pair per iteration through
+// the band rows (the first target stays in the lane, further targets go back
+// to a per-warp pool) and refill from the pool. A pair dies when its state
+// has no target on the next symbol. Since the futures of the states of a set
+// are independent, an instance whose pairs all die before meeting a final
+// state reports nothing and is settled. Any other outcome (a final target,
+// a row outside the band, the staged text or the step limit running out, a
+// full pool, matches inside the prefix) marks the instance, and marked
+// instances are queued for the exact path, which redoes them from their
+// record, so nothing is reported twice.
+__device__ __forceinline__ void mark_entry(uint32_t *marks, uint32_t j) {
+    atomicOr(&marks[j >> 5], 1u << (j & 31));
+}
+__device__ __forceinline__ bool marked(const uint32_t *marks, uint32_t j) {
+    return (marks[j >> 5] >> (j & 31)) & 1u;
+}
+
+__device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const TileView &tv,
+                                 uint32_t j0, uint32_t total, uint32_t e, int lane,
+                                 uint32_t max_steps) {
+    uint32_t *pairs = sm.pairs;
+    uint32_t *pcount = sm.pcount;
+    uint32_t *marks = sm.marks;
+    const uint32_t b = tv.b, n = tv.n, tile_end = tv.b + tv.len;
     const uint32_t *fin = sm.band + mv.Q;
-    for (int step = 0; step < INLINE_STEPS; ++step) {
-        if (cnt == 0 || pos >= tv.n) return true;
-        if (pos >= tile_end) return false;
-        const uint32_t c = tv.sm[pos - tv.b];
-        if (c >= static_cast<uint32_t>(mv.S)) return true;   // the scan fails with E_INVAL
-        uint32_t t[NFA_INLINE];
+    // 1. pairs from the prefix records of entries j0 + lane
+    {
+        const uint32_t j = j0 + lane;
+        uint32_t ns = 0, rec = 0;
+        if (j < total) {
+            if (e == PT_WALK) {
+                mark_entry(marks, j);
+            } else if (e != PT_SKIP) {
+                const uint32_t hdr = sm.pool[e];
+                if (hdr & 0xFFFFu) mark_entry(marks, j);   // matches inside the prefix
+                else ns = hdr >> 16, rec = e;
+            }
+        }
+        uint32_t incl = ns;
 #pragma unroll
-        for (int j = 0; j < NFA_INLINE; ++j) t[j] = 0;
-        uint32_t tc = 0;
-#pragma unroll
-        for (int i = 0; i < NFA_INLINE; ++i) {
-            if (static_cast<uint32_t>(i) < cnt) {
-                const uint32_t row = sm.band[s[i]];
-                if (row == BAND_CSR) return false;
-                uint32_t m = (row >> (8 * c)) & 0xFFu;
-                while (m) {
-                    const uint32_t tt = s[i] + __ffs(m);
-                    m &= m - 1;
-                    if ((fin[tt >> 5] >> (tt & 31)) & 1u) return false;
-                    bool dup = false;
-#pragma unroll
-                    for (int j = 0; j < NFA_INLINE; ++j) dup |= (static_cast<uint32_t>(j) < tc) && t[j] == tt;
-                    if (!dup) {
-                        if (tc == static_cast<uint32_t>(NFA_INLINE)) return false;
-#pragma unroll
-                        for (int j = 0; j < NFA_INLINE; ++j)
-                            if (static_cast<uint32_t>(j) == tc) t[j] = tt;
-                        ++tc;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const uint32_t base = *pcount + incl - ns;
+        const bool fits = base + ns <= static_cast<uint32_t>(SETTLE_PAIRS);
+        if (ns && !fits) mark_entry(marks, j);
+        if (ns && fits)
+            for (uint32_t x = 0; x < ns; ++x)
+                pairs[base + x] = (j << 21) | sm.pool[rec + 1 + x];   // step 0
+        const uint32_t end = __reduce_max_sync(FULLMASK, (ns && fits) ? base + ns : 0u);
+        __syncwarp();
+        if (lane == 0 && end > *pcount) *pcount = end;
+        __syncwarp();
+    }
+    // 2. advance pairs with lane refill until the pool is empty
+    bool has = false;
+    uint32_t li = 0, step = 0, q = 0, start_pos = 0;
+    while (true) {
+        const uint32_t need = __ballot_sync(FULLMASK, !has);
+        uint32_t avail = 0, take = 0;
+        if (lane == 0) {
+            avail = *pcount;
+            take = min(avail, static_cast<uint32_t>(__popc(need)));
+            *pcount = avail - take;
+        }
+        avail = __shfl_sync(FULLMASK, avail, 0);
+        take = __shfl_sync(FULLMASK, take, 0);
+        if (!has) {
+            const uint32_t r = __popc(need & lanemask_lt());
+            if (r < take) {
+                const uint32_t e = pairs[avail - take + r];
+                li = e >> 21;
+                step = (e >> 15) & 0x3Fu;
+                q = e & 0x7FFFu;
+                start_pos = b + sm.list[li] + mv.k;
+                has = true;
+            }
+        }
+        __syncwarp();
+        if (!__any_sync(FULLMASK, has)) break;
+        if (has && marked(marks, li)) has = false;
+        if (has) {
+            const uint32_t pos = start_pos + step;
+            if (pos >= n) {
+                has = false;
+            } else if (pos >= tile_end || step >= max_steps) {
+                mark_entry(marks, li);
+                has = false;
+            } else {
+                const uint32_t c = tv.sm[pos - b];
+                const uint32_t row = c < static_cast<uint32_t>(mv.S) ? sm.band[q] : 0u;
+                if (row == BAND_CSR) {
+                    mark_entry(marks, li);
+                    has = false;
+                } else {
+                    uint32_t m = (row >> (8 * c)) & 0xFFu;
+                    bool first = true;
+                    uint32_t nq = 0;
+                    while (m) {
+                        const uint32_t t = q + __ffs(m);
+                        m &= m - 1;
+                        if ((fin[t >> 5] >> (t & 31)) & 1u) {
+                            mark_entry(marks, li);
+                            first = true;
+                            m = 0;
+                            nq = 0xFFFFFFFFu;
+                            break;
+                        }
+                        if (first) {
+                            nq = t;
+                            first = false;
+                        } else {
+                            const uint32_t slot = atomicAdd(pcount, 1u);
+                            if (slot < static_cast<uint32_t>(SETTLE_PAIRS))
+                                pairs[slot] = (li << 21) | ((step + 1) << 15) | t;
+                            else
+                                mark_entry(marks, li);
+                        }
+                    }
+                    if (first || nq == 0xFFFFFFFFu) {
+                        has = false;
+                    } else {
+                        q = nq;
+                        ++step;
                     }
                 }
             }
         }
-#pragma unroll
-        for (int j = 0; j < NFA_INLINE; ++j) s[j] = t[j];
-        cnt = tc;
-        ++pos;
+        __syncwarp();
+        if (lane == 0 && *pcount > static_cast<uint32_t>(SETTLE_PAIRS)) *pcount = SETTLE_PAIRS;
+        __syncwarp();
     }
-    return cnt == 0;
 }
 
 // ------------------------------------------------------------ continuation: NFA
@@ -652,8 +762,8 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
 template <int KIND, int SB, bool TAB_SMEM, int OUTW>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t qcap, uint32_t &sn,
-                             bool &bad_symbol, uint64_t pol_keep) {
-    constexpr int SPT = 8;   // starts per thread per filter round
+                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps) {
+    constexpr int SPT = 32;   // starts per thread per filter round (4 windows of 8)
     const int tid = threadIdx.x, lane = tid & 31;
     const int NT = blockDim.x;
     const uint32_t n = tv.n, b = tv.b;
@@ -664,6 +774,9 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
     const uint32_t mm = static_cast<uint32_t>(mv.surv_m);
     const uint32_t mbits = mm * static_cast<uint32_t>(mv.sbits);
     const uint32_t mmask = mbits >= 32 ? 0xFFFFFFFFu : ((1u << mbits) - 1);
+    const uint32_t m2 = static_cast<uint32_t>(mv.surv2_m);
+    const uint32_t m2bits = m2 * static_cast<uint32_t>(mv.sbits);
+    const uint32_t m2mask = m2bits >= 32 ? 0xFFFFFFFFu : ((1u << m2bits) - 1);
     for (uint32_t r0 = b; r0 < own_end; r0 += round) {
         if (sm.misc->q_count + round > qcap) {
             drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
@@ -674,70 +787,112 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             }
             __syncthreads();
         }
-        // 1. this thread's SPT starts: symbol check and survival-bitmap test
+        // 1. this thread's SPT consecutive starts: symbol check and the
+        //    shared-memory survival bitmap, one 16-byte window per 8 starts
         const uint32_t i0 = r0 + SPT * tid;
         uint32_t live = 0;
         if (i0 < own_end) {
-            const uint8_t *tp = tv.sm + (i0 - b);
-            const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-            const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-            const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-            const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
             const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
-            if (mv.S < 256) {
-                uint64_t badm = bytes_ge(lo, mv.S);
-                if (nown < 8) badm &= (1ull << (8 * nown)) - 1;
-                if (badm) bad_symbol = true;
-            }
-            live = (1u << nown) - 1;
-            if (sm.surv) {
-                const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+            live = nown >= 32 ? 0xFFFFFFFFu : ((1u << nown) - 1);
 #pragma unroll
-                for (int r = 0; r < SPT; ++r) {
-                    if (static_cast<uint32_t>(r) < nown && i0 + r + mm <= n) {
-                        const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
-                        if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << r);
+            for (int g = 0; g < SPT / 8; ++g) {
+                if (static_cast<uint32_t>(8 * g) < nown) {
+                    const uint8_t *tp = tv.sm + (i0 - b) + 8 * g;
+                    const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                    const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                    const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                    const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                    const uint32_t gown = min(8u, nown - 8 * g);
+                    if (mv.S < 256) {
+                        uint64_t badm = bytes_ge(lo, mv.S);
+                        if (gown < 8) badm &= (1ull << (8 * gown)) - 1;
+                        if (badm) bad_symbol = true;
+                    }
+                    if (sm.surv) {
+                        const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const uint32_t i = i0 + 8 * g + r;
+                            if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
+                                const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
+                                if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << (8 * g + r));
+                            }
+                        }
                     }
                 }
             }
         }
         // 2. compact the surviving starts into this warp's list
-        const uint32_t c = __popc(live);
-        uint32_t incl = c;
+        uint32_t total = 0;
+        if (__any_sync(FULLMASK, live != 0)) {
+            const uint32_t c = __popc(live);
+            uint32_t incl = c;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
-            if (lane >= d) incl += v;
-        }
-        const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
-        {
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+                if (lane >= d) incl += v;
+            }
+            total = __shfl_sync(FULLMASK, incl, 31);
             uint32_t p = incl - c;
-#pragma unroll
-            for (int r = 0; r < SPT; ++r)
-                if (live >> r & 1u) sm.list[p++] = static_cast<uint16_t>(i0 + r - b);
+            uint32_t x = live;
+            while (x) {
+                const uint32_t r = __ffs(x) - 1;
+                x &= x - 1;
+                sm.list[p++] = static_cast<uint16_t>(i0 + r - b);
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        // 3. every lane takes list entries: prefix table, settling, queue
+        // 3a. deep survival bitmap (global memory, L2 resident): independent
+        //     loads per lane, then compact the list in place
+        if (mv.surv2 && total) {
+            uint32_t w = 0;
+            for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool keep = false;
+                uint32_t off = 0;
+                if (j < total) {
+                    off = sm.list[j];
+                    keep = true;
+                    if (b + off + m2 <= n) {
+                        const uint32_t i2 = gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
+                        keep = (ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep) >> (i2 & 31)) & 1u;
+                    }
+                }
+                const uint32_t km = __ballot_sync(FULLMASK, keep);
+                __syncwarp();
+                if (keep) sm.list[w + __popc(km & lanemask_lt())] = static_cast<uint16_t>(off);
+                w += __popc(km);
+                __syncwarp();
+            }
+            total = w;
+        }
+        // 3b. every lane takes list entries: prefix table, settling, queue
+        const bool settle = KIND == 1 && sm.band && settle_steps > 0 && total;
+        if (settle) {
+            sm.marks[lane] = 0;
+            if (lane == 0) *sm.pcount = 0;
+            __syncwarp();
+        }
         for (uint32_t j0 = 0; j0 < total; j0 += 32) {
             const uint32_t j = j0 + lane;
-            bool push = false;
-            uint32_t qe = 0;
+            uint32_t e = PT_SKIP, off = 0;
             if (j < total) {
-                const uint32_t off = sm.list[j];
-                const uint32_t i = b + off;
-                uint32_t e = PT_WALK;
-                if (kk != 0 && i + kk <= n) e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
-                push = e != PT_SKIP;
-                if (KIND == 1 && push && e != PT_WALK && sm.band && nfa_settle(mv, sm, tv, i, e))
-                    push = false;
-                qe = off | (e << 16);
+                off = sm.list[j];
+                e = PT_WALK;
+                if (kk != 0 && b + off + kk <= n)
+                    e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+            }
+            bool push = e != PT_SKIP;
+            if (settle) {
+                nfa_settle_chunk(mv, sm, tv, j0, total, e, lane, settle_steps);
+                push = j < total && marked(sm.marks, j);
             }
             const uint32_t pmask = __ballot_sync(FULLMASK, push);
             if (pmask) {
                 uint32_t base = 0;
                 if (lane == 0) base = atomicAdd(&sm.misc->q_count, __popc(pmask));
                 base = __shfl_sync(FULLMASK, base, 0);
-                if (push) sm.queue[base + __popc(pmask & lanemask_lt())] = qe;
+                if (push) sm.queue[base + __popc(pmask & lanemask_lt())] = off | (e << 16);
             }
         }
         __syncwarp();
@@ -755,7 +910,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
 __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid) {
     Smem s;
     s.misc = reinterpret_cast<Misc *>(base + a.sm_misc);
-    s.memo = reinterpret_cast<const uint16_t *>(base + a.sm_memo);
+    s.memo = a.memo_smem ? reinterpret_cast<const uint16_t *>(base + a.sm_memo) : a.memo;
     s.tab = reinterpret_cast<const uint16_t *>(base + a.sm_tab);
     s.queue = reinterpret_cast<uint32_t *>(base + a.sm_queue);
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
@@ -764,7 +919,11 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
                       : nullptr;
     s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
     s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;
-    s.list = reinterpret_cast<uint16_t *>(base + a.sm_list) + wid * (8 * 32);
+    uint8_t *wl = base + a.sm_list + wid * WARP_LIST_BYTES;
+    s.list = reinterpret_cast<uint16_t *>(wl);
+    s.pairs = reinterpret_cast<uint32_t *>(wl + 2 * WARP_LIST);
+    s.marks = reinterpret_cast<uint32_t *>(wl + 2 * WARP_LIST + 4 * SETTLE_PAIRS);
+    s.pcount = s.marks + WARP_LIST / 32;
     s.pool = a.pool_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_pool) : a.pool;
     return s;
 }
@@ -806,9 +965,9 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
-    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.dtab, a.off, a.tgt};
+    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt};
 
-    stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
+    if (a.memo_smem) stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
     if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
     if (KIND == 1) stage_nfa(smem, a.sm_band, a.sm_pool, a.band_smem ? a.band : nullptr, a.Q,
                              a.pool_smem ? a.pool : nullptr, a.pool_n, tid, NT);
@@ -861,7 +1020,7 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
         if (misc->abort) break;
         const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
         process_tile<KIND, SB, TAB_SMEM, 3>(ov, mv, tv, sm, min(b + a.tile, n), a.qcap, sn,
-                                            bad_symbol, pol_keep);
+                                            bad_symbol, pol_keep, static_cast<uint32_t>(a.settle_steps));
     }
     stage_flush<3>(sm.stage, sn, ov, 0u, lane);
     if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
@@ -893,7 +1052,7 @@ __device__ __forceinline__ uint32_t find_job(const BatchJob *jobs, uint32_t njob
 }
 
 __device__ __forceinline__ MView mview_of(const DevMachine &m) {
-    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.dtab, m.off, m.tgt};
+    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.surv2_m, m.surv2, m.dtab, m.off, m.tgt};
 }
 
 __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict__ gargs) {
@@ -962,7 +1121,7 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
         if (tid == 0) claim(buf ^ 1);   // prefetch the next item
         const DevMachine &M = A.machs[d.mach];
         if (static_cast<int32_t>(d.mach) != cur_mach) {
-            stage_u16(const_cast<uint16_t *>(sm.memo), M.memo, M.memo_n, tid, NT);
+            if (M.memo_smem) stage_u16(const_cast<uint16_t *>(sm.memo), M.memo, M.memo_n, tid, NT);
             if (M.tab_smem) stage_u16(const_cast<uint16_t *>(sm.tab), M.dtab, M.Q * M.S, tid, NT);
             if (M.kind == 1)
                 stage_nfa(smem, A.sa.sm_band, A.sa.sm_pool, M.band_smem ? M.band : nullptr, M.Q,
@@ -973,6 +1132,7 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
             }
         }
         Smem smi = sm;
+        smi.memo = M.memo_smem ? sm.memo : M.memo;
         smi.band = M.band_smem ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_band) : M.band;
         smi.pool = M.pool_smem ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_pool) : M.pool;
         smi.surv = M.surv ? reinterpret_cast<const uint32_t *>(smem + A.sa.sm_surv) : nullptr;
@@ -993,24 +1153,24 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
         if (M.kind == 0) {
             if (M.tab_smem) {
                 if (M.sbits == 2 && M.k > 0)
-                    process_tile<0, 2, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                    process_tile<0, 2, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else
-                    process_tile<0, 0, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                    process_tile<0, 0, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             } else {
                 if (M.sbits == 8 && M.k > 0)
-                    process_tile<0, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                    process_tile<0, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else if (M.sbits == 2 && M.k > 0)
-                    process_tile<0, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                    process_tile<0, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else
-                    process_tile<0, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                    process_tile<0, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             }
         } else {
             if (M.sbits == 2 && M.k > 0)
-                process_tile<1, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                process_tile<1, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             else if (M.sbits == 8 && M.k > 0)
-                process_tile<1, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                process_tile<1, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             else
-                process_tile<1, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep);
+                process_tile<1, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
         }
         // per-text counts: the staged matches all belong to this item's text
         stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
@@ -1088,14 +1248,15 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     };
     if (a.stage_n == 0) a.stage_n = STAGE;
     a.sm_misc = take(sizeof(Misc), 16);
-    a.sm_memo = take(((a.memo_n + 1) / 2) * 4 + 4, 16);
+    a.sm_memo = take(need.memo_bytes, 16);
+    a.memo_smem = need.memo_bytes > 0;
     a.sm_tab = take(need.tab_bytes, 16);
     a.sm_band = take(need.band_bytes, 16);
     a.sm_pool = take(need.pool_bytes, 16);
     a.sm_surv = take(need.surv_bytes, 16);
     a.band_smem = need.band_bytes > 0;
     a.pool_smem = need.pool_bytes > 0;
-    a.sm_list = take(nw * 8 * 32 * 2, 16);
+    a.sm_list = take(nw * WARP_LIST_BYTES, 16);
     a.sm_text = take(2 * a.text_buf, 128);
     a.sm_queue = take(a.qcap * 4, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);

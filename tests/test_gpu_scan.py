@@ -113,6 +113,8 @@ PARAMS = [
     {"threads": 128, "tile": 8192},
     {"threads": 256, "table_smem": 0},
     {"threads": 512, "tile": 32768, "halo": 4096, "ctas_per_sm": 1},
+    {"settle": -1},
+    {"settle": 2, "prefix_k": 4},
 ]
 
 
@@ -124,7 +126,8 @@ def test_params_do_not_change_dfa_result(pf, params):
     assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t))
 
 
-@pytest.mark.parametrize("params", PARAMS[:4], ids=lambda p: ",".join("%s=%s" % kv for kv in p.items()))
+@pytest.mark.parametrize("params", PARAMS[:4] + PARAMS[-2:],
+                         ids=lambda p: ",".join("%s=%s" % kv for kv in p.items()))
 def test_params_do_not_change_nfa_result(pf, params):
     nfa, t, _, _ = W.workload_motif_nfa(5, n=150_000, n_motifs=64, every=1500)
     a = pf.load(nfa)
@@ -283,10 +286,18 @@ def test_instances_outliving_tiles_use_the_carry_queue(pf):
 
 
 def test_eviction_and_reload(pf):
-    small = P.Pfsm(0, budget_bytes=80_000)
+    autos = [W.dfa_random(50 + i, Q=64, S=4) for i in range(3)]
+    autos.append(W.workload_motif_nfa(3, n=10, n_motifs=40)[0])
+    sizes = []
+    for x in autos:
+        before = P.pfsm_get_stats(pf.ctx)["resident_bytes"]
+        a = pf.load(x)
+        sizes.append(P.pfsm_get_stats(pf.ctx)["resident_bytes"] - before)
+        P.pfsm_unload(pf.ctx, a)
+    budget = max(sizes) + min(sizes)      # never room for all of them
+    assert budget < sum(sizes)
+    small = P.Pfsm(0, budget_bytes=budget)
     try:
-        autos = [W.dfa_random(50 + i, Q=64, S=4) for i in range(3)]
-        autos.append(W.workload_motif_nfa(3, n=10, n_motifs=40)[0])
         ids = [small.load(x) for x in autos]
         t = W.text_uniform(60_000, 4, 5)
         for rnd in range(2):
@@ -294,7 +305,7 @@ def test_eviction_and_reload(pf):
                 assert np.array_equal(gpu_matches(small, i, t), oracle.scan(x, t))
         st = P.pfsm_get_stats(small.ctx)
         assert st["evictions"] > 0 and st["reloads"] > 0
-        assert st["resident_bytes"] <= 80_000
+        assert st["resident_bytes"] <= budget
         P.pfsm_evict(small.ctx, ids[0])
         assert np.array_equal(gpu_matches(small, ids[0], t), oracle.scan(autos[0], t))
         P.pfsm_unload(small.ctx, ids[1])
