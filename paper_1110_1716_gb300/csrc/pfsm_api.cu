@@ -418,10 +418,10 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
     if (p.prefix_k == 0) p.prefix_k = default_k(m);
     // tile 0 = automatic: 16 KiB, smaller for texts too short to fill the GPU
     if (p.halo == 0) p.halo = 2048;
-    if (p.threads == 0) p.threads = 512;
+    // threads 0 = automatic: 512, fewer for texts too short to fill the GPU
     if (p.spt == 0) p.spt = 8;
     if (p.table_smem == 0) p.table_smem = -1;
-    if (p.settle == 0) p.settle = 8;
+    if (p.settle == 0) p.settle = 16;
 }
 
 int validate_params(const Machine &m, const pfsm_params &p) {
@@ -429,7 +429,8 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.prefix_k > 0 && p.prefix_k * m.sbits > 16) return PFSM_E_INVAL;
     if (p.tile != 0 && (p.tile < 4096 || p.tile > 49152 || p.tile % 4096)) return PFSM_E_INVAL;
     if (p.halo < 16 || p.halo > 16384 || p.halo % 16) return PFSM_E_INVAL;
-    if (p.threads != 128 && p.threads != 256 && p.threads != 512) return PFSM_E_INVAL;
+    if (p.threads != 0 && p.threads != 128 && p.threads != 256 && p.threads != 512)
+        return PFSM_E_INVAL;
     if (p.spt != 8) return PFSM_E_INVAL;
     if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
@@ -462,11 +463,21 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     memset(&a, 0, sizeof(a));
     a.text = text;
     a.n = static_cast<uint32_t>(n);
+    int threads = p.threads;
+    if (threads == 0) {
+        // a filter round covers FILTER_SPT starts per thread: keep at least
+        // two rounds' worth of tiles per SM
+        threads = 512;
+        while (threads > 128 &&
+               n < 2ull * ctx->nsm * static_cast<uint64_t>(FILTER_SPT) * threads)
+            threads /= 2;
+    }
     uint32_t tile = static_cast<uint32_t>(p.tile);
     if (tile == 0) {
         // at least two tiles per SM when the text allows it
         const uint64_t want = n / (2ull * ctx->nsm);
         tile = static_cast<uint32_t>(std::min<uint64_t>(16384, std::max<uint64_t>(4096, (want + 4095) & ~4095ull)));
+        tile = std::max<uint32_t>(tile, static_cast<uint32_t>(FILTER_SPT) * threads);
     }
     a.tile = tile;
     a.halo = p.halo;
@@ -492,7 +503,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.surv2 = m.dm.surv2;
     a.surv2_m = m.dm.surv2_m;
     a.Wq = m.kind == 1 ? m.dm.Wq : 0;
-    const uint32_t round = static_cast<uint32_t>(FILTER_SPT) * p.threads;
+    const uint32_t round = static_cast<uint32_t>(FILTER_SPT) * threads;
     uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
     // table placement: shared memory when asked, or (auto) when small
     a.tab_smem = 0;
@@ -518,7 +529,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     bool fit = false;
     a.qcap = round;   // a filter round may queue every start it owns
     for (int attempt = 0; attempt < 8 && !fit; ++attempt) {
-        smem = layout_smem(a, kmask, p.threads, need);
+        smem = layout_smem(a, kmask, threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
         // shrink, cheapest loss first: match staging, then table copies
         // (largest first)
@@ -530,10 +541,10 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         else break;
     }
     if (!fit) return PFSM_E_INVAL;
-    int occ = max_ctas_per_sm(m.kind, m.sbits, p.threads, smem, a.tab_smem != 0);
+    int occ = max_ctas_per_sm(m.kind, m.sbits, threads, smem, a.tab_smem != 0);
     if (occ <= 0) return PFSM_E_INVAL;
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
-    pl.threads = p.threads;
+    pl.threads = threads;
     pl.smem = smem;
     pl.grid = static_cast<int>(std::min<uint64_t>(a.ntiles, static_cast<uint64_t>(ctx->nsm) * occ));
     if (pl.grid < 1) pl.grid = 1;

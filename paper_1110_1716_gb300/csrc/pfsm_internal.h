@@ -58,6 +58,7 @@ constexpr int WARP_LIST = 1024;   // surviving starts a warp lists per round (32
 // bits and the pool count
 constexpr int WARP_LIST_BYTES = 2 * WARP_LIST + 4 * SETTLE_PAIRS + WARP_LIST / 8 + 16;
 constexpr int FILTER_SPT = 32;    // starts per thread per filter round
+constexpr int WARP_QUEUE = 256;   // per-warp queue of instances for the exact path
 
 struct ScanArgs {
     // text

@@ -241,7 +241,8 @@ struct Smem {
     uint32_t *pairs;                  // this warp's settling pool (SETTLE_PAIRS)
     uint32_t *pcount;                 // its fill count
     uint32_t *marks;                  // WARP_LIST bits: entries sent to the exact path
-    uint32_t *queue;
+    uint32_t *wq_start;               // this warp's work queue: absolute starts
+    uint16_t *wq_info;                //   and prefix-table entries (WARP_QUEUE)
     uint32_t *stage;   // this warp's staging buffer
     uint16_t *slots;   // this warp's NFA slots
     uint32_t *coop;    // this warp's two bitsets of Wq words
@@ -312,26 +313,25 @@ __device__ __forceinline__ void emit_direct(const OView &ov, uint32_t orig, uint
 // Drains the work queue with lane refill: one symbol per lane per iteration.
 template <bool TAB_SMEM, int OUTW>
 __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
-                          uint32_t &sn, int lane, uint64_t pol_keep) {
-    const uint32_t qn = sm.misc->q_count;
+                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep) {
+    uint32_t head = 0;
     const uint32_t S = mv.S, n = tv.n;
-    const uint32_t tile_end = tv.b + tv.len;
+    // no staged tile (the final drain): nothing to hand to the carry queue
+    const uint32_t tile_end = tv.len ? tv.b + tv.len : 0xFFFFFFFFu;
     bool act = false;
     bool gmode = false;   // past the staged text and the carry queue is full
     uint32_t start = 0, pos = 0, s = 0;
     while (true) {
         const bool need = !act;
         const uint32_t m = __ballot_sync(FULLMASK, need);
-        if (m) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&sm.misc->q_head, __popc(m));
-            base = __shfl_sync(FULLMASK, base, 0);
+        if (m && head < qn) {
+            const uint32_t base = head;
+            head += __popc(m);
             if (need) {
                 const uint32_t qi = base + __popc(m & lanemask_lt());
                 if (qi < qn) {
-                    const uint32_t e = sm.queue[qi];
-                    start = tv.b + (e & 0xFFFFu);
-                    const uint32_t info = e >> 16;
+                    start = sm.wq_start[qi];
+                    const uint32_t info = sm.wq_info[qi];
                     if (info == PT_WALK) {
                         s = mv.q0;
                         pos = start;
@@ -593,8 +593,8 @@ enum : uint32_t { MODE_LANE = 0, MODE_COOP_SLOT = 1, MODE_COOP_POOL = 2 };
 // (up to NFA_SLOT states) and advances it one symbol per iteration.
 template <int OUTW>
 __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
-                          uint32_t &sn, int lane, uint64_t pol_keep) {
-    const uint32_t qn = sm.misc->q_count;
+                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep) {
+    uint32_t head = 0;
     const uint32_t S = mv.S, n = tv.n;
     constexpr int C = NFA_SLOT;
     uint16_t *slots = sm.slots;
@@ -605,16 +605,14 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
     while (true) {
         const bool need = !act;
         const uint32_t m = __ballot_sync(FULLMASK, need);
-        if (m) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&sm.misc->q_head, __popc(m));
-            base = __shfl_sync(FULLMASK, base, 0);
+        if (m && head < qn) {
+            const uint32_t base = head;
+            head += __popc(m);
             if (need) {
                 const uint32_t qi = base + __popc(m & lanemask_lt());
                 if (qi < qn) {
-                    const uint32_t e = sm.queue[qi];
-                    start = tv.b + (e & 0xFFFFu);
-                    const uint32_t info = e >> 16;
+                    start = sm.wq_start[qi];
+                    const uint32_t info = sm.wq_info[qi];
                     act = true;
                     mode = MODE_LANE;
                     pm_left = 0;
@@ -749,11 +747,15 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
 
 template <int KIND, bool TAB_SMEM, int OUTW>
 __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const TileView &tv,
-                                      const Smem &sm, uint32_t &sn, int lane, uint64_t pol_keep) {
+                                      const Smem &sm, uint32_t &wq_n, uint32_t &sn, int lane,
+                                      uint64_t pol_keep) {
+    if (wq_n == 0) return;
     if (KIND == 0)
-        drain_dfa<TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+        drain_dfa<TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     else
-        drain_nfa<OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
+        drain_nfa<OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+    __syncwarp();
+    wq_n = 0;
 }
 
 // ------------------------------------------------------------ one tile
@@ -761,7 +763,7 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
 // continuation of every queued instance. All threads of the CTA call this.
 template <int KIND, int SB, bool TAB_SMEM, int OUTW>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
-                             const Smem &sm, uint32_t own_end, uint32_t qcap, uint32_t &sn,
+                             const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
                              bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps) {
     constexpr int SPT = 32;   // starts per thread per filter round (4 windows of 8)
     const int tid = threadIdx.x, lane = tid & 31;
@@ -778,15 +780,6 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
     const uint32_t m2bits = m2 * static_cast<uint32_t>(mv.sbits);
     const uint32_t m2mask = m2bits >= 32 ? 0xFFFFFFFFu : ((1u << m2bits) - 1);
     for (uint32_t r0 = b; r0 < own_end; r0 += round) {
-        if (sm.misc->q_count + round > qcap) {
-            drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
-            __syncthreads();
-            if (tid == 0) {
-                sm.misc->q_count = 0;
-                sm.misc->q_head = 0;
-            }
-            __syncthreads();
-        }
         // 1. this thread's SPT consecutive starts: symbol check and the
         //    shared-memory survival bitmap, one 16-byte window per 8 starts
         const uint32_t i0 = r0 + SPT * tid;
@@ -889,22 +882,20 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             }
             const uint32_t pmask = __ballot_sync(FULLMASK, push);
             if (pmask) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(&sm.misc->q_count, __popc(pmask));
-                base = __shfl_sync(FULLMASK, base, 0);
-                if (push) sm.queue[base + __popc(pmask & lanemask_lt())] = off | (e << 16);
+                // this warp's queue: drain it first when these would not fit
+                if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
+                    drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+                if (push) {
+                    const uint32_t p = wq_n + __popc(pmask & lanemask_lt());
+                    sm.wq_start[p] = b + off;
+                    sm.wq_info[p] = static_cast<uint16_t>(e);
+                }
+                wq_n += __popc(pmask);
+                __syncwarp();
             }
         }
         __syncwarp();
-        __syncthreads();
     }
-    drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, sn, lane, pol_keep);
-    __syncthreads();
-    if (tid == 0) {
-        sm.misc->q_count = 0;
-        sm.misc->q_head = 0;
-    }
-    __syncthreads();
 }
 
 __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid) {
@@ -912,7 +903,9 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
     s.misc = reinterpret_cast<Misc *>(base + a.sm_misc);
     s.memo = a.memo_smem ? reinterpret_cast<const uint16_t *>(base + a.sm_memo) : a.memo;
     s.tab = reinterpret_cast<const uint16_t *>(base + a.sm_tab);
-    s.queue = reinterpret_cast<uint32_t *>(base + a.sm_queue);
+    s.wq_start = reinterpret_cast<uint32_t *>(base + a.sm_queue) + wid * WARP_QUEUE;
+    s.wq_info = reinterpret_cast<uint16_t *>(base + a.sm_queue + (blockDim.x >> 5) * WARP_QUEUE * 4) +
+                wid * WARP_QUEUE;
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
     s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
     s.coop = a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
@@ -986,6 +979,7 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
     __syncthreads();
 
     uint32_t sn = 0;
+    uint32_t wq_n = 0;   // entries in this warp's queue
     bool bad_symbol = false;
     const uint32_t n = a.n;
     auto issue = [&](uint32_t tile, int buf) {
@@ -1019,8 +1013,16 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
         __syncthreads();
         if (misc->abort) break;
         const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
-        process_tile<KIND, SB, TAB_SMEM, 3>(ov, mv, tv, sm, min(b + a.tile, n), a.qcap, sn,
+        process_tile<KIND, SB, TAB_SMEM, 3>(ov, mv, tv, sm, min(b + a.tile, n), wq_n, sn,
                                             bad_symbol, pol_keep, static_cast<uint32_t>(a.settle_steps));
+        // the staged buffer is refilled two tiles on: every warp must be done
+        __syncthreads();
+    }
+    // instances queued across tiles run now, reading the text from global
+    // memory (the staged tiles are gone)
+    {
+        const TileView tv{text_sm, a.text, 0u, 0u, n, 0u, 0u};
+        drain<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     }
     stage_flush<3>(sm.stage, sn, ov, 0u, lane);
     if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
@@ -1113,6 +1115,7 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
     __syncthreads();
 
     uint32_t sn = 0;
+    uint32_t wq_n = 0;
     bool bad_symbol = false;
     for (uint32_t it = 0;; ++it) {
         const int buf = it & 1;
@@ -1149,30 +1152,37 @@ __global__ void __launch_bounds__(256, 1) scan_items(const BatchArgs *__restrict
         const MView mv = mview_of(M);
         const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
-        const uint32_t qcap = A.sa.qcap;
+
         if (M.kind == 0) {
             if (M.tab_smem) {
                 if (M.sbits == 2 && M.k > 0)
-                    process_tile<0, 2, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                    process_tile<0, 2, true, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else
-                    process_tile<0, 0, true, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                    process_tile<0, 0, true, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             } else {
                 if (M.sbits == 8 && M.k > 0)
-                    process_tile<0, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                    process_tile<0, 8, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else if (M.sbits == 2 && M.k > 0)
-                    process_tile<0, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                    process_tile<0, 2, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
                 else
-                    process_tile<0, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                    process_tile<0, 0, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             }
         } else {
             if (M.sbits == 2 && M.k > 0)
-                process_tile<1, 2, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                process_tile<1, 2, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             else if (M.sbits == 8 && M.k > 0)
-                process_tile<1, 8, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                process_tile<1, 8, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
             else
-                process_tile<1, 0, false, 4>(ov, mv, tv, smi, own_end, qcap, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
+                process_tile<1, 0, false, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep, static_cast<uint32_t>(A.sa.settle_steps));
         }
-        // per-text counts: the staged matches all belong to this item's text
+        // this item's queued instances, then its staged matches (per-text
+        // counts need both to belong to this item's text)
+        if (M.kind == 0) {
+            if (M.tab_smem) drain<0, true, 4>(ov, mv, tv, smi, wq_n, sn, lane, pol_keep);
+            else drain<0, false, 4>(ov, mv, tv, smi, wq_n, sn, lane, pol_keep);
+        } else {
+            drain<1, false, 4>(ov, mv, tv, smi, wq_n, sn, lane, pol_keep);
+        }
         stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
         __syncthreads();
     }
@@ -1258,7 +1268,7 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     a.pool_smem = need.pool_bytes > 0;
     a.sm_list = take(nw * WARP_LIST_BYTES, 16);
     a.sm_text = take(2 * a.text_buf, 128);
-    a.sm_queue = take(a.qcap * 4, 16);
+    a.sm_queue = take(nw * WARP_QUEUE * 6, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
     a.sm_coop = 0;   // warp-wide bitsets live in global scratch (coop_g)
