@@ -181,6 +181,13 @@ int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64
 int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
                     uint64_t cap, uint64_t *counts, uint64_t *total, void *stream);
 
+/* Launch shape of batches on this context: `threads` (128 or 256) and
+ * `tile` (multiple of 4096, at most 32768) of *p are used, other fields are
+ * ignored; 0 or a NULL p restores the defaults (256, 16384). Per-machine
+ * parameters (prefix depth, settling) still come from pfsm_set_params. The
+ * autotuner sets this. Errors: E_INVAL. */
+int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p);
+
 /* Asynchronous form of pfsm_scan_batch: enqueues the batch on `stream` and
  * returns. status_dev (device, k + 2 uint64) receives, when the stream
  * reaches it: [0] total matches, [1] error bits (as pfsm_scan_async),

@@ -31,7 +31,7 @@ PFSM_E_CUDA = 6
 
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
-           "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_get_stats", "pfsm_set_timing",
+           "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
            "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc")
 
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_scan_async": [P, I32, P, U64, P, U64, P, P],
         "pfsm_scan_batch": [P, P, I32, P, U64, P, ctypes.POINTER(U64), P],
         "pfsm_scan_batch_async": [P, P, I32, P, U64, P, P],
+        "pfsm_set_batch_params": [P, ctypes.POINTER(pfsm_params)],
         "pfsm_get_stats": [P, ctypes.POINTER(pfsm_stats)],
         "pfsm_set_timing": [P, ctypes.c_int],
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
@@ -248,6 +249,16 @@ def pfsm_scan_batch_async(ctx: int, jobs: Sequence, out, status, cap: Optional[i
     _check(load_library().pfsm_scan_batch_async(ctx, arr, len(jobs), _dev_ptr(out), cap,
                                                 _dev_ptr(status), _stream_ptr(stream)),
            "pfsm_scan_batch_async")
+
+
+def pfsm_set_batch_params(ctx: int, params: Optional[dict] = None) -> None:
+    """Batch launch shape: {"threads": 128|256, "tile": 4096..32768} (None
+    restores the defaults)."""
+    p = None
+    if params is not None:
+        p = pfsm_params(**{k: int(v) for k, v in params.items()})
+    _check(load_library().pfsm_set_batch_params(ctx, ctypes.byref(p) if p is not None else None),
+           "pfsm_set_batch_params")
 
 
 def pfsm_get_stats(ctx: int) -> dict:

@@ -177,8 +177,8 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     a.Wq = wq_max;
     a.stage_n = (kmask & 1) ? STAGE : 32;
     a.settle_steps = 8;
-    uint32_t tile = kBatchTile;
-    int threads = 256;
+    uint32_t tile = ctx->batch_tile ? ctx->batch_tile : kBatchTile;
+    int threads = ctx->batch_threads ? ctx->batch_threads : 256;
     uint32_t smem = 0;
     bool fit = false;
     a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
@@ -349,6 +349,17 @@ extern "C" int pfsm_scan_batch_async(pfsm_ctx *ctx, const pfsm_job *jobs, int32_
     if (cudaMemcpyAsync(status_dev, b->status, (static_cast<size_t>(k) + 2) * 8,
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return PFSM_E_CUDA;
+    return PFSM_OK;
+}
+
+extern "C" int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p) {
+    if (!ctx) return PFSM_E_INVAL;
+    const int threads = p ? p->threads : 0;
+    const int tile = p ? p->tile : 0;
+    if (threads != 0 && threads != 128 && threads != 256) return PFSM_E_INVAL;
+    if (tile != 0 && (tile < 4096 || tile > 32768 || tile % 4096)) return PFSM_E_INVAL;
+    ctx->batch_threads = threads ? threads : 256;
+    ctx->batch_tile = tile ? static_cast<uint32_t>(tile) : kBatchTile;
     return PFSM_OK;
 }
 

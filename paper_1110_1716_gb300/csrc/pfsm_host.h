@@ -87,8 +87,10 @@ struct pfsm_ctx {
     bool timing = false;
     double time_ms = 0.0;
     uint64_t time_launches = 0;
-    // batch executors, one per stream (batch.cu)
+    // batch executors, one per stream (batch.cu), and their launch shape
     std::map<cudaStream_t, pfsm::BatchState *> batch;
+    int batch_threads = 256;
+    uint32_t batch_tile = 16384;
 };
 
 namespace pfsm {

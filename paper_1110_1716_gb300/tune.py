@@ -17,7 +17,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import pfsm_get_params, pfsm_scan, pfsm_scan_async, pfsm_set_params
+from . import (pfsm_get_params, pfsm_scan, pfsm_scan_async, pfsm_scan_batch,
+               pfsm_scan_batch_async, pfsm_set_batch_params, pfsm_set_params)
 
 CACHE_PATH = os.environ.get(
     "PFSM_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json"))
@@ -120,3 +121,38 @@ def tune(ctx: int, aut: int, machine, sample_text, gpu_name: str = "", force: bo
     chosen = pfsm_get_params(ctx, aut)
     _store(key, chosen, best_ms)
     return chosen
+
+
+def tune_batch(ctx: int, jobs, reps: int = 2, stream=None) -> dict:
+    """Pick the batch launch shape (threads per CTA, tile length) for a
+    representative batch `jobs` ([(aut, text_tensor, n), ...]) by timing each
+    candidate with CUDA events; sets and returns the fastest."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    st, counts, total = pfsm_scan_batch(ctx, jobs, None, 0)
+    dev = jobs[0][1].device if jobs else torch.device("cuda")
+    out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
+    status = torch.zeros(len(jobs) + 2, dtype=torch.int64, device=dev)
+    best, best_ms = None, float("inf")
+    for threads in (128, 256):
+        for tile in (8192, 16384, 32768):
+            p = {"threads": threads, "tile": tile}
+            try:
+                pfsm_set_batch_params(ctx, p)
+            except Exception:
+                continue
+            times = []
+            for r in range(reps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pfsm_scan_batch_async(ctx, jobs, out, status, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            if ms < best_ms:
+                best, best_ms = p, ms
+    pfsm_set_batch_params(ctx, best)
+    return dict(best or {}, ms=best_ms)
