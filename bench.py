@@ -378,7 +378,7 @@ def serve_texts(w, seed=0):
 def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
     """Continuous batching under Poisson arrivals at `load` x the burst
     capacity, against the plain form (one synchronous scan per request)."""
-    from paper_1110_1716_gb300.serve import Server, replay
+    from paper_1110_1716_gb300.serve import Server
     w = W.serve_workload(seed=0, n_req=n_req)
     texts = serve_texts(w)
     nbytes = int(sum(len(t) for t in texts))
@@ -397,12 +397,11 @@ def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
         res["plain_req_per_s"] = k / plain_s
         res["plain_gbps"] = sum(len(t) for t in texts[:k]) / plain_s / 1e9
         # burst: every request at once, to find the served capacity
-        with srv:
-            t0 = time.perf_counter()
-            futs = [srv.submit(int(w.req_aut[i]), texts[i], arrival=t0) for i in range(n_req)]
-            for f in futs:
-                f.result()
-            burst_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        futs = srv.run_trace(np.zeros(n_req), w.req_aut, texts, t0=t0)
+        for f in futs:
+            f.result()
+        burst_s = time.perf_counter() - t0
         cap_rps = n_req / burst_s
         res["burst_req_per_s"] = cap_rps
         res["burst_gbps"] = nbytes / burst_s / 1e9
@@ -410,11 +409,10 @@ def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
         srv2 = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
                       max_jobs=1024)
         gaps = np.random.default_rng(1).exponential(1.0 / (load * cap_rps), size=n_req)
-        with srv2:
-            t0 = time.perf_counter()
-            futs = replay(srv2, np.cumsum(gaps), w.req_aut, texts, t0=t0)
-            m = sum(len(f.result()) for f in futs)
-            el = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        futs = srv2.run_trace(np.cumsum(gaps), w.req_aut, texts, t0=t0)
+        m = sum(len(f.result()) for f in futs)
+        el = time.perf_counter() - t0
         st = srv2.latency_stats()
         res.update({"offered_load": load, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                     "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9,
