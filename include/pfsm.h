@@ -170,9 +170,11 @@ int pfsm_scan(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
 int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
                     pfsm_match *out_dev, uint64_t cap, uint64_t *status_dev, void *stream);
 
-/* Scan k texts, each with its own automaton, in one persistent launch (the
- * regex and data partitioning of Sec. III.D combined: every (text, tile) is a
- * work item).
+/* Scan k texts, each with its own automaton, in one batch (the regex and
+ * data partitioning of Sec. III.D combined). The automata are grouped into
+ * classes (DFA or NFA, prefix-symbol width, DFA table in shared memory); each
+ * class runs one persistent kernel over work units of a few consecutive tiles
+ * of one text, and the class kernels of a batch run concurrently.
  *   jobs     host, k entries; texts are device pointers
  *   out_dev  device, room for `cap` pfsm_bmatch entries (text = job index)
  *   counts   host, k entries; receives |M| per job (may be NULL)
@@ -181,11 +183,13 @@ int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64
 int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
                     uint64_t cap, uint64_t *counts, uint64_t *total, void *stream);
 
-/* Launch shape of batches on this context: `threads` (128 or 256) and
- * `tile` (multiple of 4096, at most 32768) of *p are used, other fields are
- * ignored; 0 or a NULL p restores the defaults (256, 16384). Per-machine
- * parameters (prefix depth, settling) still come from pfsm_set_params. The
- * autotuner sets this. Errors: E_INVAL. */
+/* Launch shape of batches on this context: `threads` (128, 256 or 512 per
+ * CTA), `ctas_per_sm` (1 to 4) and `tile` (multiple of 4096, at most 32768)
+ * of *p are used, other fields are ignored. 0 in a field, or a NULL p,
+ * selects the default: 256 threads x 2 CTAs per SM for DFA classes, 512 x 1
+ * for NFA classes, tiles of 16384. Per-machine parameters (prefix depth,
+ * settling) still come from pfsm_set_params. The autotuner sets this.
+ * Errors: E_INVAL (a value outside those ranges). */
 int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p);
 
 /* Asynchronous form of pfsm_scan_batch: enqueues the batch on `stream` and
@@ -226,8 +230,9 @@ int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_t S, int32_
 int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);
 
 /* Kernel timing: when enabled, every scan records CUDA events around its
- * tile kernel on the scan's stream; pfsm_kernel_time returns the summed
- * milliseconds and launch count since the last reset. */
+ * tile kernel (a batch: around its graph) on the scan's stream;
+ * pfsm_kernel_time returns the summed milliseconds and launch count since
+ * timing was last enabled. */
 int pfsm_set_timing(pfsm_ctx *ctx, int enable);
 int pfsm_kernel_time(pfsm_ctx *ctx, double *ms, uint64_t *launches);
 

@@ -213,7 +213,29 @@ def pfsm_scan_async(ctx: int, aut: int, text, n: Optional[int], out, status,
            "pfsm_scan_async")
 
 
-def _job_array(jobs: Sequence):
+# numpy layout of pfsm_job, for building large job tables without a Python loop
+JOB_DTYPE = np.dtype([("aut", "<i4"), ("reserved", "<u4"), ("text", "<u8"), ("n", "<u8")])
+
+
+def job_table(auts, text_ptrs, lengths) -> np.ndarray:
+    """A pfsm_job table as a numpy structured array (JOB_DTYPE) from three
+    equal-length sequences: automaton ids, device text addresses, lengths.
+    The batch functions accept it in place of a list of tuples."""
+    t = np.zeros(len(auts), dtype=JOB_DTYPE)
+    t["aut"] = auts
+    t["text"] = text_ptrs
+    t["n"] = lengths
+    return t
+
+
+def _job_array(jobs):
+    """(pointer, count, keep-alive) of a job table given as a JOB_DTYPE array
+    or as a sequence of (aut, text, n) tuples."""
+    if isinstance(jobs, np.ndarray):
+        if jobs.dtype != JOB_DTYPE:
+            raise TypeError("job table must have dtype JOB_DTYPE")
+        jobs = np.ascontiguousarray(jobs)
+        return jobs.ctypes.data, len(jobs), jobs
     k = len(jobs)
     arr = (pfsm_job * max(1, k))()
     for i, (aut, text, n) in enumerate(jobs):
@@ -221,19 +243,19 @@ def _job_array(jobs: Sequence):
         arr[i].reserved = 0
         arr[i].text = text if isinstance(text, int) else _dev_ptr(text)
         arr[i].n = text.numel() if n is None else n
-    return arr
+    return ctypes.addressof(arr), k, arr
 
 
 def pfsm_scan_batch(ctx: int, jobs: Sequence, out, cap: Optional[int] = None, stream=None):
     """`jobs` = [(aut, text, n), ...] with `text` a CUDA uint8 tensor (or a
-    device address and n given); `out` CUDA int32 [cap, 4] of (text, start,
-    end, state) rows. Returns (status, per-job counts as uint64, total)."""
-    k = len(jobs)
-    arr = _job_array(jobs)
+    device address and n given), or a ``job_table``; `out` CUDA int32
+    [cap, 4] of (text, start, end, state) rows. Returns (status, per-job
+    counts as uint64, total)."""
+    ptr, k, _keep = _job_array(jobs)
     cap = (out.shape[0] if out is not None else 0) if cap is None else cap
     counts = np.zeros(max(1, k), dtype=np.uint64)
     total = ctypes.c_uint64()
-    st = load_library().pfsm_scan_batch(ctx, arr, k, _dev_ptr(out), cap, counts.ctypes.data,
+    st = load_library().pfsm_scan_batch(ctx, ptr, k, _dev_ptr(out), cap, counts.ctypes.data,
                                         ctypes.byref(total), _stream_ptr(stream))
     if st not in (PFSM_OK, PFSM_E_OVERFLOW):
         _check(st, "pfsm_scan_batch")
@@ -244,16 +266,16 @@ def pfsm_scan_batch_async(ctx: int, jobs: Sequence, out, status, cap: Optional[i
                           stream=None) -> None:
     """Enqueue a batch; `status` is a CUDA int64 tensor of len(jobs) + 2
     entries: (total, error bits, count of job 0, ...)."""
-    arr = _job_array(jobs)
+    ptr, k, _keep = _job_array(jobs)
     cap = (out.shape[0] if out is not None else 0) if cap is None else cap
-    _check(load_library().pfsm_scan_batch_async(ctx, arr, len(jobs), _dev_ptr(out), cap,
+    _check(load_library().pfsm_scan_batch_async(ctx, ptr, k, _dev_ptr(out), cap,
                                                 _dev_ptr(status), _stream_ptr(stream)),
            "pfsm_scan_batch_async")
 
 
 def pfsm_set_batch_params(ctx: int, params: Optional[dict] = None) -> None:
-    """Batch launch shape: {"threads": 128|256, "tile": 4096..32768} (None
-    restores the defaults)."""
+    """Batch launch shape: {"threads": 0|128|256|512, "ctas_per_sm": 0..4,
+    "tile": 4096..32768}; 0 (or None for all) selects the per-class defaults."""
     p = None
     if params is not None:
         p = pfsm_params(**{k: int(v) for k, v in params.items()})

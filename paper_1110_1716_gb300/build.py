@@ -34,7 +34,8 @@ def _newest(paths):
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+               glob.glob(os.path.join(INCLUDE, "*.h")))
     os.makedirs(BUILD, exist_ok=True)
     hdr_time = _newest(headers + [__file__])
     jobs = []

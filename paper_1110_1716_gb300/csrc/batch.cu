@@ -1,18 +1,22 @@
-// Batched scans: many texts, each with its own machine, in one persistent
-// launch. This combines the two partitionings of Sec. III.D: the set of
-// machines is split across texts (regex partitioning) and every text is cut
-// into tiles (data partitioning); every (text, tile) pair is one work item
-// pulled by persistent CTAs from a global counter.
+// Batched scans: many texts, each with its own machine. This combines the
+// two partitionings of Sec. III.D: the set of machines is split across texts
+// (regex partitioning) and every text is cut into tiles (data partitioning).
 //
-// The launch sequence (counter and status resets, the persistent kernel, the
-// carry kernel) is captured once per stream and layout as a CUDA graph and
-// replayed for every batch; the per-batch job table, machine table and
-// kernel arguments are copied to a fixed device block before each replay.
+// The machines of a batch are grouped into classes, one specialised
+// persistent kernel each (batch_kernels.cu). Every class has a fixed launch
+// shape per context (threads, CTAs, shared-memory layout with a table arena
+// of fixed size), so the launch sequence of a batch depends only on which
+// classes it contains: counter and status resets, one branch per class
+// (the class kernels run side by side), then the DFA carry kernel. That
+// sequence is captured once per stream and class set as a CUDA graph and
+// replayed; the per-batch argument blocks, job table and machine table are
+// copied to a fixed device block before each replay.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "pfsm_host.h"
@@ -21,31 +25,49 @@ namespace pfsm {
 
 constexpr uint32_t kBatchTile = 16384;
 constexpr uint32_t kBatchHalo = 2048;
-constexpr uint32_t kBatchTabMax = 32768;   // DFA tables up to this size go to smem
+constexpr uint32_t kMinArena = 8192;     // smallest table arena worth a class shape
+constexpr int kUnitTilesMax = 8;        // tiles per work unit, at most
+constexpr int kCarryCtr = 15;           // counter word holding the carry count
+
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t gen = 0;
+};
 
 struct BatchState {
-    cudaStream_t capture = nullptr;   // private stream used to capture the graph
+    cudaStream_t capture = nullptr;   // private stream used to capture the graphs
+    cudaStream_t aux[kBatchClasses] = {};   // one capture branch per class
+    cudaEvent_t fork = nullptr, join[kBatchClasses] = {};
     size_t cap_jobs = 0, cap_machs = 0;
     size_t off_jobs = 0, off_machs = 0, block_bytes = 0;
-    uint8_t *dev = nullptr;           // BatchArgs | jobs | machines
+    uint8_t *dev = nullptr;           // BatchArgs[kBatchClasses] | jobs | machines
     uint8_t *host = nullptr;          // pinned staging of the same layout
-    uint32_t *ctr = nullptr;          // device: [0] item counter, [1] carry count
+    uint32_t *ctr = nullptr;          // device: [c] unit counter of class c, [15] carry count
     unsigned long long *status = nullptr;       // device: total, errors, per-job counts
     unsigned long long *host_status = nullptr;  // pinned copy of status
     uint32_t *carry = nullptr;
-    uint32_t *coop = nullptr;         // warp-wide NFA bitsets
+    uint32_t *coop = nullptr;         // warp-wide NFA bitsets of every NFA class
     size_t coop_words = 0;
     cudaEvent_t staged = nullptr;     // previous staging copy has been consumed
     bool staged_pending = false;
-    cudaGraphExec_t exec = nullptr;
-    uint32_t g_smem = 0;
-    int g_threads = 0, g_grid = 0;
+    std::map<uint32_t, BatchGraph> graphs;   // by class mask
 };
+
+static void drop_graphs(BatchState *b) {
+    for (auto &kv : b->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    b->graphs.clear();
+}
 
 static void state_free(BatchState *b) {
     if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
+    drop_graphs(b);
     if (b->staged) cudaEventDestroy(b->staged);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (b->join[c]) cudaEventDestroy(b->join[c]);
+        if (b->aux[c]) cudaStreamDestroy(b->aux[c]);
+    }
     if (b->capture) cudaStreamDestroy(b->capture);
     cudaFree(b->dev);
     cudaFree(b->ctr);
@@ -65,8 +87,13 @@ static int state_reserve(pfsm_ctx *ctx, cudaStream_t s, size_t njobs, size_t nma
     BatchState *&b = ctx->batch[s];
     if (!b) {
         b = new BatchState();
-        if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) {
+        bool ok = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int c = 0; ok && c < kBatchClasses; ++c)
+            ok = cudaStreamCreateWithFlags(&b->aux[c], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
             return PFSM_E_CUDA;
         }
@@ -79,10 +106,7 @@ static int state_reserve(pfsm_ctx *ctx, cudaStream_t s, size_t njobs, size_t nma
     if (b->staged_pending) cudaEventSynchronize(b->staged);
     b->staged_pending = false;
     cudaStreamSynchronize(s);
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-    }
+    drop_graphs(b);
     cudaFree(b->dev);
     cudaFree(b->ctr);
     cudaFreeHost(b->host);
@@ -93,10 +117,10 @@ static int state_reserve(pfsm_ctx *ctx, cudaStream_t s, size_t njobs, size_t nma
     b->host_status = nullptr;
     b->cap_jobs = std::max<size_t>(std::max<size_t>(njobs, 2 * b->cap_jobs), 256);
     b->cap_machs = std::max<size_t>(std::max<size_t>(nmachs, 2 * b->cap_machs), 16);
-    b->off_jobs = align256(sizeof(BatchArgs));
+    b->off_jobs = align256(kBatchClasses * sizeof(BatchArgs));
     b->off_machs = align256(b->off_jobs + b->cap_jobs * sizeof(BatchJob));
     b->block_bytes = align256(b->off_machs + b->cap_machs * sizeof(DevMachine));
-    const size_t ctr_bytes = 256 + (b->cap_jobs + 2) * 8 + static_cast<size_t>(kCarryCap) * 16;
+    const size_t ctr_bytes = 256 + align256((b->cap_jobs + 2) * 8) + static_cast<size_t>(kCarryCap) * 16;
     if (cudaMalloc(&b->dev, b->block_bytes) != cudaSuccess ||
         cudaMalloc(&b->ctr, ctr_bytes) != cudaSuccess ||
         cudaMallocHost(&b->host, b->block_bytes) != cudaSuccess ||
@@ -112,159 +136,230 @@ static int state_reserve(pfsm_ctx *ctx, cudaStream_t s, size_t njobs, size_t nma
     return PFSM_OK;
 }
 
+// The launch shape of class `cls`: threads and CTAs per SM from the batch
+// parameters (or the class default), everything but the table arena laid out
+// by layout_smem, and the arena taking the rest of the CTA's share of the
+// SM's shared memory. Shrinks the match staging, then the tile, then the
+// thread count until an arena of kMinArena fits.
+static int class_shape(pfsm_ctx *ctx, int cls) {
+    BatchShape &sh = ctx->batch_shape[cls];
+    if (sh.ready) return PFSM_OK;
+    const int kind = cls >= 6 ? 1 : 0;
+    int threads = ctx->batch_threads ? ctx->batch_threads : (kind ? 512 : 256);
+    const int ctas = ctx->batch_ctas ? ctx->batch_ctas : (kind ? 1 : 2);
+    uint32_t tile = ctx->batch_tile ? ctx->batch_tile : kBatchTile;
+    ScanArgs a;
+    memset(&a, 0, sizeof(a));
+    a.stage_n = kind ? 32 : STAGE;
+    const uint32_t share = ctx->smem_sm / static_cast<uint32_t>(ctas);
+    const uint32_t budget =
+        std::min<uint32_t>(kSmemMax, share > ctx->smem_rsv ? share - ctx->smem_rsv : 0) - kSmemStatic;
+    uint32_t base = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        a.tile = tile;
+        a.halo = kBatchHalo;
+        a.text_buf = (tile + kBatchHalo + 32 + 127) & ~127u;
+        a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
+        base = layout_smem(a, kind ? 2 : 1, threads, SmemNeed{0u, 0u, 0u, 0u, 0u});
+        if (base + kMinArena <= budget) break;
+        if (a.stage_n > 32) a.stage_n = 32;
+        else if (tile > 8192) tile = 8192;
+        else if (threads > 128) threads /= 2;
+        else return PFSM_E_INVAL;
+    }
+    if (base + kMinArena > budget) return PFSM_E_INVAL;
+    const uint32_t arena = (budget - base) & ~15u;
+    const uint32_t smem = base + arena;
+    const int occ = max_units_ctas_per_sm(cls, threads, smem);
+    if (occ <= 0) return PFSM_E_INVAL;
+    sh.threads = threads;
+    sh.grid = ctx->nsm * std::min(occ, ctas);
+    sh.smem = smem;
+    sh.arena = arena;
+    sh.layout = a;
+    sh.ready = true;
+    return PFSM_OK;
+}
+
+// Chooses which of a machine's tables go to the table arena (in order of
+// use per start: survival bitmap, prefix table, DFA table, NFA band rows,
+// NFA prefix records) and returns the machine's class. With a deep bitmap
+// in global memory few starts reach the prefix table, so the prefix table
+// and records stay in global memory and leave the arena to the rest.
+static int place_tables(const Machine &m, uint32_t arena, DevMachine &d) {
+    d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = kNotStaged;
+    d.settle = m.params.settle > 0 ? m.params.settle : 0;
+    uint32_t used = 0;
+    auto take = [&](uint32_t bytes) {
+        const uint32_t at = (used + 15) & ~15u;
+        if (bytes == 0 || at + bytes > arena) return kNotStaged;
+        used = at + bytes;
+        return at;
+    };
+    const bool deep = !m.surv2.empty();
+    if (!m.surv.empty()) d.a_surv = take(static_cast<uint32_t>(m.surv.size() * 4));
+    if (!deep && d.memo_n > 0) d.a_memo = take(((d.memo_n + 1) / 2) * 4);
+    if (m.kind == 0) {
+        d.a_tab = take(((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4);
+    } else {
+        if (!m.band.empty()) d.a_band = take(static_cast<uint32_t>(m.band.size() * 4));
+        if (!deep && !m.pool.empty()) d.a_pool = take(static_cast<uint32_t>(m.pool.size() * 4));
+    }
+    return batch_class(m.kind, m.sbits, m.k, m.kind == 0 && d.a_tab != kNotStaged);
+}
+
 struct BatchPlan {
     std::vector<BatchJob> jobs;
     std::vector<DevMachine> machs;
-    ScanArgs sa{};
-    uint32_t nitems = 0;
-    int threads = 256, grid = 1;
-    uint32_t smem = 0;
+    uint32_t mask = 0;                      // classes with work
+    uint32_t job_lo[kBatchClasses] = {}, job_hi[kBatchClasses] = {};
+    uint32_t nunits[kBatchClasses] = {}, unit_tiles[kBatchClasses] = {};
+    int32_t wq[kBatchClasses] = {};         // NFA: widest state bitset (words)
 };
 
-// Validate the jobs, make their machines resident and lay out the launch.
+// Validate the jobs, make their machines resident, classify them and cut
+// every class's texts into work units.
 static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan &pl) {
     ctx->epoch++;
+    // machine slot of every job (slots numbered in order of first use)
     std::map<int, uint32_t> slot_of;
     std::vector<int> ids;
+    std::vector<uint32_t> job_slot(static_cast<size_t>(k));
+    int last_aut = 0;
+    uint32_t last_slot = 0xFFFFFFFFu;
     for (int32_t i = 0; i < k; ++i) {
         const pfsm_job &j = jobs[i];
         if (j.reserved != 0 || j.n >= (1ull << 32) || (j.n > 0 && !j.text)) return PFSM_E_INVAL;
-        auto it = ctx->machines.find(j.aut);
-        if (it == ctx->machines.end()) return PFSM_E_NOENT;
-        if (!slot_of.count(j.aut)) {
-            slot_of[j.aut] = static_cast<uint32_t>(ids.size());
-            ids.push_back(j.aut);
-            it->second.pin = ctx->epoch;
+        if (last_slot == 0xFFFFFFFFu || j.aut != last_aut) {
+            auto f = slot_of.find(j.aut);
+            if (f == slot_of.end()) {
+                auto it = ctx->machines.find(j.aut);
+                if (it == ctx->machines.end()) return PFSM_E_NOENT;
+                it->second.pin = ctx->epoch;
+                f = slot_of.emplace(j.aut, static_cast<uint32_t>(ids.size())).first;
+                ids.push_back(j.aut);
+            }
+            last_aut = j.aut;
+            last_slot = f->second;
         }
+        job_slot[i] = last_slot;
     }
+    if (ids.size() >= (1u << 24)) return PFSM_E_INVAL;
     for (int id : ids) {
         int st = make_resident(ctx, id, ctx->machines[id]);
         if (st) return st;
     }
-    uint32_t memo_max = 0, tab_max = 0, band_max = 0, pool_max = 0, surv_max = 0;
-    int32_t wq_max = 0;
-    int kmask = 0;
-    for (int id : ids) {
-        Machine &m = ctx->machines[id];
+    // the DFA classes share one shape (threads, arena), as do the NFA classes
+    int st = class_shape(ctx, 0);
+    if (!st) st = class_shape(ctx, 6);
+    if (st) return st;
+    for (int c = 1; c < kBatchClasses && !st; ++c)
+        if (!ctx->batch_shape[c].ready) st = class_shape(ctx, c);
+    if (st) return st;
+    std::vector<int> cls_of(ids.size());
+    for (size_t i = 0; i < ids.size(); ++i) {
+        Machine &m = ctx->machines[ids[i]];
         DevMachine d = m.dm;
-        const uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
-        d.tab_smem = (m.kind == 0 && tab_bytes <= kBatchTabMax) ? 1 : 0;
-        if (d.tab_smem) tab_max = std::max(tab_max, tab_bytes);
-        const uint32_t band_bytes = static_cast<uint32_t>(m.band.size() * 4);
-        const uint32_t pool_bytes = m.kind == 1 ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
-        d.band_smem = band_bytes > 0 && band_bytes <= kBatchTabMax * 2;
-        d.pool_smem = pool_bytes > 0 && pool_bytes <= kBatchTabMax * 2;
-        if (d.band_smem) band_max = std::max(band_max, band_bytes);
-        if (d.pool_smem) pool_max = std::max(pool_max, pool_bytes);
-        d.memo_smem = m.surv2.empty() && d.memo_n > 0;
-        if (d.memo_smem) memo_max = std::max(memo_max, d.memo_n);
-        if (!m.surv2.empty()) d.pool_smem = 0;
-        surv_max = std::max(surv_max, static_cast<uint32_t>(m.surv.size() * 4));
-        if (m.kind == 1) wq_max = std::max(wq_max, d.Wq);
-        kmask |= m.kind == 0 ? 1 : 2;
+        const uint32_t arena = ctx->batch_shape[m.kind == 1 ? 6 : 0].arena;
+        cls_of[i] = place_tables(m, arena, d);
+        if (m.kind == 1) pl.wq[cls_of[i]] = std::max(pl.wq[cls_of[i]], d.Wq);
         pl.machs.push_back(d);
     }
-    // jobs ordered by machine, so that consecutive items share tables
-    std::vector<int32_t> order(k);
-    for (int32_t i = 0; i < k; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return slot_of[jobs[x].aut] < slot_of[jobs[y].aut];
-    });
-    // launch geometry: shrink until the layout fits one CTA's shared memory
-    ScanArgs &a = pl.sa;
-    memset(&a, 0, sizeof(a));
-    a.memo_n = memo_max;
-    a.Wq = wq_max;
-    a.stage_n = (kmask & 1) ? STAGE : 32;
-    a.settle_steps = 8;
-    uint32_t tile = ctx->batch_tile ? ctx->batch_tile : kBatchTile;
-    int threads = ctx->batch_threads ? ctx->batch_threads : 256;
-    uint32_t smem = 0;
-    bool fit = false;
-    a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
-    for (int attempt = 0; attempt < 12 && !fit; ++attempt) {
-        a.tile = tile;
-        a.halo = kBatchHalo;
-        a.text_buf = (tile + kBatchHalo + 16 + 127) & ~127u;
-        const SmemNeed need{memo_max ? ((memo_max + 1) / 2) * 4 + 4 : 0u, tab_max, band_max,
-                            pool_max, surv_max};
-        smem = layout_smem(a, kmask, threads, need);
-        if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
-        if (a.stage_n > 32) {
-            a.stage_n = 32;
-        } else if (pool_max) {
-            pool_max = 0;
-            for (auto &d : pl.machs) d.pool_smem = 0;
-        } else if (tile > 8192) {
-            tile = 8192;
-        } else if (band_max) {
-            band_max = 0;
-            for (auto &d : pl.machs) d.band_smem = 0;
-        } else if (tab_max) {
-            tab_max = 0;
-            for (auto &d : pl.machs) d.tab_smem = 0;
-        } else if (threads > 128) {
-            threads /= 2;
-            a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
-        } else {
-            break;
-        }
+    // jobs grouped by class, then by machine, so that consecutive units share
+    // tables; a sort of packed keys (class, slot, job index) keeps the order
+    // of the caller's jobs within a machine
+    std::vector<uint64_t> key(static_cast<size_t>(k));
+    for (int32_t i = 0; i < k; ++i)
+        key[i] = (static_cast<uint64_t>(cls_of[job_slot[i]]) << 56) |
+                 (static_cast<uint64_t>(job_slot[i]) << 32) | static_cast<uint32_t>(i);
+    std::sort(key.begin(), key.end());
+    uint64_t tiles_of[kBatchClasses] = {};
+    for (int32_t i = 0; i < k; ++i) {
+        const int c = cls_of[job_slot[i]];
+        tiles_of[c] += (jobs[i].n + ctx->batch_shape[c].layout.tile - 1) / ctx->batch_shape[c].layout.tile;
     }
-    if (!fit) return PFSM_E_INVAL;
-    uint32_t item = 0;
-    for (int32_t x : order) {
+    // units of up to kUnitTilesMax tiles, fewer when a class has too little
+    // work for about four units per CTA
+    for (int c = 0; c < kBatchClasses; ++c) {
+        const uint64_t per = tiles_of[c] / (4ull * std::max(1, ctx->batch_shape[c].grid));
+        pl.unit_tiles[c] = static_cast<uint32_t>(std::min<uint64_t>(kUnitTilesMax, std::max<uint64_t>(1, per)));
+    }
+    int cur = -1;
+    pl.jobs.reserve(static_cast<size_t>(k));
+    for (int32_t r = 0; r < k; ++r) {
+        const int32_t x = static_cast<int32_t>(key[r] & 0xFFFFFFFFu);
         const pfsm_job &j = jobs[x];
+        const uint32_t slot = job_slot[x];
+        const int c = cls_of[slot];
+        if (c != cur) {
+            if (cur >= 0) pl.job_hi[cur] = static_cast<uint32_t>(pl.jobs.size());
+            pl.job_lo[c] = static_cast<uint32_t>(pl.jobs.size());
+            cur = c;
+        }
+        const uint32_t tile = ctx->batch_shape[c].layout.tile;
         BatchJob b{};
         b.text = j.text;
         b.n = static_cast<uint32_t>(j.n);
-        b.mach = slot_of[j.aut];
+        b.mach = slot;
         b.orig = static_cast<uint32_t>(x);
-        b.tile_begin = item;
-        const uint64_t tiles = (j.n + a.tile - 1) / a.tile;
-        if (item + tiles >= (1ull << 32)) return PFSM_E_INVAL;
-        item += static_cast<uint32_t>(tiles);
+        b.ntiles = static_cast<uint32_t>((j.n + tile - 1) / tile);
+        b.unit_begin = pl.nunits[c];
+        const uint64_t units = (b.ntiles + pl.unit_tiles[c] - 1) / pl.unit_tiles[c];
+        if (pl.nunits[c] + units >= (1ull << 32)) return PFSM_E_INVAL;
+        pl.nunits[c] += static_cast<uint32_t>(units);
         pl.jobs.push_back(b);
     }
-    pl.nitems = item;
-    int occ = max_batch_ctas_per_sm(threads, smem);
-    if (occ <= 0) return PFSM_E_INVAL;
-    pl.threads = threads;
-    pl.smem = smem;
-    pl.grid = ctx->nsm * occ;
+    if (cur >= 0) pl.job_hi[cur] = static_cast<uint32_t>(pl.jobs.size());
+    for (int c = 0; c < kBatchClasses; ++c)
+        if (pl.nunits[c] > 0) pl.mask |= 1u << c;
     return PFSM_OK;
 }
 
-static int capture_graph(BatchState *b, const BatchPlan &pl, int nsm) {
-    if (b->exec && b->g_smem == pl.smem && b->g_threads == pl.threads && b->g_grid == pl.grid)
+// The graph of one class set: resets, one branch per class, the carry kernel.
+static int graph_for(pfsm_ctx *ctx, BatchState *b, uint32_t mask, cudaGraphExec_t *out) {
+    BatchGraph &bg = b->graphs[mask];
+    if (bg.exec && bg.gen == ctx->batch_gen) {
+        *out = bg.exec;
         return PFSM_OK;
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+    }
+    if (bg.exec) {
+        cudaGraphExecDestroy(bg.exec);
+        bg.exec = nullptr;
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return PFSM_E_CUDA;
     const BatchArgs *dargs = reinterpret_cast<const BatchArgs *>(b->dev);
-    cudaMemsetAsync(b->ctr, 0, 8, b->capture);
-    cudaMemsetAsync(b->status, 0, (b->cap_jobs + 2) * 8, b->capture);
-    cudaError_t e = launch_batch(dargs, pl.threads, pl.grid, pl.smem, b->capture);
-    if (e == cudaSuccess) e = launch_carry_batch(dargs, 2 * nsm, b->capture);
+    cudaError_t e = cudaMemsetAsync(b->ctr, 0, 256, b->capture);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, (b->cap_jobs + 2) * 8, b->capture);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->capture);
+    int carry_cls = -1;
+    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c) {
+        if (!(mask & (1u << c))) continue;
+        if (c < 6 && carry_cls < 0) carry_cls = c;
+        const BatchShape &sh = ctx->batch_shape[c];
+        e = cudaStreamWaitEvent(b->aux[c], b->fork, 0);
+        if (e == cudaSuccess) e = launch_units(c, dargs + c, sh.threads, sh.grid, sh.smem, b->aux[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[c], b->aux[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->join[c], 0);
+    }
+    if (e == cudaSuccess && carry_cls >= 0)
+        e = launch_carry_batch(dargs + carry_cls, 2 * ctx->nsm, b->capture);
     cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         return PFSM_E_CUDA;
     }
-    e = cudaGraphInstantiate(&b->exec, g, 0);
+    e = cudaGraphInstantiate(&bg.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        b->exec = nullptr;
+        bg.exec = nullptr;
         return PFSM_E_CUDA;
     }
-    b->g_smem = pl.smem;
-    b->g_threads = pl.threads;
-    b->g_grid = pl.grid;
+    bg.gen = ctx->batch_gen;
+    *out = bg.exec;
     return PFSM_OK;
 }
 
@@ -283,27 +378,41 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
     st = state_reserve(ctx, s, std::max<size_t>(1, pl.jobs.size()), std::max<size_t>(1, pl.machs.size()), &b);
     if (st) return st;
     if (b->staged_pending) cudaEventSynchronize(b->staged);   // staging buffer is free again
-    // kernel arguments
-    BatchArgs args{};
-    args.sa = pl.sa;
-    args.sa.out = reinterpret_cast<uint32_t *>(out);
-    args.sa.cap = cap;
-    args.sa.status = b->status;
-    args.sa.carry = b->carry;
-    args.sa.carry_n = b->ctr + 1;
-    args.sa.carry_cap = kCarryCap;
-    args.nitems = pl.nitems;
-    args.njobs = static_cast<uint32_t>(pl.jobs.size());
-    args.item_counter = b->ctr;
-    args.jobs = reinterpret_cast<const BatchJob *>(b->dev + b->off_jobs);
-    args.machs = reinterpret_cast<const DevMachine *>(b->dev + b->off_machs);
-    args.job_counts = b->status + 2;
-    if (pl.sa.Wq > 0) {
-        const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * pl.sa.Wq;
-        if (ensure_words(&b->coop, &b->coop_words, need)) return PFSM_E_NOMEM;
-        args.sa.coop_g = b->coop;
+    // warp bitsets of the NFA classes, one region per class
+    size_t coop_need = 0, coop_off[kBatchClasses] = {};
+    for (int c = 6; c < kBatchClasses; ++c) {
+        if (!(pl.mask & (1u << c)) || pl.wq[c] <= 0) continue;
+        const BatchShape &sh = ctx->batch_shape[c];
+        coop_off[c] = coop_need;
+        coop_need += static_cast<size_t>(sh.grid) * (sh.threads / 32) * 2 * pl.wq[c];
     }
-    memcpy(b->host, &args, sizeof(args));
+    if (coop_need && ensure_words(&b->coop, &b->coop_words, coop_need)) return PFSM_E_NOMEM;
+    BatchArgs args[kBatchClasses];
+    memset(args, 0, sizeof(args));
+    for (int c = 0; c < kBatchClasses; ++c) {
+        if (!(pl.mask & (1u << c))) continue;
+        const BatchShape &sh = ctx->batch_shape[c];
+        BatchArgs &A = args[c];
+        A.sa = sh.layout;
+        A.sa.out = reinterpret_cast<uint32_t *>(out);
+        A.sa.cap = cap;
+        A.sa.status = b->status;
+        A.sa.carry = b->carry;
+        A.sa.carry_n = b->ctr + kCarryCtr;
+        A.sa.carry_cap = kCarryCap;
+        A.sa.Wq = pl.wq[c];
+        A.sa.coop_g = (c >= 6 && pl.wq[c] > 0) ? b->coop + coop_off[c] : nullptr;
+        A.nunits = pl.nunits[c];
+        A.job_lo = pl.job_lo[c];
+        A.job_hi = pl.job_hi[c];
+        A.unit_tiles = pl.unit_tiles[c];
+        A.sm_arena = sh.smem - sh.arena;
+        A.unit_counter = b->ctr + c;
+        A.jobs = reinterpret_cast<const BatchJob *>(b->dev + b->off_jobs);
+        A.machs = reinterpret_cast<const DevMachine *>(b->dev + b->off_machs);
+        A.job_counts = b->status + 2;
+    }
+    memcpy(b->host, args, sizeof(args));
     if (!pl.jobs.empty())
         memcpy(b->host + b->off_jobs, pl.jobs.data(), pl.jobs.size() * sizeof(BatchJob));
     if (!pl.machs.empty())
@@ -313,7 +422,8 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
         return PFSM_E_CUDA;
     cudaEventRecord(b->staged, s);
     b->staged_pending = true;
-    st = capture_graph(b, pl, ctx->nsm);
+    cudaGraphExec_t exec = nullptr;
+    st = graph_for(ctx, b, pl.mask, &exec);
     if (st) return st;
     int ev = -1;
     Slot *slot = ctx->timing ? get_slot(ctx, s) : nullptr;
@@ -322,7 +432,7 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
         ev = slot->ev_head;
         cudaEventRecord(slot->ev[2 * ev], s);
     }
-    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return PFSM_E_CUDA;
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) return PFSM_E_CUDA;
     if (slot) {
         cudaEventRecord(slot->ev[2 * ev + 1], s);
         slot->ev_head = (slot->ev_head + 1) % kEventRing;
@@ -356,10 +466,15 @@ extern "C" int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p) {
     if (!ctx) return PFSM_E_INVAL;
     const int threads = p ? p->threads : 0;
     const int tile = p ? p->tile : 0;
-    if (threads != 0 && threads != 128 && threads != 256) return PFSM_E_INVAL;
+    const int ctas = p ? p->ctas_per_sm : 0;
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512) return PFSM_E_INVAL;
     if (tile != 0 && (tile < 4096 || tile > 32768 || tile % 4096)) return PFSM_E_INVAL;
-    ctx->batch_threads = threads ? threads : 256;
+    if (ctas < 0 || ctas > 4) return PFSM_E_INVAL;
+    ctx->batch_threads = threads;
+    ctx->batch_ctas = ctas;
     ctx->batch_tile = tile ? static_cast<uint32_t>(tile) : kBatchTile;
+    for (int c = 0; c < kBatchClasses; ++c) ctx->batch_shape[c].ready = false;
+    ctx->batch_gen++;   // captured graphs hold the old shapes
     return PFSM_OK;
 }
 

@@ -1,0 +1,283 @@
+// Batch scan kernels for sm_103a: many texts, each with its own machine.
+//
+// The machines of a batch are grouped into classes (kind, prefix-symbol
+// width, DFA table in shared memory) and every class runs its own
+// specialised persistent kernel, so each keeps the register budget of the
+// matching single-text kernel. The class kernels of one batch run side by
+// side on the device (parallel branches of one CUDA graph).
+//
+// Inside a class, the texts' tiles are cut into work units of a few
+// consecutive tiles of one text; persistent CTAs pull units from the class's
+// counter. While consecutive tiles belong to the same text, a CTA keeps its
+// per-warp instance queues and staged matches across the tile boundary
+// (queued instances read the earlier bytes from global memory), and drains
+// them only when the text changes: this combines the regex partitioning of
+// Sec. III.D (machines split across texts) with the data partitioning of the
+// same section (texts cut into tiles).
+//
+// Each machine's tables (survival bitmap, prefix table, DFA table, NFA band
+// rows and prefix records) are copied into a shared-memory table arena when
+// a CTA moves to that machine, at offsets chosen on the host.
+#include "scan_device.cuh"
+
+namespace pfsm {
+
+// One claimed tile of a unit.
+struct UnitDesc {
+    const uint8_t *text;
+    uint32_t valid, job, orig, mach, b, len, n, sh, parity;
+};
+
+// Last job of [lo, hi) whose unit_begin <= u.
+__device__ __forceinline__ uint32_t find_unit_job(const BatchJob *jobs, uint32_t lo, uint32_t hi,
+                                                  uint32_t u) {
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].unit_begin <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ MView mview_of(const DevMachine &m) {
+    return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.surv2_m, m.surv2, m.dtab, m.off, m.tgt};
+}
+
+// Copies `words` 32-bit words (16-byte aligned source and destination).
+__device__ __forceinline__ void stage_words(uint8_t *dst, const void *src, uint32_t words, int tid,
+                                            int nt) {
+    const uint32_t quads = words >> 2;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (uint32_t i = tid; i < quads; i += nt) d4[i] = __ldg(s4 + i);
+    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d1 = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = 4 * quads + tid; i < words; i += nt) d1[i] = __ldg(s1 + i);
+}
+
+template <int KIND, int SB, bool TAB>
+__global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict__ gargs) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ BatchArgs A;
+    __shared__ UnitDesc desc[2];
+    __shared__ uint32_t tma_uses[2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int NT = blockDim.x;
+    if (tid == 0) {
+        A = *gargs;
+        tma_uses[0] = tma_uses[1] = 0;
+    }
+    __syncthreads();
+    const Smem sm = smem_regions(smem, A.sa, wid);
+    Misc *misc = sm.misc;
+    uint8_t *text_sm = smem + A.sa.sm_text;
+    uint8_t *arena = smem + A.sm_arena;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const OView ov{A.sa.out, A.sa.cap, A.sa.status, A.job_counts, A.sa.carry, A.sa.carry_n,
+                   A.sa.carry_cap, A.sa.stage_n};
+    if (tid == 0) {
+        mbar_init(&misc->bar[0], 1);
+        mbar_init(&misc->bar[1], 1);
+        misc->q_count = 0;
+        misc->q_head = 0;
+        misc->abort = 0;
+        fence_mbar_init();
+    }
+
+    // thread 0's cursor: the tiles [cur_tile, cur_end) of job cur_job remain
+    // in its current unit
+    uint32_t cur_job = 0, cur_tile = 0, cur_end = 0;
+    // thread 0: take the next tile (claiming a new unit when the current one
+    // is used up) and start its copy into buffer `buf`
+    auto claim = [&](int buf) {
+        UnitDesc &d = desc[buf];
+        if (cur_tile >= cur_end) {
+            const uint32_t u = atomicAdd(A.unit_counter, 1u);
+            if (u >= A.nunits) {
+                d.valid = 0;
+                return;
+            }
+            cur_job = find_unit_job(A.jobs, A.job_lo, A.job_hi, u);
+            const BatchJob &J = A.jobs[cur_job];
+            cur_tile = (u - J.unit_begin) * A.unit_tiles;
+            cur_end = min(cur_tile + A.unit_tiles, J.ntiles);
+        }
+        const BatchJob &J = A.jobs[cur_job];
+        d.valid = 1;
+        d.job = cur_job;
+        d.text = J.text;
+        d.n = J.n;
+        d.orig = J.orig;
+        d.mach = J.mach;
+        d.b = cur_tile * A.sa.tile;
+        ++cur_tile;
+        d.len = min(A.sa.tile + A.sa.halo, d.n - d.b);
+        // one bulk copy from the 16-byte boundary at or below the tile's
+        // first byte (the block it starts in lies in the text's page)
+        const uintptr_t src = reinterpret_cast<uintptr_t>(d.text) + d.b;
+        d.sh = static_cast<uint32_t>(src & 15u);
+        const uint32_t bytes = (d.sh + d.len + 15) & ~15u;
+        d.parity = tma_uses[buf] & 1;
+        tma_uses[buf]++;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&misc->bar[buf], bytes);
+        tma_load_1d(text_sm + buf * A.sa.text_buf, reinterpret_cast<const void *>(src - d.sh), bytes,
+                    &misc->bar[buf], pol_stream);
+    };
+    if (tid == 0) claim(0);
+    __syncthreads();
+
+    uint32_t sn = 0;
+    uint32_t wq_n = 0;
+    bool bad_symbol = false;
+    uint32_t cur_mach = 0xFFFFFFFFu;
+    Smem smi = sm;
+    for (uint32_t it = 0;; ++it) {
+        const int buf = it & 1;
+        const UnitDesc d = desc[buf];
+        if (!d.valid) break;
+        if (tid == 0) claim(buf ^ 1);   // prefetch the next tile
+        const DevMachine &M = A.machs[d.mach];
+        if (d.mach != cur_mach) {
+            // a new machine: every warp drained the previous one's queues and
+            // passed the barrier that ended its last tile
+            if (M.a_surv != kNotStaged) stage_words(arena + M.a_surv, M.surv, M.surv_words, tid, NT);
+            if (M.a_memo != kNotStaged) stage_words(arena + M.a_memo, M.memo, (M.memo_n + 1) / 2, tid, NT);
+            if (TAB) stage_words(arena + M.a_tab, M.dtab, (static_cast<uint32_t>(M.Q) * M.S + 1) / 2, tid, NT);
+            if (KIND == 1) {
+                if (M.a_band != kNotStaged)
+                    stage_words(arena + M.a_band, M.band, static_cast<uint32_t>(M.Q + (M.Q + 31) / 32), tid, NT);
+                if (M.a_pool != kNotStaged) stage_words(arena + M.a_pool, M.pool, M.pool_n, tid, NT);
+            }
+            smi.surv = M.a_surv != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_surv) : nullptr;
+            smi.memo = M.a_memo != kNotStaged ? reinterpret_cast<const uint16_t *>(arena + M.a_memo) : M.memo;
+            smi.tab = TAB ? reinterpret_cast<const uint16_t *>(arena + M.a_tab) : nullptr;
+            smi.band = M.a_band != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_band) : M.band;
+            smi.pool = M.a_pool != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_pool) : M.pool;
+            cur_mach = d.mach;
+        }
+        uint8_t *tsm = text_sm + buf * A.sa.text_buf;
+        if (!mbar_wait_bounded(&misc->bar[buf], d.parity)) misc->abort = 1;
+        if (d.sh) realign_tile(tsm, d.sh, d.len, tid, NT);   // ends with a barrier
+        else __syncthreads();
+        if (misc->abort) break;
+        const MView mv = mview_of(M);
+        const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
+        const uint32_t own_end = min(d.b + A.sa.tile, d.n);
+        process_tile<KIND, SB, TAB, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
+                                       static_cast<uint32_t>(M.settle));
+        // the next tile continues this text: queued instances and staged
+        // matches stay; otherwise drain and flush them now (per-text counts
+        // need every staged match of a flush to belong to one text)
+        const bool same_text = desc[buf ^ 1].valid && desc[buf ^ 1].job == d.job;
+        if (!same_text) {
+            drain<KIND, TAB, 4>(ov, mv, tv, smi, wq_n, sn, lane, pol_keep);
+            stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
+        }
+        // the staged buffer is refilled two tiles on: every warp must be done
+        __syncthreads();
+    }
+    if (bad_symbol) atomicOr(&A.sa.status[1], ERR_SYMBOL);
+    if (tid == 0 && misc->abort) {
+        atomicOr(&A.sa.status[1], ERR_TIMEOUT);
+        // a copy may still be in flight: wait for it (bounded) before exit
+        mbar_wait_bounded(&misc->bar[0], 0);
+        mbar_wait_bounded(&misc->bar[1], 0);
+    }
+}
+
+// ------------------------------------------------------------ DFA carry queue
+// Batch form of the carry continuation (chained data partitioning,
+// Sec. III.D.2); entries are {job, start, pos, state} with global job indices.
+__global__ void __launch_bounds__(256) carry_batch(const BatchArgs *__restrict__ g) {
+    const uint32_t nc = min(*g->sa.carry_n, g->sa.carry_cap);
+    const uint64_t pol_keep = policy_evict_last();
+    const OView ov{g->sa.out, g->sa.cap, g->sa.status, g->job_counts, g->sa.carry,
+                   g->sa.carry_n, g->sa.carry_cap, g->sa.stage_n};
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
+         idx += gridDim.x * blockDim.x) {
+        const uint32_t *c = g->sa.carry + 4 * idx;
+        const uint32_t start = c[1];
+        uint32_t pos = c[2], s = c[3];
+        const BatchJob &J = g->jobs[c[0]];
+        const DevMachine &M = g->machs[J.mach];
+        const uint32_t S = M.S;
+        while (pos < J.n) {
+            const uint32_t ch = __ldg(J.text + pos);
+            if (ch >= S) break;
+            const uint16_t e = ldg_u16_keep(M.dtab + s * S + ch, pol_keep);
+            if (e == DEAD16) break;
+            s = e & 0x7FFFu;
+            if (e & FINAL_BIT) emit_direct<4>(ov, J.orig, start, pos, s);
+            ++pos;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host helpers
+int batch_class(int kind, int sbits, int k, bool tab_smem) {
+    const int sbi = (k > 0 && sbits == 2) ? 1 : ((k > 0 && sbits == 8) ? 2 : 0);
+    if (kind == 1) return 6 + sbi;
+    return 3 * (tab_smem ? 1 : 0) + sbi;
+}
+
+template <int KIND, int SB, bool TAB>
+static cudaError_t launch_u(const BatchArgs *dev_args, int threads, int grid, uint32_t smem,
+                            cudaStream_t s) {
+    auto k = scan_units<KIND, SB, TAB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, s>>>(dev_args);
+    return cudaGetLastError();
+}
+
+template <int KIND, int SB, bool TAB>
+static int occ_u(int threads, uint32_t smem) {
+    int nb = 0;
+    auto k = scan_units<KIND, SB, TAB>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+cudaError_t launch_units(int cls, const BatchArgs *dev_args, int threads, int grid,
+                         uint32_t smem, cudaStream_t s) {
+    switch (cls) {
+        case 0: return launch_u<0, 0, false>(dev_args, threads, grid, smem, s);
+        case 1: return launch_u<0, 2, false>(dev_args, threads, grid, smem, s);
+        case 2: return launch_u<0, 8, false>(dev_args, threads, grid, smem, s);
+        case 3: return launch_u<0, 0, true>(dev_args, threads, grid, smem, s);
+        case 4: return launch_u<0, 2, true>(dev_args, threads, grid, smem, s);
+        case 5: return launch_u<0, 8, true>(dev_args, threads, grid, smem, s);
+        case 6: return launch_u<1, 0, false>(dev_args, threads, grid, smem, s);
+        case 7: return launch_u<1, 2, false>(dev_args, threads, grid, smem, s);
+        case 8: return launch_u<1, 8, false>(dev_args, threads, grid, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int max_units_ctas_per_sm(int cls, int threads, uint32_t smem) {
+    switch (cls) {
+        case 0: return occ_u<0, 0, false>(threads, smem);
+        case 1: return occ_u<0, 2, false>(threads, smem);
+        case 2: return occ_u<0, 8, false>(threads, smem);
+        case 3: return occ_u<0, 0, true>(threads, smem);
+        case 4: return occ_u<0, 2, true>(threads, smem);
+        case 5: return occ_u<0, 8, true>(threads, smem);
+        case 6: return occ_u<1, 0, false>(threads, smem);
+        case 7: return occ_u<1, 2, false>(threads, smem);
+        case 8: return occ_u<1, 8, false>(threads, smem);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_carry_batch(const BatchArgs *dev_args, int grid, cudaStream_t s) {
+    carry_batch<<<grid, 256, 0, s>>>(dev_args);
+    return cudaGetLastError();
+}
+
+}  // namespace pfsm

@@ -482,8 +482,8 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.tile = tile;
     a.halo = p.halo;
     a.ntiles = static_cast<uint32_t>((n + tile - 1) / tile);
-    a.text_buf = (tile + p.halo + 16 + 127) & ~127u;
-    a.aligned = (reinterpret_cast<uintptr_t>(text) & 15) == 0;
+    a.text_buf = (tile + p.halo + 32 + 127) & ~127u;
+    a.shift = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15);
     a.Q = m.Q;
     a.S = m.S;
     a.q0 = m.q0;
@@ -644,6 +644,8 @@ int pfsm_ctx_create(int device, uint64_t budget_bytes, pfsm_ctx **out) {
         return PFSM_E_CUDA;
     }
     c->nsm = prop.multiProcessorCount;
+    c->smem_sm = static_cast<uint32_t>(prop.sharedMemPerMultiprocessor);
+    c->smem_rsv = static_cast<uint32_t>(prop.reservedSharedMemPerBlock);
     *out = c;
     return PFSM_OK;
 }

@@ -57,6 +57,16 @@ struct Slot {   // per-stream scratch
 
 struct BatchState;   // batch.cu
 
+// Launch shape of one batch class (batch.cu), fixed per context until the
+// batch parameters change: the layout of everything but the table arena,
+// and the arena's size.
+struct BatchShape {
+    bool ready = false;
+    int threads = 0, grid = 0;
+    uint32_t smem = 0, arena = 0;
+    ScanArgs layout{};
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int d) {
@@ -89,8 +99,13 @@ struct pfsm_ctx {
     uint64_t time_launches = 0;
     // batch executors, one per stream (batch.cu), and their launch shape
     std::map<cudaStream_t, pfsm::BatchState *> batch;
-    int batch_threads = 256;
+    int batch_threads = 0;        // 0: per-class default
+    int batch_ctas = 0;           // CTAs per SM, 0: per-class default
     uint32_t batch_tile = 16384;
+    uint64_t batch_gen = 1;       // bumped when the batch parameters change
+    pfsm::BatchShape batch_shape[pfsm::kBatchClasses];
+    uint32_t smem_sm = 233472;    // shared memory per SM
+    uint32_t smem_rsv = 1024;     // shared memory the system reserves per CTA
 };
 
 namespace pfsm {

@@ -41,9 +41,8 @@ constexpr uint32_t BAND_CSR = 0xFFFFFFFFu;
 // started at q0 meets a final state within those m symbols or still holds a
 // state after them; a clear bit settles the start without a lookup.
 
-// Work-queue entry of the filter phase (uint32): start offset inside the
-// tile in bits 0..15, info in bits 16..31 (a prefix-table entry, or PT_WALK
-// when the instance has to step from q0).
+// Work-queue entry of the filter phase: the absolute start (uint32) and its
+// prefix-table entry (uint16; PT_WALK when the instance steps from q0).
 
 // ---- per-scan device state ---------------------------------------------
 // status[0] = match count, status[1] = error bits (ERR_*).
@@ -67,8 +66,9 @@ struct ScanArgs {
     uint32_t ntiles;
     uint32_t tile;          // starts per tile
     uint32_t halo;          // bytes staged past the tile
-    uint32_t text_buf;      // bytes per staging buffer (tile + halo + 16)
-    uint32_t aligned;       // text pointer is 16-byte aligned
+    uint32_t text_buf;      // bytes per staging buffer (tile + halo + 32, rounded)
+    uint32_t shift;         // text address mod 16 (tiles are staged from the
+                            // 16-byte boundary below and moved down by it)
     // machine
     int32_t Q, S, q0, k, sbits;
     uint32_t memo_n;        // entries of the prefix table (0 when k == 0)
@@ -106,24 +106,32 @@ struct ScanArgs {
     int32_t settle_steps;   // NFA: settling step cap (0 = no settling)
 };
 
-// One text of a batch in the device job table (sorted by machine).
+// ---- batch executor ------------------------------------------------------
+// Machines of a batch fall into classes, one specialised persistent kernel
+// each: (kind, prefix-symbol width SB in {0, 2, 8}, DFA table in shared
+// memory). Class index: DFA 3 * tab + sb_index, NFA 6 + sb_index.
+constexpr int kBatchClasses = 9;
+constexpr uint32_t kNotStaged = 0xFFFFFFFFu;   // arena offset of a table left in global memory
+
+// One text of a batch in the device job table (grouped by class, then
+// sorted by machine). Its tiles are cut into work units of up to
+// BatchArgs::unit_tiles consecutive tiles.
 struct BatchJob {
     const uint8_t *text;
     uint32_t n;
     uint32_t mach;        // index into the batch's machine table
     uint32_t orig;        // caller's job index, reported with each match
-    uint32_t tile_begin;  // first work item of this text
+    uint32_t unit_begin;  // first work unit of this text within its class
+    uint32_t ntiles;      // tiles of this text
+    uint32_t pad;
 };
+static_assert(sizeof(BatchJob) == 32, "BatchJob layout");
 
 struct DevMachine {
     int32_t kind;     // 0 DFA, 1 NFA
     int32_t Q, S, q0, k, sbits;
     uint32_t memo_n;
     int32_t Wq;
-    int32_t tab_smem; // batch: DFA table staged to shared memory
-    int32_t band_smem;// batch: NFA band rows staged to shared memory
-    int32_t pool_smem;// batch: NFA prefix records staged to shared memory
-    int32_t memo_smem;// batch: prefix table staged to shared memory
     const uint16_t *memo;
     const uint16_t *dtab;
     const uint32_t *off;
@@ -136,16 +144,25 @@ struct DevMachine {
     uint32_t surv_words;
     int32_t surv2_m;
     const uint32_t *surv2;
+    // batch: byte offsets of the tables copied into the CTA's shared-memory
+    // table arena when this machine's tiles run (kNotStaged: read from
+    // global memory; for the survival bitmap: not used)
+    uint32_t a_memo, a_tab, a_band, a_pool, a_surv;
+    int32_t settle;   // batch: NFA settling step cap (0 = no settling)
 };
 static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
 
-// Arguments of the persistent batch kernel, read from device memory so that
-// one captured graph serves every batch of the same shape.
+// Arguments of one class's persistent batch kernel, read from device memory
+// so that one captured graph serves every batch with the same classes.
 struct BatchArgs {
-    ScanArgs sa;              // layout, output, status, carry (text/machine unused)
-    uint32_t nitems, njobs;
-    uint32_t *item_counter;
-    const BatchJob *jobs;
+    ScanArgs sa;              // class layout, output, status, carry, warp bitsets
+    uint32_t nunits;          // work units of this class
+    uint32_t job_lo, job_hi;  // this class's slice of the job table
+    uint32_t unit_tiles;      // tiles per work unit
+    uint32_t sm_arena;        // shared-memory offset of the table arena
+    uint32_t pad;
+    uint32_t *unit_counter;
+    const BatchJob *jobs;     // the whole job table (carry entries use its indices)
     const DevMachine *machs;
     unsigned long long *job_counts;
 };
@@ -164,11 +181,14 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
 cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
                         cudaStream_t s);
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_batch(const BatchArgs *dev_args, int threads, int grid, uint32_t smem,
-                         cudaStream_t s);
-cudaError_t launch_carry_batch(const BatchArgs *dev_args, int grid, cudaStream_t s);
 int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem);
-int max_batch_ctas_per_sm(int threads, uint32_t smem);
+
+// ---- batch launch helpers (batch_kernels.cu) -----------------------------
+int batch_class(int kind, int sbits, int k, bool tab_smem);
+cudaError_t launch_units(int cls, const BatchArgs *dev_args, int threads, int grid,
+                         uint32_t smem, cudaStream_t s);
+cudaError_t launch_carry_batch(const BatchArgs *dev_args, int grid, cudaStream_t s);
+int max_units_ctas_per_sm(int cls, int threads, uint32_t smem);
 
 // Release the batch executor state of a context (batch.cu).
 void batch_free(pfsm_ctx *ctx);

@@ -1,0 +1,994 @@
+// Device building blocks of the PFSM scan for sm_103a, shared by the
+// single-text kernels (scan_kernels.cu) and the batch kernels (batch_kernels.cu).
+//
+//
+// One persistent CTA loops over text tiles. A tile owns the instances that
+// start in [b, b + tile) and stages t[b, b + tile + halo) into shared memory
+// with a 1-D bulk TMA copy (double buffered, evict-first in L2). Instances
+// that are still alive past the staged halo continue on the global text:
+// DFA instances are pushed to a carry queue drained by a second kernel
+// (chained data partitioning, Sec. III.D.2), NFA instances continue in place
+// (lazy data partitioning, same section).
+//
+// Every start i is an instance {(i, q0)} (reinitialisation, Sec. III.B step 1).
+// Its first k steps depend only on t[i..i+k), so their outcome is read from a
+// start-prefix table built at load time (one entry per k-gram: dies, a single
+// surviving DFA state, or an NFA record of matches and survivors). The filter
+// phase streams the tile, looks each start up and queues only the instances
+// that still have work. The continuation phase drains the queue: every lane
+// holds one instance, advances it one symbol per iteration through delta
+// (Sec. III.B steps 3-4), reports final targets (start = tag, end = current
+// position), and refills from the queue when its instance dies. A lane that
+// holds an NFA set too large for its slot hands it to the whole warp, which
+// advances it as a bitset over Q.
+//
+// Matches are staged per warp in shared memory with ballot/popc appends and
+// flushed with one global atomic per flush.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pfsm_internal.h"
+
+namespace pfsm {
+
+#define FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint16_t ldg_u16_keep(const uint16_t *p, uint64_t pol) {
+    uint16_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ldg_u32_keep(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a bulk-copy barrier: gives up after ~2 s of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+    return true;
+}
+
+// Shared-memory control words of a CTA.
+struct Misc {
+    uint64_t bar[2];
+    uint32_t q_count;
+    uint32_t q_head;
+    uint32_t abort;
+    uint32_t pad;
+};
+
+// ------------------------------------------------------------ symbol checks
+// Byte-wise "x >= S" over a 64-bit word, high bit of each byte set on hit.
+__device__ __forceinline__ uint64_t bytes_ge(uint64_t x, uint32_t S) {
+    const uint64_t ones = 0x0101010101010101ull, m7 = 0x7F7F7F7F7F7F7F7Full,
+                   h = 0x8080808080808080ull;
+    if (S <= 128) return (((x & m7) + (uint64_t)(0x80 - S) * ones) | x) & h;
+    return (((x & m7) + (uint64_t)(0x80 - (S - 128)) * ones) & x) & h;
+}
+
+// 2-bit packing of 8 bytes (each 0..3) into 16 bits, byte m at bits 2m.
+__device__ __forceinline__ uint32_t pack2(uint64_t x) {
+    x &= 0x0303030303030303ull;
+    x = (x | (x >> 6)) & 0x000F000F000F000Full;
+    x = (x | (x >> 12)) & 0x000000FF000000FFull;
+    x = (x | (x >> 24)) & 0xFFFFull;
+    return static_cast<uint32_t>(x);
+}
+
+// Prefix-table index of the start at window byte r (k symbols from byte r).
+template <int SB>
+__device__ __forceinline__ uint32_t memo_index(uint64_t lo, uint64_t hi, uint32_t p2, int r,
+                                               int k, int sbits, uint32_t mask) {
+    if (SB == 2) {
+        return (p2 >> (2 * r)) & mask;
+    } else if (SB == 8) {
+        const uint64_t w = r == 0 ? lo : ((lo >> (8 * r)) | (hi << (64 - 8 * r)));
+        return static_cast<uint32_t>(w) & mask;
+    } else {
+        uint32_t idx = 0;
+        const uint32_t sm = (1u << sbits) - 1;
+        for (int m = 0; m < k; ++m) {
+            const int j = r + m;
+            const uint32_t byte =
+                static_cast<uint32_t>((j < 8 ? (lo >> (8 * j)) : (hi >> (8 * (j - 8)))) & 0xFF);
+            idx |= (byte & sm) << (sbits * m);
+        }
+        return idx;
+    }
+}
+
+// m-gram index (m <= 12) of the start at offset `off` of the staged tile,
+// read from four aligned words.
+template <int SB>
+__device__ __forceinline__ uint32_t gram_at16(const uint8_t *tsm, uint32_t off, int m, int sbits,
+                                              uint32_t mask) {
+    const uint32_t a4 = off & ~3u, r = off & 3u;
+    const uint4 w = *reinterpret_cast<const uint4 *>(tsm + (a4 & ~15u));
+    // realign to a4 (a4 may sit 4, 8 or 12 bytes into the 16-byte block)
+    const uint32_t sh = (a4 & 15u) >> 2;
+    const uint32_t x0 = sh == 0 ? w.x : sh == 1 ? w.y : sh == 2 ? w.z : w.w;
+    const uint32_t x1 = sh == 0 ? w.y : sh == 1 ? w.z : sh == 2 ? w.w : 0u;
+    const uint32_t x2 = sh == 0 ? w.z : sh == 1 ? w.w : 0u;
+    const uint32_t x3 = sh == 0 ? w.w : 0u;
+    uint32_t y1 = x1, y2 = x2, y3 = x3;
+    if (sh) {   // the missing words come from the next 16-byte block
+        const uint4 v = *reinterpret_cast<const uint4 *>(tsm + (a4 & ~15u) + 16);
+        if (sh == 1) y3 = v.x;
+        if (sh == 2) { y2 = v.x; y3 = v.y; }
+        if (sh == 3) { y1 = v.x; y2 = v.y; y3 = v.z; }
+    }
+    const uint64_t lo = x0 | (static_cast<uint64_t>(y1) << 32);
+    const uint64_t hi = y2 | (static_cast<uint64_t>(y3) << 32);
+    const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+    return memo_index<SB>(lo, hi, p2, static_cast<int>(r), m, sbits, mask);
+}
+
+// Prefix-table index of the start at offset `off` of the staged tile (k
+// symbols read from three aligned words; k <= 8).
+template <int SB>
+__device__ __forceinline__ uint32_t kgram_at(const uint8_t *tsm, uint32_t off, int k, int sbits,
+                                             uint32_t mask) {
+    const uint32_t a4 = off & ~3u, r = off & 3u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t *>(tsm + a4);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t *>(tsm + a4 + 4);
+    const uint32_t w2 = *reinterpret_cast<const uint32_t *>(tsm + a4 + 8);
+    const uint64_t lo = w0 | (static_cast<uint64_t>(w1) << 32);
+    const uint64_t hi = w2;
+    const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+    return memo_index<SB>(lo, hi, p2, static_cast<int>(r), k, sbits, mask);
+}
+
+// ------------------------------------------------------------ views
+// The machine one tile runs (registers).
+struct MView {
+    int32_t Q, S, q0, k, sbits, Wq, surv_m, surv2_m;
+    const uint32_t *surv2;
+    const uint16_t *dtab;
+    const uint32_t *off;
+    const uint16_t *tgt;
+};
+
+// Where matches and carried instances go.
+struct OView {
+    uint32_t *out;
+    uint64_t cap;
+    unsigned long long *status;       // [0] match count, [1] error bits
+    unsigned long long *job_counts;   // per-text counts (batch) or null
+    uint32_t *carry;                  // {job, start, pos, state} entries
+    uint32_t *carry_n;
+    uint32_t carry_cap;
+    uint32_t stage_n;                 // per-warp staging capacity (entries)
+};
+
+// One staged tile: bytes [b, b + len) of a text are in shared memory.
+struct TileView {
+    const uint8_t *sm;
+    const uint8_t *text;
+    uint32_t b, len, n;
+    uint32_t job;    // index into the device job table (batch), 0 otherwise
+    uint32_t orig;   // caller's text index reported with the matches
+};
+
+// Shared-memory regions of one CTA.
+struct Smem {
+    Misc *misc;
+    const uint16_t *memo;
+    const uint16_t *tab;
+    const uint32_t *band;             // NFA band image (shared copy, global, or null)
+    const uint32_t *pool;             // NFA prefix records (shared copy or global)
+    const uint32_t *surv;             // survival bitmap (shared copy) or null
+    uint16_t *list;                   // this warp's list of surviving starts
+    uint32_t *pairs;                  // this warp's settling pool (SETTLE_PAIRS)
+    uint32_t *pcount;                 // its fill count
+    uint32_t *marks;                  // WARP_LIST bits: entries sent to the exact path
+    uint32_t *wq_start;               // this warp's work queue: absolute starts
+    uint16_t *wq_info;                //   and prefix-table entries (WARP_QUEUE)
+    uint32_t *stage;   // this warp's staging buffer
+    uint16_t *slots;   // this warp's NFA slots
+    uint32_t *coop;    // this warp's two bitsets of Wq words
+};
+
+__device__ __forceinline__ uint32_t text_at(const TileView &tv, uint32_t pos) {
+    const uint32_t rel = pos - tv.b;
+    return rel < tv.len ? tv.sm[rel] : __ldg(tv.text + pos);
+}
+
+// ------------------------------------------------------------ match output
+// Per-warp staging of matches (OUTW words each: [text,] start, end, state);
+// `sn` is warp-uniform. A flush reserves room with one global atomic.
+template <int OUTW>
+__device__ __forceinline__ void stage_flush(uint32_t *buf, uint32_t &sn, const OView &ov,
+                                            uint32_t orig, int lane) {
+    __syncwarp();
+    if (sn == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&ov.status[0], (unsigned long long)sn);
+        if (ov.job_counts) atomicAdd(&ov.job_counts[orig], (unsigned long long)sn);
+    }
+    base = __shfl_sync(FULLMASK, base, 0);
+    const uint32_t words = OUTW * sn;
+    for (uint32_t w = lane; w < words; w += 32) {
+        const unsigned long long idx = base + w / OUTW;
+        if (idx < ov.cap) ov.out[base * OUTW + w] = buf[w];
+    }
+    __syncwarp();
+    sn = 0;
+}
+
+template <int OUTW>
+__device__ __forceinline__ void warp_emit(bool has, uint32_t s, uint32_t e, uint32_t st,
+                                          uint32_t *buf, uint32_t &sn, const OView &ov,
+                                          const TileView &tv, int lane) {
+    const uint32_t m = __ballot_sync(FULLMASK, has);
+    if (m == 0) return;
+    const uint32_t c = __popc(m);
+    if (sn + c > ov.stage_n) stage_flush<OUTW>(buf, sn, ov, tv.orig, lane);
+    if (has) {
+        uint32_t *p = buf + OUTW * (sn + __popc(m & lanemask_lt()));
+        if (OUTW == 4) *p++ = tv.orig;
+        p[0] = s;
+        p[1] = e;
+        p[2] = st;
+    }
+    sn += c;
+}
+
+// Direct append for divergent callers (warp-cooperative sets, carried runs).
+template <int OUTW>
+__device__ __forceinline__ void emit_direct(const OView &ov, uint32_t orig, uint32_t s,
+                                            uint32_t e, uint32_t st) {
+    const unsigned long long idx = atomicAdd(&ov.status[0], 1ull);
+    if (ov.job_counts) atomicAdd(&ov.job_counts[orig], 1ull);
+    if (idx < ov.cap) {
+        uint32_t *p = ov.out + idx * OUTW;
+        if (OUTW == 4) *p++ = orig;
+        p[0] = s;
+        p[1] = e;
+        p[2] = st;
+    }
+}
+
+// ------------------------------------------------------------ continuation: DFA
+// Drains the work queue with lane refill: one symbol per lane per iteration.
+template <bool TAB_SMEM, int OUTW>
+__device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
+                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep) {
+    uint32_t head = 0;
+    const uint32_t S = mv.S, n = tv.n;
+    // no staged tile (the final drain): nothing to hand to the carry queue
+    const uint32_t tile_end = tv.len ? tv.b + tv.len : 0xFFFFFFFFu;
+    bool act = false;
+    bool gmode = false;   // past the staged text and the carry queue is full
+    uint32_t start = 0, pos = 0, s = 0;
+    while (true) {
+        const bool need = !act;
+        const uint32_t m = __ballot_sync(FULLMASK, need);
+        if (m && head < qn) {
+            const uint32_t base = head;
+            head += __popc(m);
+            if (need) {
+                const uint32_t qi = base + __popc(m & lanemask_lt());
+                if (qi < qn) {
+                    start = sm.wq_start[qi];
+                    const uint32_t info = sm.wq_info[qi];
+                    if (info == PT_WALK) {
+                        s = mv.q0;
+                        pos = start;
+                    } else {
+                        s = info;
+                        pos = start + mv.k;
+                    }
+                    act = true;
+                    gmode = false;
+                }
+            }
+        }
+        if (!__any_sync(FULLMASK, act)) break;
+        bool hit = false;
+        uint32_t hend = 0;
+        if (act) {
+            if (pos >= n) {
+                act = false;
+            } else if (pos >= tile_end && !gmode) {
+                const uint32_t ci = atomicAdd(ov.carry_n, 1u);
+                if (ci < ov.carry_cap) {
+                    uint32_t *c = ov.carry + 4 * ci;
+                    c[0] = tv.job;
+                    c[1] = start;
+                    c[2] = pos;
+                    c[3] = s;
+                    act = false;
+                } else {
+                    gmode = true;
+                }
+            }
+            if (act) {
+                const uint32_t c = text_at(tv, pos);
+                uint16_t e = DEAD16;
+                if (c < S) {
+                    const uint32_t ix = s * S + c;
+                    e = TAB_SMEM ? sm.tab[ix] : ldg_u16_keep(mv.dtab + ix, pol_keep);
+                }
+                if (e == DEAD16) {
+                    act = false;
+                } else {
+                    s = e & 0x7FFFu;
+                    hit = (e & FINAL_BIT) != 0;
+                    hend = pos;
+                    ++pos;
+                }
+            }
+        }
+        warp_emit<OUTW>(hit, start, hend, s, sm.stage, sn, ov, tv, lane);
+    }
+}
+
+// ------------------------------------------------------------ NFA rows
+// Visits delta(q, c) as (state | FINAL_BIT) values: from the band row of q
+// when it has one, otherwise from the CSR arrays.
+template <class F>
+__device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *band, uint32_t q,
+                                            uint32_t c, uint64_t pol_keep, F &&f) {
+    if (band) {
+        const uint32_t row = band[q];
+        if (row != BAND_CSR) {
+            const uint32_t *fin = band + mv.Q;
+            uint32_t m = (row >> (8 * c)) & 0xFFu;
+            while (m) {
+                const uint32_t t = q + __ffs(m);
+                m &= m - 1;
+                f(t | (((fin[t >> 5] >> (t & 31)) & 1u) << 15));
+            }
+            return;
+        }
+    }
+    const uint32_t lo = ldg_u32_keep(mv.off + q * mv.S + c, pol_keep);
+    const uint32_t hi = ldg_u32_keep(mv.off + q * mv.S + c + 1, pol_keep);
+    for (uint32_t e = lo; e < hi; ++e) f(static_cast<uint32_t>(ldg_u16_keep(mv.tgt + e, pol_keep)));
+}
+
+// Settling of surviving NFA starts, one warp at a time. The instances of a
+// chunk of <= 32 list entries are split into (start, state) pairs, one per
+// state of their prefix record; lanes advance one pair per iteration through
+// the band rows (the first target stays in the lane, further targets go back
+// to a per-warp pool) and refill from the pool. A pair dies when its state
+// has no target on the next symbol. Since the futures of the states of a set
+// are independent, an instance whose pairs all die before meeting a final
+// state reports nothing and is settled. Any other outcome (a final target,
+// a row outside the band, the staged text or the step limit running out, a
+// full pool, matches inside the prefix) marks the instance, and marked
+// instances are queued for the exact path, which redoes them from their
+// record, so nothing is reported twice.
+__device__ __forceinline__ void mark_entry(uint32_t *marks, uint32_t j) {
+    atomicOr(&marks[j >> 5], 1u << (j & 31));
+}
+__device__ __forceinline__ bool marked(const uint32_t *marks, uint32_t j) {
+    return (marks[j >> 5] >> (j & 31)) & 1u;
+}
+
+static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const TileView &tv,
+                                 uint32_t j0, uint32_t total, uint32_t e, int lane,
+                                 uint32_t max_steps) {
+    uint32_t *pairs = sm.pairs;
+    uint32_t *pcount = sm.pcount;
+    uint32_t *marks = sm.marks;
+    const uint32_t b = tv.b, n = tv.n, tile_end = tv.b + tv.len;
+    const uint32_t *fin = sm.band + mv.Q;
+    // 1. pairs from the prefix records of entries j0 + lane
+    {
+        const uint32_t j = j0 + lane;
+        uint32_t ns = 0, rec = 0;
+        if (j < total) {
+            if (e == PT_WALK) {
+                mark_entry(marks, j);
+            } else if (e != PT_SKIP) {
+                const uint32_t hdr = sm.pool[e];
+                if (hdr & 0xFFFFu) mark_entry(marks, j);   // matches inside the prefix
+                else ns = hdr >> 16, rec = e;
+            }
+        }
+        uint32_t incl = ns;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const uint32_t base = *pcount + incl - ns;
+        const bool fits = base + ns <= static_cast<uint32_t>(SETTLE_PAIRS);
+        if (ns && !fits) mark_entry(marks, j);
+        if (ns && fits)
+            for (uint32_t x = 0; x < ns; ++x)
+                pairs[base + x] = (j << 21) | sm.pool[rec + 1 + x];   // step 0
+        const uint32_t end = __reduce_max_sync(FULLMASK, (ns && fits) ? base + ns : 0u);
+        __syncwarp();
+        if (lane == 0 && end > *pcount) *pcount = end;
+        __syncwarp();
+    }
+    // 2. advance pairs with lane refill until the pool is empty
+    bool has = false;
+    uint32_t li = 0, step = 0, q = 0, start_pos = 0;
+    while (true) {
+        const uint32_t need = __ballot_sync(FULLMASK, !has);
+        uint32_t avail = 0, take = 0;
+        if (lane == 0) {
+            avail = *pcount;
+            take = min(avail, static_cast<uint32_t>(__popc(need)));
+            *pcount = avail - take;
+        }
+        avail = __shfl_sync(FULLMASK, avail, 0);
+        take = __shfl_sync(FULLMASK, take, 0);
+        if (!has) {
+            const uint32_t r = __popc(need & lanemask_lt());
+            if (r < take) {
+                const uint32_t e = pairs[avail - take + r];
+                li = e >> 21;
+                step = (e >> 15) & 0x3Fu;
+                q = e & 0x7FFFu;
+                start_pos = b + sm.list[li] + mv.k;
+                has = true;
+            }
+        }
+        __syncwarp();
+        if (!__any_sync(FULLMASK, has)) break;
+        if (has && marked(marks, li)) has = false;
+        if (has) {
+            const uint32_t pos = start_pos + step;
+            if (pos >= n) {
+                has = false;
+            } else if (pos >= tile_end || step >= max_steps) {
+                mark_entry(marks, li);
+                has = false;
+            } else {
+                const uint32_t c = tv.sm[pos - b];
+                const uint32_t row = c < static_cast<uint32_t>(mv.S) ? sm.band[q] : 0u;
+                if (row == BAND_CSR) {
+                    mark_entry(marks, li);
+                    has = false;
+                } else {
+                    uint32_t m = (row >> (8 * c)) & 0xFFu;
+                    bool first = true;
+                    uint32_t nq = 0;
+                    while (m) {
+                        const uint32_t t = q + __ffs(m);
+                        m &= m - 1;
+                        if ((fin[t >> 5] >> (t & 31)) & 1u) {
+                            mark_entry(marks, li);
+                            first = true;
+                            m = 0;
+                            nq = 0xFFFFFFFFu;
+                            break;
+                        }
+                        if (first) {
+                            nq = t;
+                            first = false;
+                        } else {
+                            const uint32_t slot = atomicAdd(pcount, 1u);
+                            if (slot < static_cast<uint32_t>(SETTLE_PAIRS))
+                                pairs[slot] = (li << 21) | ((step + 1) << 15) | t;
+                            else
+                                mark_entry(marks, li);
+                        }
+                    }
+                    if (first || nq == 0xFFFFFFFFu) {
+                        has = false;
+                    } else {
+                        q = nq;
+                        ++step;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && *pcount > static_cast<uint32_t>(SETTLE_PAIRS)) *pcount = SETTLE_PAIRS;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------ continuation: NFA
+// Warp-cooperative advance of one instance as a bitset over Q (lazy data
+// partitioning: reads the global text once past the staged bytes).
+template <int OUTW>
+__device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
+                                      const uint32_t *band, const TileView &tv,
+                                      uint32_t *bits0, uint32_t *bits1, uint32_t start,
+                                      uint32_t pos, int lane, uint64_t pol_keep) {
+    const uint32_t Wq = mv.Wq, S = mv.S, n = tv.n;
+    uint32_t *cur = bits0, *nxt = bits1;
+    while (pos < n) {
+        const uint32_t c = text_at(tv, pos);
+        if (c >= S) break;
+        for (uint32_t w = lane; w < Wq; w += 32) {
+            uint32_t x = cur[w];
+            while (x) {
+                const uint32_t bit = __ffs(x) - 1;
+                x &= x - 1;
+                nfa_targets(mv, band, w * 32 + bit, c, pol_keep, [&](uint32_t t) {
+                    const uint32_t ts = t & 0x7FFFu;
+                    const uint32_t mb = 1u << (ts & 31);
+                    const uint32_t old = atomicOr(&nxt[ts >> 5], mb);
+                    if ((t & FINAL_BIT) && !(old & mb)) emit_direct<OUTW>(ov, tv.orig, start, pos, ts);
+                });
+            }
+        }
+        __syncwarp();
+        uint32_t any = 0;
+        for (uint32_t w = lane; w < Wq; w += 32) {
+            cur[w] = 0;
+            any |= nxt[w];
+        }
+        uint32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        ++pos;
+        if (!__any_sync(FULLMASK, any != 0)) break;
+        __syncwarp();
+    }
+    __syncwarp();
+}
+
+enum : uint32_t { MODE_LANE = 0, MODE_COOP_SLOT = 1, MODE_COOP_POOL = 2 };
+
+// Drains the work queue for an NFA: each lane holds one instance's state set
+// (up to NFA_SLOT states) and advances it one symbol per iteration.
+template <int OUTW>
+__device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
+                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep) {
+    uint32_t head = 0;
+    const uint32_t S = mv.S, n = tv.n;
+    constexpr int C = NFA_SLOT;
+    uint16_t *slots = sm.slots;
+#define SLOT(sel, i) slots[((sel) * C + (i)) * 32 + lane]
+    bool act = false;
+    uint32_t start = 0, pos = 0, cnt = 0, cb = 0, mode = MODE_LANE;
+    uint32_t pm_left = 0, pm_ptr = 0, cptr = 0;
+    while (true) {
+        const bool need = !act;
+        const uint32_t m = __ballot_sync(FULLMASK, need);
+        if (m && head < qn) {
+            const uint32_t base = head;
+            head += __popc(m);
+            if (need) {
+                const uint32_t qi = base + __popc(m & lanemask_lt());
+                if (qi < qn) {
+                    start = sm.wq_start[qi];
+                    const uint32_t info = sm.wq_info[qi];
+                    act = true;
+                    mode = MODE_LANE;
+                    pm_left = 0;
+                    if (info == PT_WALK) {
+                        SLOT(cb, 0) = static_cast<uint16_t>(mv.q0);
+                        cnt = 1;
+                        pos = start;
+                    } else {
+                        const uint32_t ro = info;
+                        const uint32_t w0 = sm.pool[ro];
+                        const uint32_t nm = w0 & 0xFFFFu, ns = w0 >> 16;
+                        pm_left = nm;
+                        pm_ptr = ro + 1;
+                        pos = start + mv.k;
+                        cnt = ns;
+                        if (ns > static_cast<uint32_t>(C)) {
+                            mode = MODE_COOP_POOL;
+                            cptr = ro + 1 + nm;
+                        } else {
+                            for (uint32_t i = 0; i < ns; ++i)
+                                SLOT(cb, i) = static_cast<uint16_t>(sm.pool[ro + 1 + nm + i]);
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULLMASK, act)) break;
+
+        // matches inside the first k steps, from the prefix record
+        while (__any_sync(FULLMASK, pm_left > 0)) {
+            const bool has = pm_left > 0;
+            uint32_t o = 0, f = 0;
+            if (has) {
+                const uint32_t w = sm.pool[pm_ptr];
+                o = w >> 16;
+                f = w & 0xFFFFu;
+                ++pm_ptr;
+                --pm_left;
+            }
+            warp_emit<OUTW>(has, start, start + o, f, sm.stage, sn, ov, tv, lane);
+        }
+        if (act && mode == MODE_LANE && cnt == 0) act = false;
+
+        // one symbol for every lane-held instance
+        bool anyfin = false;
+        if (act && mode == MODE_LANE) {
+            if (pos >= n) {
+                act = false;
+            } else {
+                const uint32_t c = text_at(tv, pos);
+                if (c >= S) {
+                    act = false;
+                } else {
+                    uint32_t ncnt = 0;
+                    bool ovf = false;
+                    for (uint32_t i = 0; i < cnt && !ovf; ++i) {
+                        const uint32_t q = SLOT(cb, i) & 0x7FFFu;
+                        nfa_targets(mv, sm.band, q, c, pol_keep, [&](uint32_t t) {
+                            if (ovf) return;
+                            const uint32_t ts = t & 0x7FFFu;
+                            for (uint32_t j = 0; j < ncnt; ++j)
+                                if ((SLOT(cb ^ 1, j) & 0x7FFFu) == ts) return;
+                            if (ncnt == static_cast<uint32_t>(C)) {
+                                ovf = true;
+                                return;
+                            }
+                            SLOT(cb ^ 1, ncnt) = static_cast<uint16_t>(t);
+                            ++ncnt;
+                            anyfin |= (t & FINAL_BIT) != 0;
+                        });
+                    }
+                    if (ovf) {
+                        mode = MODE_COOP_SLOT;   // redo this symbol on the warp
+                        anyfin = false;
+                    } else {
+                        cb ^= 1;
+                        cnt = ncnt;
+                    }
+                }
+            }
+        }
+        if (__any_sync(FULLMASK, anyfin)) {
+            for (uint32_t j = 0; j < static_cast<uint32_t>(C); ++j) {
+                const bool has = anyfin && j < cnt && (SLOT(cb, j) & FINAL_BIT);
+                warp_emit<OUTW>(has, start, pos, has ? (SLOT(cb, j) & 0x7FFFu) : 0u, sm.stage,
+                                sn, ov, tv, lane);
+            }
+        }
+        if (act && mode == MODE_LANE) {
+            ++pos;
+            if (cnt == 0) act = false;
+        }
+
+        // instances whose set outgrew the lane slot run on the whole warp
+        uint32_t cm = __ballot_sync(FULLMASK, act && mode != MODE_LANE);
+        while (cm) {
+            const int src = __ffs(cm) - 1;
+            cm &= cm - 1;
+            const uint32_t cs = __shfl_sync(FULLMASK, start, src);
+            const uint32_t cp = __shfl_sync(FULLMASK, pos, src);
+            const uint32_t cmode = __shfl_sync(FULLMASK, mode, src);
+            const uint32_t ccnt = __shfl_sync(FULLMASK, cnt, src);
+            const uint32_t ccb = __shfl_sync(FULLMASK, cb, src);
+            const uint32_t cpt = __shfl_sync(FULLMASK, cptr, src);
+            uint32_t *b0 = sm.coop, *b1 = sm.coop + mv.Wq;
+            for (uint32_t w = lane; w < static_cast<uint32_t>(mv.Wq); w += 32) {
+                b0[w] = 0;
+                b1[w] = 0;
+            }
+            __syncwarp();
+            if (cmode == MODE_COOP_SLOT) {
+                if (static_cast<uint32_t>(lane) < ccnt) {
+                    const uint32_t q = slots[(ccb * C + lane) * 32 + src] & 0x7FFFu;
+                    atomicOr(&b0[q >> 5], 1u << (q & 31));
+                }
+            } else {
+                for (uint32_t i = lane; i < ccnt; i += 32) {
+                    const uint32_t q = sm.pool[cpt + i];
+                    atomicOr(&b0[q >> 5], 1u << (q & 31));
+                }
+            }
+            __syncwarp();
+            coop_run<OUTW>(ov, mv, sm.band, tv, b0, b1, cs, cp, lane, pol_keep);
+            if (lane == src) {
+                act = false;
+                mode = MODE_LANE;
+            }
+        }
+    }
+#undef SLOT
+}
+
+template <int KIND, bool TAB_SMEM, int OUTW>
+__device__ __forceinline__ void drain(const OView &ov, const MView &mv, const TileView &tv,
+                                      const Smem &sm, uint32_t &wq_n, uint32_t &sn, int lane,
+                                      uint64_t pol_keep) {
+    if (wq_n == 0) return;
+    if (KIND == 0)
+        drain_dfa<TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+    else
+        drain_nfa<OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+    __syncwarp();
+    wq_n = 0;
+}
+
+// ------------------------------------------------------------ one tile
+// Filter phase over the tile's own starts [b, own_end), then the
+// continuation of every queued instance. All threads of the CTA call this.
+template <int KIND, int SB, bool TAB_SMEM, int OUTW>
+__device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
+                             const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
+                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps) {
+    constexpr int SPT = 32;   // starts per thread per filter round (4 windows of 8)
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int NT = blockDim.x;
+    const uint32_t n = tv.n, b = tv.b;
+    const uint32_t kk = static_cast<uint32_t>(mv.k);
+    const uint32_t kbits = static_cast<uint32_t>(mv.k * mv.sbits);
+    const uint32_t mask = kbits >= 32 ? 0xFFFFFFFFu : ((1u << kbits) - 1);
+    const uint32_t round = SPT * NT;
+    const uint32_t mm = static_cast<uint32_t>(mv.surv_m);
+    const uint32_t mbits = mm * static_cast<uint32_t>(mv.sbits);
+    const uint32_t mmask = mbits >= 32 ? 0xFFFFFFFFu : ((1u << mbits) - 1);
+    const uint32_t m2 = static_cast<uint32_t>(mv.surv2_m);
+    const uint32_t m2bits = m2 * static_cast<uint32_t>(mv.sbits);
+    const uint32_t m2mask = m2bits >= 32 ? 0xFFFFFFFFu : ((1u << m2bits) - 1);
+    for (uint32_t r0 = b; r0 < own_end; r0 += round) {
+        // 1. this thread's SPT consecutive starts: symbol check and the
+        //    shared-memory survival bitmap, one 16-byte window per 8 starts
+        const uint32_t i0 = r0 + SPT * tid;
+        uint32_t live = 0;
+        if (i0 < own_end) {
+            const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
+            live = nown >= 32 ? 0xFFFFFFFFu : ((1u << nown) - 1);
+#pragma unroll
+            for (int g = 0; g < SPT / 8; ++g) {
+                if (static_cast<uint32_t>(8 * g) < nown) {
+                    const uint8_t *tp = tv.sm + (i0 - b) + 8 * g;
+                    const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                    const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                    const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                    const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                    const uint32_t gown = min(8u, nown - 8 * g);
+                    if (mv.S < 256) {
+                        uint64_t badm = bytes_ge(lo, mv.S);
+                        if (gown < 8) badm &= (1ull << (8 * gown)) - 1;
+                        if (badm) bad_symbol = true;
+                    }
+                    if (sm.surv) {
+                        const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const uint32_t i = i0 + 8 * g + r;
+                            if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
+                                const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
+                                if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << (8 * g + r));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // 2. compact the surviving starts into this warp's list
+        uint32_t total = 0;
+        if (__any_sync(FULLMASK, live != 0)) {
+            const uint32_t c = __popc(live);
+            uint32_t incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+                if (lane >= d) incl += v;
+            }
+            total = __shfl_sync(FULLMASK, incl, 31);
+            uint32_t p = incl - c;
+            uint32_t x = live;
+            while (x) {
+                const uint32_t r = __ffs(x) - 1;
+                x &= x - 1;
+                sm.list[p++] = static_cast<uint16_t>(i0 + r - b);
+            }
+            __syncwarp();
+        }
+        // 3a. deep survival bitmap (global memory, L2 resident): independent
+        //     loads per lane, then compact the list in place
+        if (mv.surv2 && total) {
+            uint32_t w = 0;
+            for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool keep = false;
+                uint32_t off = 0;
+                if (j < total) {
+                    off = sm.list[j];
+                    keep = true;
+                    if (b + off + m2 <= n) {
+                        const uint32_t i2 = gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
+                        keep = (ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep) >> (i2 & 31)) & 1u;
+                    }
+                }
+                const uint32_t km = __ballot_sync(FULLMASK, keep);
+                __syncwarp();
+                if (keep) sm.list[w + __popc(km & lanemask_lt())] = static_cast<uint16_t>(off);
+                w += __popc(km);
+                __syncwarp();
+            }
+            total = w;
+        }
+        // 3b. every lane takes list entries: prefix table, settling, queue
+        const bool settle = KIND == 1 && sm.band && settle_steps > 0 && total;
+        if (settle) {
+            sm.marks[lane] = 0;
+            if (lane == 0) *sm.pcount = 0;
+            __syncwarp();
+        }
+        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            uint32_t e = PT_SKIP, off = 0;
+            if (j < total) {
+                off = sm.list[j];
+                e = PT_WALK;
+                if (kk != 0 && b + off + kk <= n)
+                    e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+            }
+            bool push = e != PT_SKIP;
+            if (settle) {
+                nfa_settle_chunk(mv, sm, tv, j0, total, e, lane, settle_steps);
+                push = j < total && marked(sm.marks, j);
+            }
+            const uint32_t pmask = __ballot_sync(FULLMASK, push);
+            if (pmask) {
+                // this warp's queue: drain it first when these would not fit
+                if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
+                    drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+                if (push) {
+                    const uint32_t p = wq_n + __popc(pmask & lanemask_lt());
+                    sm.wq_start[p] = b + off;
+                    sm.wq_info[p] = static_cast<uint16_t>(e);
+                }
+                wq_n += __popc(pmask);
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid) {
+    Smem s;
+    s.misc = reinterpret_cast<Misc *>(base + a.sm_misc);
+    s.memo = a.memo_smem ? reinterpret_cast<const uint16_t *>(base + a.sm_memo) : a.memo;
+    s.tab = reinterpret_cast<const uint16_t *>(base + a.sm_tab);
+    s.wq_start = reinterpret_cast<uint32_t *>(base + a.sm_queue) + wid * WARP_QUEUE;
+    s.wq_info = reinterpret_cast<uint16_t *>(base + a.sm_queue + (blockDim.x >> 5) * WARP_QUEUE * 4) +
+                wid * WARP_QUEUE;
+    s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
+    s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
+    s.coop = a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
+                      : nullptr;
+    s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
+    s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;
+    uint8_t *wl = base + a.sm_list + wid * WARP_LIST_BYTES;
+    s.list = reinterpret_cast<uint16_t *>(wl);
+    s.pairs = reinterpret_cast<uint32_t *>(wl + 2 * WARP_LIST);
+    s.marks = reinterpret_cast<uint32_t *>(wl + 2 * WARP_LIST + 4 * SETTLE_PAIRS);
+    s.pcount = s.marks + WARP_LIST / 32;
+    s.pool = a.pool_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_pool) : a.pool;
+    return s;
+}
+
+__device__ __forceinline__ void stage_u16(uint16_t *dst, const uint16_t *src, uint32_t count,
+                                          int tid, int nt) {
+    const uint32_t words = (count + 1) / 2;
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = tid; i < words; i += nt) d[i] = __ldg(s + i);
+}
+
+// Moves the staged bytes buf[sh, sh + len) down to buf[0, len) (0 < sh < 16;
+// buf is 16-byte aligned with room for len + 32 bytes). A tile of a text
+// that does not start on a 16-byte boundary is copied by TMA from the
+// boundary below it and realigned here. Every thread of the CTA calls it;
+// it ends with a barrier.
+__device__ __forceinline__ void realign_tile(uint8_t *buf, uint32_t sh, uint32_t len, int tid,
+                                             int nt) {
+    constexpr int PER = 4;   // output blocks per thread per chunk
+    uint4 *b4 = reinterpret_cast<uint4 *>(buf);
+    const uint32_t q = (len + 15) >> 4;
+    const uint32_t ws = sh >> 2, bs = (sh & 3u) * 8u;
+    for (uint32_t c0 = 0; c0 < q; c0 += PER * nt) {
+        uint4 o[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t i = c0 + j * nt + tid;
+            if (i < q) {
+                const uint4 x = b4[i], y = b4[i + 1];
+                // words ws .. ws + 4 of the eight words of x and y
+                const uint32_t w0 = ws == 0 ? x.x : ws == 1 ? x.y : ws == 2 ? x.z : x.w;
+                const uint32_t w1 = ws == 0 ? x.y : ws == 1 ? x.z : ws == 2 ? x.w : y.x;
+                const uint32_t w2 = ws == 0 ? x.z : ws == 1 ? x.w : ws == 2 ? y.x : y.y;
+                const uint32_t w3 = ws == 0 ? x.w : ws == 1 ? y.x : ws == 2 ? y.y : y.z;
+                const uint32_t w4 = ws == 0 ? y.x : ws == 1 ? y.y : ws == 2 ? y.z : y.w;
+                o[j].x = __funnelshift_r(w0, w1, bs);
+                o[j].y = __funnelshift_r(w1, w2, bs);
+                o[j].z = __funnelshift_r(w2, w3, bs);
+                o[j].w = __funnelshift_r(w3, w4, bs);
+            }
+        }
+        __syncthreads();   // this chunk's reads precede its writes; later
+                           // chunks read only blocks this one does not write
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t i = c0 + j * nt + tid;
+            if (i < q) b4[i] = o[j];
+        }
+    }
+    __syncthreads();
+}
+
+// Copies an NFA's band rows and prefix records into shared memory (either
+// source may be null: that table is then read from global memory).
+__device__ __forceinline__ void stage_nfa(uint8_t *base, uint32_t sm_band, uint32_t sm_pool,
+                                          const uint32_t *band, int32_t Q,
+                                          const uint32_t *pool, uint32_t pool_n, int tid,
+                                          int nt) {
+    if (band) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(base + sm_band);
+        const int32_t words = Q + (Q + 31) / 32;
+        for (int32_t i = tid; i < words; i += nt) d[i] = __ldg(band + i);
+    }
+    if (pool) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(base + sm_pool);
+        for (uint32_t i = tid; i < pool_n; i += nt) d[i] = __ldg(pool + i);
+    }
+}
+
+}  // namespace pfsm

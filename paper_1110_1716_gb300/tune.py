@@ -124,7 +124,7 @@ def tune(ctx: int, aut: int, machine, sample_text, gpu_name: str = "", force: bo
 
 
 def tune_batch(ctx: int, jobs, reps: int = 2, stream=None) -> dict:
-    """Pick the batch launch shape (threads per CTA, tile length) for a
+    """Pick the batch launch shape (threads and CTAs per SM, tile length) for a
     representative batch `jobs` ([(aut, text_tensor, n), ...]) by timing each
     candidate with CUDA events; sets and returns the fastest."""
     import torch
@@ -134,9 +134,9 @@ def tune_batch(ctx: int, jobs, reps: int = 2, stream=None) -> dict:
     out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
     status = torch.zeros(len(jobs) + 2, dtype=torch.int64, device=dev)
     best, best_ms = None, float("inf")
-    for threads in (128, 256):
+    for threads, ctas in ((0, 0), (256, 1), (256, 2), (512, 1), (128, 4)):
         for tile in (8192, 16384, 32768):
-            p = {"threads": threads, "tile": tile}
+            p = {"threads": threads, "ctas_per_sm": ctas, "tile": tile}
             try:
                 pfsm_set_batch_params(ctx, p)
             except Exception:
