@@ -160,7 +160,7 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
         a.halo = kBatchHalo;
         a.text_buf = (tile + kBatchHalo + 32 + 127) & ~127u;
         a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
-        base = layout_smem(a, kind ? 2 : 1, threads, SmemNeed{0u, 0u, 0u, 0u, 0u});
+        base = layout_smem(a, kind ? 2 : 1, threads, SmemNeed{0u, 0u, 0u, 0u, 0u, 0u});
         if (base + kMinArena <= budget) break;
         if (a.stage_n > 32) a.stage_n = 32;
         else if (tile > 8192) tile = 8192;
@@ -183,12 +183,14 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
 
 // Chooses which of a machine's tables go to the table arena (in order of
 // use per start: survival bitmap, prefix table, DFA table, NFA band rows,
-// NFA prefix records) and returns the machine's class. With a deep bitmap
-// in global memory few starts reach the prefix table, so the prefix table
-// and records stay in global memory and leave the arena to the rest.
-static int place_tables(const Machine &m, uint32_t arena, DevMachine &d) {
-    d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = kNotStaged;
+// the warp-wide NFA bitsets of `warps` warps, NFA prefix records) and
+// returns the machine's class. With a deep bitmap in global memory few
+// starts reach the prefix table, so the prefix table and records stay in
+// global memory and leave the arena to the rest.
+static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine &d) {
+    d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = d.a_coop = kNotStaged;
     d.settle = m.params.settle > 0 ? m.params.settle : 0;
+    d.pad = 0;
     uint32_t used = 0;
     auto take = [&](uint32_t bytes) {
         const uint32_t at = (used + 15) & ~15u;
@@ -203,6 +205,7 @@ static int place_tables(const Machine &m, uint32_t arena, DevMachine &d) {
         d.a_tab = take(((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4);
     } else {
         if (!m.band.empty()) d.a_band = take(static_cast<uint32_t>(m.band.size() * 4));
+        d.a_coop = take(static_cast<uint32_t>(warps * 2 * d.Wq * 4));
         if (!deep && !m.pool.empty()) d.a_pool = take(static_cast<uint32_t>(m.pool.size() * 4));
     }
     return batch_class(m.kind, m.sbits, m.k, m.kind == 0 && d.a_tab != kNotStaged);
@@ -214,7 +217,7 @@ struct BatchPlan {
     uint32_t mask = 0;                      // classes with work
     uint32_t job_lo[kBatchClasses] = {}, job_hi[kBatchClasses] = {};
     uint32_t nunits[kBatchClasses] = {}, unit_tiles[kBatchClasses] = {};
-    int32_t wq[kBatchClasses] = {};         // NFA: widest state bitset (words)
+    int32_t wq[kBatchClasses] = {};         // NFA: widest bitset kept in global scratch (words)
 };
 
 // Validate the jobs, make their machines resident, classify them and cut
@@ -260,9 +263,9 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     for (size_t i = 0; i < ids.size(); ++i) {
         Machine &m = ctx->machines[ids[i]];
         DevMachine d = m.dm;
-        const uint32_t arena = ctx->batch_shape[m.kind == 1 ? 6 : 0].arena;
-        cls_of[i] = place_tables(m, arena, d);
-        if (m.kind == 1) pl.wq[cls_of[i]] = std::max(pl.wq[cls_of[i]], d.Wq);
+        const BatchShape &sh = ctx->batch_shape[m.kind == 1 ? 6 : 0];
+        cls_of[i] = place_tables(m, sh.arena, sh.threads / 32, d);
+        if (m.kind == 1 && d.a_coop == kNotStaged) pl.wq[cls_of[i]] = std::max(pl.wq[cls_of[i]], d.Wq);
         pl.machs.push_back(d);
     }
     // jobs grouped by class, then by machine, so that consecutive units share

@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
             smi.tab = TAB ? reinterpret_cast<const uint16_t *>(arena + M.a_tab) : nullptr;
             smi.band = M.a_band != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_band) : M.band;
             smi.pool = M.a_pool != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_pool) : M.pool;
+            smi.coop = M.a_coop != kNotStaged
+                           ? reinterpret_cast<uint32_t *>(arena + M.a_coop) + wid * 2 * M.Wq : sm.coop;
             cur_mach = d.mach;
         }
         uint8_t *tsm = text_sm + buf * A.sa.text_buf;

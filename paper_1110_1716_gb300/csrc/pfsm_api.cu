@@ -525,6 +525,9 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
     a.settle_steps = m.params.settle > 0 ? m.params.settle : 0;
     need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
+    // warp-wide bitsets of sets too large for a lane: shared memory keeps
+    // their atomics on chip
+    need.coop_bytes = m.kind == 1 ? static_cast<uint32_t>((threads / 32) * 2 * m.dm.Wq * 4) : 0u;
     uint32_t smem = 0;
     bool fit = false;
     a.qcap = round;   // a filter round may queue every start it owns
@@ -536,6 +539,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         if (a.stage_n > 32) a.stage_n = 32;
         else if (need.pool_bytes) need.pool_bytes = 0;
         else if (need.memo_bytes) need.memo_bytes = 0;
+        else if (need.coop_bytes) need.coop_bytes = 0;
         else if (need.band_bytes) need.band_bytes = 0;
         else if (need.tab_bytes && p.table_smem == -1) { need.tab_bytes = 0; a.tab_smem = 0; }
         else break;
@@ -585,7 +589,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     pl.a.carry = slot->carry;
     pl.a.carry_n = slot->carry_n;
     pl.a.carry_cap = kCarryCap;
-    if (m.kind == 1) {
+    if (m.kind == 1 && !pl.a.coop_smem) {
         const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * m.dm.Wq;
         if (ensure_words(&slot->coop, &slot->coop_words, need)) return PFSM_E_NOMEM;
         pl.a.coop_g = slot->coop;

@@ -99,6 +99,7 @@ struct ScanArgs {
     uint32_t carry_cap;
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
+    int32_t coop_smem;      // NFA: warp-wide bitsets at sm_coop (else in coop_g)
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t qcap;
     uint32_t stage_n;       // staged matches per warp before a flush
@@ -148,7 +149,9 @@ struct DevMachine {
     // table arena when this machine's tiles run (kNotStaged: read from
     // global memory; for the survival bitmap: not used)
     uint32_t a_memo, a_tab, a_band, a_pool, a_surv;
+    uint32_t a_coop;  // batch: NFA warp-wide bitsets, 2 * Wq words per warp
     int32_t settle;   // batch: NFA settling step cap (0 = no settling)
+    int32_t pad;
 };
 static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
 
@@ -176,6 +179,7 @@ struct SmemNeed {
     uint32_t band_bytes;   // NFA band image copy (0 = read from global)
     uint32_t pool_bytes;   // NFA prefix records copy (0 = read from global)
     uint32_t surv_bytes;   // survival bitmap (always in shared memory when used)
+    uint32_t coop_bytes;   // NFA warp-wide bitsets, all warps (0 = global scratch)
 };
 uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &need);
 cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,

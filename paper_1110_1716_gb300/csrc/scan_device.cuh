@@ -912,7 +912,8 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
                 wid * WARP_QUEUE;
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
     s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
-    s.coop = a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
+    s.coop = a.coop_smem ? reinterpret_cast<uint32_t *>(base + a.sm_coop) + wid * 2 * a.Wq
+           : a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
                       : nullptr;
     s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
     s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;

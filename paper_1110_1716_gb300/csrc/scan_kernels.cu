@@ -142,7 +142,9 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     a.sm_queue = take(nw * WARP_QUEUE * 6, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
-    a.sm_coop = 0;   // warp-wide bitsets live in global scratch (coop_g)
+    // warp-wide NFA bitsets: shared memory when planned, else global scratch
+    a.sm_coop = take(has_nfa ? need.coop_bytes : 0u, 16);
+    a.coop_smem = has_nfa && need.coop_bytes > 0;
     return (o + 127) & ~127u;
 }
 
