@@ -106,6 +106,9 @@ struct NfaMemoBuilder {
              const std::vector<uint32_t> &matches) {
         if (!ok) return;
         const int k = m.k, sb = m.sbits;
+        // a text that ends here: the matches so far are the start's result
+        if (depth > 0 && depth < k && !matches.empty())
+            m.tail[tail_base(depth, sb) + prefix] = record(matches, {});
         if (depth == k) {
             if (!matches.empty() || !set.empty()) m.memo[prefix] = record(matches, set);
             return;
@@ -117,6 +120,10 @@ struct NfaMemoBuilder {
             const uint32_t rest = static_cast<uint32_t>(k - depth) * sb;
             for (uint32_t hiw = 0; hiw < (1u << rest); ++hiw)
                 m.memo[prefix | (hiw << (depth * sb))] = id;
+            // and every longer short gram through this prefix
+            for (int j = std::max(depth + 1, 1); j < k; ++j)
+                for (uint32_t hiw = 0; hiw < (1u << ((j - depth) * sb)); ++hiw)
+                    m.tail[tail_base(j, sb) + (prefix | (hiw << (depth * sb)))] = id;
             return;
         }
         for (int a = 0; a < (1 << sb); ++a) {
@@ -143,12 +150,15 @@ struct NfaMemoBuilder {
 
 bool build_memo_nfa(Machine &m) {
     m.pool.clear();
+    m.tail.clear();
     if (m.k <= 0) {
         m.memo.clear();
         return true;
     }
     const uint32_t nent = 1u << (m.k * m.sbits);
     m.memo.assign(nent + (nent & 1), PT_SKIP);
+    const uint32_t ntail = tail_base(m.k, m.sbits);
+    m.tail.assign(ntail + (ntail & 1), PT_SKIP);
     NfaMemoBuilder b(m);
     b.dfs(0, 0, {static_cast<uint16_t>(m.q0)}, {});
     if (!b.ok) return false;
@@ -261,7 +271,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t device_bytes(const Machine &m) {
     size_t b = align256(m.memo.size() * 2 + 4) + align256(m.surv.size() * 4 + 4) +
-               align256(m.surv2.size() * 4 + 4);
+               align256(m.surv2.size() * 4 + 4) + align256(m.tail.size() * 2 + 4);
     if (m.kind == 0) {
         b += align256(m.dtab.size() * 2 + 4);
     } else {
@@ -326,6 +336,8 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
     uint8_t *base = static_cast<uint8_t *>(p);
     const size_t o_memo = put(m.memo.data(), m.memo.size() * 2);
     dm.memo = reinterpret_cast<const uint16_t *>(base + o_memo);
+    const size_t o_tail = put(m.tail.data(), m.tail.size() * 2);
+    dm.tail = m.tail.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + o_tail);
     const size_t o_surv = put(m.surv.data(), m.surv.size() * 4);
     dm.surv = m.surv.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv);
     dm.surv_m = m.sm_m;
@@ -491,6 +503,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.sbits = m.sbits;
     a.memo_n = m.dm.memo_n;
     a.memo = m.dm.memo;
+    a.tail = m.dm.tail;
     a.dtab = m.dm.dtab;
     a.off = m.dm.off;
     a.tgt = m.dm.tgt;

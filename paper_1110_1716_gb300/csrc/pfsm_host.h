@@ -28,6 +28,7 @@ struct Machine {
     // start-prefix table
     int k = 0, sbits = 1;
     std::vector<uint16_t> memo;
+    std::vector<uint16_t> tail;       // NFA: records of the j-grams, 0 < j < k (text ends)
     std::vector<uint32_t> pool;
     std::vector<uint32_t> band;   // NFA band image (S <= 4) or empty
     // survival bitmap over m-grams (m = 0: none)

@@ -30,6 +30,17 @@ constexpr uint16_t FINAL_BIT = 0x8000;
 constexpr uint16_t PT_SKIP = 0xFFFF;
 constexpr uint16_t PT_WALK = 0xFFFE;
 
+// NFA short-gram table: a start with only j < k symbols left before the end
+// of its text has its whole future fixed by those j symbols: the matches it
+// meets within them. Entry tail_base(j) + (index of the j-gram) holds
+// PT_SKIP (no match) or the pool offset of a record with those matches and
+// no survivors. tail_base(j) = sum of 2^(i * sbits) for 0 < i < j.
+__host__ __device__ inline uint32_t tail_base(int j, int sbits) {
+    uint32_t b = 0;
+    for (int i = 1; i < j; ++i) b += 1u << (i * sbits);
+    return b;
+}
+
 // NFA band image (alphabets of at most 4 symbols): Q uint32 rows followed by
 // a final-state bitmap of ceil(Q/32) words. Byte a of row q is the mask of
 // delta(q, a) within q+1..q+8 (bit d set iff q+1+d is a target). BAND_CSR
@@ -73,6 +84,7 @@ struct ScanArgs {
     int32_t Q, S, q0, k, sbits;
     uint32_t memo_n;        // entries of the prefix table (0 when k == 0)
     const uint16_t *memo;   // prefix table (global copy, staged to smem)
+    const uint16_t *tail;   // NFA: short-gram table for starts within k of the end, or null
     const uint16_t *dtab;   // DFA: [Q][S]
     const uint32_t *off;    // NFA: [Q*S + 1] CSR offsets
     const uint16_t *tgt;    // NFA: targets
@@ -134,6 +146,7 @@ struct DevMachine {
     uint32_t memo_n;
     int32_t Wq;
     const uint16_t *memo;
+    const uint16_t *tail;   // NFA: short-gram table (see tail_base), or null
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;

@@ -210,6 +210,7 @@ struct MView {
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;
+    const uint16_t *tail;   // NFA short-gram table, or null
 };
 
 // Where matches and carried instances go.
@@ -876,8 +877,15 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             if (j < total) {
                 off = sm.list[j];
                 e = PT_WALK;
-                if (kk != 0 && b + off + kk <= n)
+                if (kk != 0 && b + off + kk <= n) {
                     e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                } else if (kk != 0 && mv.tail) {
+                    // fewer than k symbols left: their matches are the whole result
+                    const int jl = static_cast<int>(n - (b + off));
+                    const uint32_t jm = (1u << (jl * mv.sbits)) - 1;
+                    e = __ldg(mv.tail + tail_base(jl, mv.sbits) +
+                              (kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask) & jm));
+                }
             }
             bool push = e != PT_SKIP;
             if (settle) {

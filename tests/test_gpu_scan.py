@@ -47,6 +47,25 @@ def test_paper_examples_on_gpu(pf, fixture):
     assert oracle.labelled(got, m.labels) == want
 
 
+# ---------------------------------------------------------------- text ends
+@pytest.mark.parametrize("k", [2, 4, 6, 8])
+def test_nfa_starts_near_the_end_of_the_text(pf, k):
+    """Starts with fewer than k symbols left read the short-gram table; texts
+    of every length up to 3k + 2 put each j < k at the end of a text (and of
+    a tile), with matches of length 1 (a*c, ac) among them."""
+    m = W.eps_free(W.fig1_union())
+    a = pf.load(m)
+    P.pfsm_set_params(pf.ctx, a, {"prefix_k": k})
+    for n in range(0, 3 * k + 3):
+        for rep in range(3):
+            t = W.text_uniform(n, m.S, 77_000 + 100 * n + rep)
+            assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), (k, n, rep)
+    # a long text whose last tile ends in every phase
+    t = W.text_uniform(4096 * 3 + 5, m.S, 78_000 + k)
+    P.pfsm_set_params(pf.ctx, a, {"prefix_k": k, "tile": 4096, "halo": 16})
+    assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), k
+
+
 # ---------------------------------------------------------------- small machines, ragged sizes
 SIZES = [0, 1, 2, 7, 15, 16, 17, 100, 4095, 4096, 4097, 16383, 16384, 16385, 70001]
 
