@@ -84,6 +84,26 @@ def run_probe(args):
                           "params": P.pfsm_get_params(pf.ctx, aid)}))
 
 
+def kernel_traffic(name, text_bytes):
+    """DRAM bytes per launch of the scan kernel on `name`, scaled from the
+    recorded ncu capture by text length (the kernel reads its text once), or
+    None when there is no capture or the kernel sources changed since."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for fn in rec["source_files"]:
+            with open(os.path.join(ROOT, fn), "rb") as f:
+                h.update(f.read())
+        w = rec["workloads"].get(name)
+        if w is None or h.hexdigest() != rec["source_sha256"]:
+            return None
+        return w["dram_bytes"] * text_bytes / w["captured_text_bytes"]
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -243,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "achieved": algo_bytes / (kernel_ms * 1e-3) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": algo_bytes / (kernel_ms * 1e-3) / 1e9 / hbm,
-                         "traffic": None, "peak_source": peak_kind,
+                         "traffic": kernel_traffic(name, n), "peak_source": peak_kind,
                          "algorithmic_bytes": algo_bytes},
             "clocks": clk.summary(), "gpu_launches": launches_per_step * steps,
             "wall_s": wall,
