@@ -408,9 +408,12 @@ def serve_texts(w, seed=0):
     return texts
 
 
-def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
-    """Continuous batching under Poisson arrivals at `load` x the burst
-    capacity, against the plain form (one synchronous scan per request)."""
+def measure_serving(P, pf_unused, torch, dev, n_req=100_000, loads=(0.25, 0.5, 0.8)):
+    """Continuous batching under Poisson arrivals at several fractions of the
+    burst capacity, against the plain form (one synchronous scan per
+    request); then the 50 % load again with a residency budget of a third of
+    the machines' device bytes, so that machines are evicted and reloaded
+    while serving."""
     from paper_1110_1716_gb300.serve import Server
     w = W.serve_workload(seed=0, n_req=n_req)
     texts = serve_texts(w)
@@ -418,9 +421,27 @@ def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
     res = {"desc": "Poisson arrivals, lognormal lengths (median 4 KiB, sigma 1.5, max 4 MiB), "
                    "Zipf(1.1) over 64 machines of 64-16,384 states", "requests": n_req,
            "bytes": nbytes}
+
+    def poisson(srv, load, cap_rps, seed):
+        srv.reset_stats()
+        gaps = np.random.default_rng(seed).exponential(1.0 / (load * cap_rps), size=n_req)
+        before = P.pfsm_get_stats(srv.pf.ctx)
+        t0 = time.perf_counter()
+        futs = srv.run_trace(np.cumsum(gaps), w.req_aut, texts, t0=t0)
+        m = sum(len(f.result()) for f in futs)
+        el = time.perf_counter() - t0
+        st = srv.latency_stats()
+        return {"offered_req_per_s": load * cap_rps, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9, "matches_per_s": m / el,
+                "batches": st["batches"], "nomem_splits": st["nomem_splits"],
+                "evictions": st["residency_evictions"] - before["evictions"],
+                "reloads": st["residency_reloads"] - before["reloads"]}
+
     with P.Pfsm(dev.index, budget_bytes=8 << 30) as pf:
         srv = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
                      max_jobs=1024)
+        fleet = P.pfsm_get_stats(pf.ctx)["resident_bytes"]
+        res["fleet_bytes"] = fleet
         # plain form: one request at a time through pfsm_scan
         k = min(2000, n_req)
         t0 = time.perf_counter()
@@ -438,19 +459,20 @@ def measure_serving(P, pf_unused, torch, dev, n_req=20_000, load=0.5):
         cap_rps = n_req / burst_s
         res["burst_req_per_s"] = cap_rps
         res["burst_gbps"] = nbytes / burst_s / 1e9
-        # Poisson arrivals at a fraction of that capacity
-        srv2 = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
-                      max_jobs=1024)
-        gaps = np.random.default_rng(1).exponential(1.0 / (load * cap_rps), size=n_req)
-        t0 = time.perf_counter()
-        futs = srv2.run_trace(np.cumsum(gaps), w.req_aut, texts, t0=t0)
-        m = sum(len(f.result()) for f in futs)
-        el = time.perf_counter() - t0
-        st = srv2.latency_stats()
-        res.update({"offered_load": load, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                    "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9,
-                    "matches_per_s": m / el, "batches": st["batches"],
-                    "evictions": st["residency_evictions"], "reloads": st["residency_reloads"]})
+        res["loads"] = {}
+        for i, load in enumerate(loads):
+            res["loads"]["%g" % load] = poisson(srv, load, cap_rps, 1 + i)
+    # the same at 50 % load with a budget of a third of the fleet's device bytes
+    small_budget = fleet // 3
+    with P.Pfsm(dev.index, budget_bytes=small_budget) as pf:
+        srv = Server(pf, w.automata, slots=3, slot_bytes=64 << 20, out_rows=4 << 20,
+                     max_jobs=1024)
+        r = poisson(srv, 0.5, cap_rps, 9)
+        r["budget_bytes"] = small_budget
+        res["small_budget"] = r
+    mid = res["loads"].get("0.5") or next(iter(res["loads"].values()))
+    res.update({"offered_load": 0.5, "p50_ms": mid["p50_ms"], "p99_ms": mid["p99_ms"],
+                "served_gbps": mid["served_gbps"], "matches_per_s": mid["matches_per_s"]})
     return res
 
 

@@ -19,6 +19,7 @@ on the host.
 from __future__ import annotations
 
 import collections
+import gc
 import threading
 import time
 from concurrent.futures import Future
@@ -83,7 +84,9 @@ class Server:
         self.lock = threading.Condition()
         self.running = False
         self.thread = None
-        self.done: List[Request] = []
+        # latency (s) of every completed request; finished Request objects are
+        # not kept, so the interpreter's cycle collector has less to scan
+        self.latencies: List[float] = []
         self.batches = 0
         self.overflow_reruns = 0
         self.nomem_splits = 0
@@ -212,7 +215,7 @@ class Server:
             for i, r in enumerate(slot.reqs):
                 r.t_done = now
                 r.future.set_result(m[bounds[i]:bounds[i + 1], 1:])
-                self.done.append(r)
+                self.latencies.append(now - r.arrival)
         slot.reqs = []
         slot.busy = False
 
@@ -255,6 +258,12 @@ class Server:
         ones on free slots. Latency counts from the scheduled arrival."""
         if self.running:
             raise RuntimeError("run_trace needs the scheduler thread stopped")
+        # the interpreter's cycle collector stops the whole loop for tens of
+        # milliseconds once many objects are alive: pause it for the trace and
+        # re-enable it afterwards (reference counting still frees everything
+        # that is not in a cycle)
+        gc_was_enabled = gc.isenabled()
+        gc.disable()
         t0 = time.perf_counter() if t0 is None else t0
         due = t0 + np.asarray(arrivals, dtype=np.float64)
         futs: List[Future] = []
@@ -286,11 +295,21 @@ class Server:
                     time.sleep(max(0.0, min(nxt - time.perf_counter(), 20e-6)))
         finally:
             self.running = False
+            if gc_was_enabled:
+                gc.enable()
         return futs
 
     # -------------------------------------------------------------- reporting
+    def reset_stats(self):
+        """Forget completed requests and counters (between measured runs)."""
+        self.latencies = []
+        self.batches = 0
+        self.overflow_reruns = 0
+        self.nomem_splits = 0
+        self.bytes_scanned = 0
+
     def latency_stats(self) -> Dict[str, float]:
-        lat = np.array([r.t_done - r.arrival for r in self.done if r.t_done is not None])
+        lat = np.asarray(self.latencies, dtype=np.float64)
         if len(lat) == 0:
             return {}
         return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
