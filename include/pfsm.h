@@ -74,7 +74,11 @@ typedef struct {
 typedef struct {
     int32_t prefix_k;   /* depth of the start-prefix table: the first k steps of
                            every instance are looked up once per k-gram;
-                           -1 = off (every instance steps from q0) */
+                           -1 = off (every instance steps from q0); 0 = the
+                           deepest table of 16 bits of k-gram index for an
+                           NFA (14 for a DFA), lowered when an NFA's records
+                           outgrow 16-bit offsets; an explicit k that does
+                           not fit fails with E_INVAL, keeping the old table */
     int32_t tile;       /* starts owned by one CTA tile (multiple of 4096, at
                            most 49152; 0 = automatic: 16384, smaller for short
                            texts) */

@@ -29,10 +29,13 @@ int ceil_log2(int S) {
 }
 
 // Default depth of the start-prefix table: the k-gram index has k * sbits
-// bits; the table holds 2^(k*sbits) uint16 entries kept in shared memory.
+// bits; the table holds 2^(k*sbits) uint16 entries (shared memory when it
+// fits beside the rest, else L2). An NFA takes the deepest table (16 bits):
+// every prefix step it covers is a set union the scan no longer performs
+// per start (a record pool too large for 16-bit offsets lowers k at load).
 int default_k(const Machine &m) {
-    if (m.sbits >= 8) return m.kind == 0 ? 2 : 1;
-    const int max_bits = m.kind == 0 ? 14 : 12;   // 32 KB / 8 KB of entries
+    if (m.sbits >= 8) return 2;
+    const int max_bits = m.kind == 0 ? 14 : 16;   // 32 KB / 128 KB of entries
     int k = std::max(1, max_bits / m.sbits);
     return std::min(k, 8);
 }
@@ -450,15 +453,30 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     return PFSM_OK;
 }
 
-// Apply the params' prefix depth to the machine (rebuilding its table).
-int apply_k(pfsm_ctx *ctx, Machine &m) {
+// Apply the params' prefix depth to the machine (rebuilding its table). An
+// NFA whose records do not fit 16-bit pool offsets at that depth gets a
+// smaller one when `may_lower` (the depth was the default); otherwise the
+// previous table is rebuilt and E_INVAL returned.
+int apply_k(pfsm_ctx *ctx, Machine &m, bool may_lower) {
     const int k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
     if (k == m.k && (k == 0 || !m.memo.empty())) return PFSM_OK;
-    const bool was_resident = m.dev != nullptr;
+    const int old_k = m.k;
     release(ctx, m);
     m.k = k;
-    if (!build_memo(m)) return PFSM_E_INVAL;
-    (void)was_resident;
+    while (!build_memo(m)) {
+        if (!may_lower) {
+            m.k = old_k;
+            build_memo(m);
+            m.params.prefix_k = old_k > 0 ? old_k : -1;
+            return PFSM_E_INVAL;
+        }
+        if (--m.k <= 0) {
+            m.k = 0;
+            build_memo(m);
+            break;
+        }
+    }
+    m.params.prefix_k = m.k > 0 ? m.k : -1;
     return PFSM_OK;
 }
 
@@ -828,17 +846,13 @@ int pfsm_set_params(pfsm_ctx *ctx, pfsm_aut aut, const pfsm_params *p) {
     Machine &m = it->second;
     pfsm_params np{};
     if (p) np = *p;
+    const bool default_depth = np.prefix_k == 0;
     fill_defaults(m, np);
     int st = validate_params(m, np);
     if (st) return st;
     DeviceGuard g(ctx->device);
     m.params = np;
-    st = apply_k(ctx, m);
-    if (st) {
-        m.params.prefix_k = m.k > 0 ? m.k : -1;
-        return st;
-    }
-    return PFSM_OK;
+    return apply_k(ctx, m, default_depth);
 }
 
 int pfsm_get_params(pfsm_ctx *ctx, pfsm_aut aut, pfsm_params *out) {
