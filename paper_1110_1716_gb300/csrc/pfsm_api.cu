@@ -256,7 +256,7 @@ static bool survival_bits(const Machine &m, int mm, std::vector<uint32_t> &bits)
 }
 
 // Two filters: a shallow one kept in shared memory (<= 32 KB) and a deep
-// one read from global memory / L2 (<= 2 MB) for the starts that pass the
+// one read from global memory / L2 (<= 8 MB) for the starts that pass the
 // first.
 void build_survival(Machine &m) {
     m.surv.clear();
@@ -265,7 +265,7 @@ void build_survival(Machine &m) {
     m.sm_m2 = 0;
     const int m1 = std::min(9, 18 / m.sbits);
     if (m1 >= 1 && survival_bits(m, m1, m.surv)) m.sm_m = m1;
-    const int m2 = std::min(12, 24 / m.sbits);
+    const int m2 = std::min(13, 26 / m.sbits);
     if (m2 > m1 && survival_bits(m, m2, m.surv2)) m.sm_m2 = m2;
 }
 

@@ -63,6 +63,7 @@ constexpr unsigned long long ERR_TIMEOUT = 2ull;
 constexpr int NFA_SLOT = 8;       // states one lane holds for a small NFA set
 constexpr int STAGE = 128;        // largest per-warp match staging (entries)
 constexpr int SETTLE_PAIRS = 128; // per-warp pool of (start, state) pairs being settled
+constexpr int SETTLE_BURST = 4;   // symbols a lane advances its pair between warp syncs
 constexpr int WARP_LIST = 1024;   // surviving starts a warp lists per round (32 lanes x 32)
 // per-warp list area: the start offsets (uint16), the settling pool, the mark
 // bits and the pool count

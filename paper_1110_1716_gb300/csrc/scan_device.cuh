@@ -497,52 +497,57 @@ static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const T
         __syncwarp();
         if (!__any_sync(FULLMASK, has)) break;
         if (has && marked(marks, li)) has = false;
-        if (has) {
+        // each lane advances its pair up to SETTLE_BURST symbols between warp
+        // synchronisations (pairs forked on the way go to the pool with
+        // shared-memory atomics; a pair whose start another lane marked in
+        // the meantime only does some useless steps)
+        for (int burst = 0; burst < SETTLE_BURST && has; ++burst) {
             const uint32_t pos = start_pos + step;
             if (pos >= n) {
                 has = false;
-            } else if (pos >= tile_end || step >= max_steps) {
+                break;
+            }
+            if (pos >= tile_end || step >= max_steps) {
                 mark_entry(marks, li);
                 has = false;
-            } else {
-                const uint32_t c = tv.sm[pos - b];
-                const uint32_t row = c < static_cast<uint32_t>(mv.S) ? sm.band[q] : 0u;
-                if (row == BAND_CSR) {
+                break;
+            }
+            const uint32_t c = tv.sm[pos - b];
+            const uint32_t row = c < static_cast<uint32_t>(mv.S) ? sm.band[q] : 0u;
+            if (row == BAND_CSR) {
+                mark_entry(marks, li);
+                has = false;
+                break;
+            }
+            uint32_t m = (row >> (8 * c)) & 0xFFu;
+            bool first = true;
+            uint32_t nq = 0;
+            while (m) {
+                const uint32_t t = q + __ffs(m);
+                m &= m - 1;
+                if ((fin[t >> 5] >> (t & 31)) & 1u) {
                     mark_entry(marks, li);
-                    has = false;
+                    first = true;
+                    nq = 0xFFFFFFFFu;
+                    break;
+                }
+                if (first) {
+                    nq = t;
+                    first = false;
                 } else {
-                    uint32_t m = (row >> (8 * c)) & 0xFFu;
-                    bool first = true;
-                    uint32_t nq = 0;
-                    while (m) {
-                        const uint32_t t = q + __ffs(m);
-                        m &= m - 1;
-                        if ((fin[t >> 5] >> (t & 31)) & 1u) {
-                            mark_entry(marks, li);
-                            first = true;
-                            m = 0;
-                            nq = 0xFFFFFFFFu;
-                            break;
-                        }
-                        if (first) {
-                            nq = t;
-                            first = false;
-                        } else {
-                            const uint32_t slot = atomicAdd(pcount, 1u);
-                            if (slot < static_cast<uint32_t>(SETTLE_PAIRS))
-                                pairs[slot] = (li << 21) | ((step + 1) << 15) | t;
-                            else
-                                mark_entry(marks, li);
-                        }
-                    }
-                    if (first || nq == 0xFFFFFFFFu) {
-                        has = false;
-                    } else {
-                        q = nq;
-                        ++step;
-                    }
+                    const uint32_t slot = atomicAdd(pcount, 1u);
+                    if (slot < static_cast<uint32_t>(SETTLE_PAIRS))
+                        pairs[slot] = (li << 21) | ((step + 1) << 15) | t;
+                    else
+                        mark_entry(marks, li);
                 }
             }
+            if (first || nq == 0xFFFFFFFFu) {
+                has = false;
+                break;
+            }
+            q = nq;
+            ++step;
         }
         __syncwarp();
         if (lane == 0 && *pcount > static_cast<uint32_t>(SETTLE_PAIRS)) *pcount = SETTLE_PAIRS;
