@@ -84,10 +84,11 @@ def run_probe(args):
                           "params": P.pfsm_get_params(pf.ctx, aid)}))
 
 
-def kernel_traffic(name, text_bytes):
+def kernel_traffic(name, text_bytes, params=None):
     """DRAM bytes per launch of the scan kernel on `name`, scaled from the
     recorded ncu capture by text length (the kernel reads its text once), or
-    None when there is no capture or the kernel sources changed since."""
+    None when there is no capture, the kernel sources changed since, or the
+    scan runs with other parameters than the captured ones."""
     try:
         import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -98,6 +99,8 @@ def kernel_traffic(name, text_bytes):
                 h.update(f.read())
         w = rec["workloads"].get(name)
         if w is None or h.hexdigest() != rec["source_sha256"]:
+            return None
+        if params is not None and any(params.get(k) != v for k, v in w.get("params", {}).items()):
             return None
         return w["dram_bytes"] * text_bytes / w["captured_text_bytes"]
     except Exception:
@@ -263,7 +266,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "achieved": algo_bytes / (kernel_ms * 1e-3) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": algo_bytes / (kernel_ms * 1e-3) / 1e9 / hbm,
-                         "traffic": kernel_traffic(name, n), "peak_source": peak_kind,
+                         "traffic": kernel_traffic(name, n, P.pfsm_get_params(pf.ctx, aid)),
+                         "peak_source": peak_kind,
                          "algorithmic_bytes": algo_bytes},
             "clocks": clk.summary(), "gpu_launches": launches_per_step * steps,
             "wall_s": wall,

@@ -813,12 +813,29 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                     }
                     if (sm.surv) {
                         const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+                        if ((SB == 2 || SB == 8) && gown == 8 && i0 + 8 * g + 7 + mm <= n) {
+                            // all eight starts have their m-gram: branch-free
+                            // indices and keep bits
+                            const uint32_t x0 = static_cast<uint32_t>(lo);
+                            const uint32_t x1 = static_cast<uint32_t>(lo >> 32);
+                            const uint32_t x2 = static_cast<uint32_t>(hi);
+                            uint32_t keep = 0;
 #pragma unroll
-                        for (int r = 0; r < 8; ++r) {
-                            const uint32_t i = i0 + 8 * g + r;
-                            if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
-                                const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
-                                if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << (8 * g + r));
+                            for (int r = 0; r < 8; ++r) {
+                                const uint32_t idx =
+                                    SB == 2 ? (p2 >> (2 * r)) & mmask
+                                            : __funnelshift_r(r < 4 ? x0 : x1, r < 4 ? x1 : x2, 8 * (r & 3)) & mmask;
+                                keep |= ((sm.surv[idx >> 5] >> (idx & 31)) & 1u) << r;
+                            }
+                            live &= ~(0xFFu << (8 * g)) | (keep << (8 * g));
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                const uint32_t i = i0 + 8 * g + r;
+                                if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
+                                    const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
+                                    if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << (8 * g + r));
+                                }
                             }
                         }
                     }
