@@ -233,6 +233,13 @@ int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_t S, int32_
 /* ------------------------------------------------------------------ misc */
 int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);
 
+/* Device bytes that automaton `aut` holds while resident (its encoded
+ * tables; every automaton of one batch must fit the budget together), and
+ * in *resident whether it is resident now (either pointer may be NULL).
+ * The paper has no counterpart: this is a query for callers that pack
+ * batches under a residency budget. Errors: E_INVAL, E_NOENT. */
+int pfsm_aut_bytes(pfsm_ctx *ctx, pfsm_aut aut, uint64_t *bytes, int32_t *resident);
+
 /* Kernel timing: when enabled, every scan records CUDA events around its
  * tile kernel (a batch: around its graph) on the scan's stream;
  * pfsm_kernel_time returns the summed milliseconds and launch count since

@@ -32,7 +32,7 @@ PFSM_E_CUDA = 6
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
-           "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc")
+           "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes")
 
 
 class pfsm_params(ctypes.Structure):
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
         "pfsm_strerror": [ctypes.c_int],
         "pfsm_scan_dfa_noalloc": [P, I32, I32, I32, I32, P, P, U64, P, U64, P, P],
+        "pfsm_aut_bytes": [P, I32, ctypes.POINTER(U64), ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +288,14 @@ def pfsm_get_stats(ctx: int) -> dict:
     s = pfsm_stats()
     _check(load_library().pfsm_get_stats(ctx, ctypes.byref(s)), "pfsm_get_stats")
     return s.as_dict()
+
+
+def pfsm_aut_bytes(ctx: int, aut: int):
+    """(device bytes of `aut` while resident, resident now)."""
+    b = ctypes.c_uint64()
+    r = ctypes.c_int32()
+    _check(load_library().pfsm_aut_bytes(ctx, aut, ctypes.byref(b), ctypes.byref(r)), "pfsm_aut_bytes")
+    return b.value, bool(r.value)
 
 
 def pfsm_set_timing(ctx: int, enable: bool) -> None:

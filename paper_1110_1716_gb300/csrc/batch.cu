@@ -214,6 +214,7 @@ static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine 
 struct BatchPlan {
     std::vector<BatchJob> jobs;
     std::vector<DevMachine> machs;
+    std::vector<Machine *> used;            // the machines the batch reads
     uint32_t mask = 0;                      // classes with work
     uint32_t job_lo[kBatchClasses] = {}, job_hi[kBatchClasses] = {};
     uint32_t nunits[kBatchClasses] = {}, unit_tiles[kBatchClasses] = {};
@@ -222,7 +223,8 @@ struct BatchPlan {
 
 // Validate the jobs, make their machines resident, classify them and cut
 // every class's texts into work units.
-static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan &pl) {
+static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan &pl,
+                      cudaStream_t s) {
     ctx->epoch++;
     // machine slot of every job (slots numbered in order of first use)
     std::map<int, uint32_t> slot_of;
@@ -249,7 +251,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     }
     if (ids.size() >= (1u << 24)) return PFSM_E_INVAL;
     for (int id : ids) {
-        int st = make_resident(ctx, id, ctx->machines[id]);
+        int st = make_resident(ctx, id, ctx->machines[id], s);
         if (st) return st;
     }
     // the DFA classes share one shape (threads, arena), as do the NFA classes
@@ -264,6 +266,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
         Machine &m = ctx->machines[ids[i]];
         DevMachine d = m.dm;
         const BatchShape &sh = ctx->batch_shape[m.kind == 1 ? 6 : 0];
+        pl.used.push_back(&m);
         cls_of[i] = place_tables(m, sh.arena, sh.threads / 32, d);
         if (m.kind == 1 && d.a_coop == kNotStaged) pl.wq[cls_of[i]] = std::max(pl.wq[cls_of[i]], d.Wq);
         pl.machs.push_back(d);
@@ -371,7 +374,7 @@ static int graph_for(pfsm_ctx *ctx, BatchState *b, uint32_t mask, cudaGraphExec_
 static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out,
                          uint64_t cap, cudaStream_t s, BatchState **bs) {
     BatchPlan pl;
-    int st = plan_batch(ctx, jobs, k, pl);
+    int st = plan_batch(ctx, jobs, k, pl, s);
     // the pins protect this batch's machines while it is planned; once its
     // pointers are recorded they may be evicted again (an eviction frees
     // device memory with cudaFree, which waits for work in flight)
@@ -436,6 +439,8 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
         cudaEventRecord(slot->ev[2 * ev], s);
     }
     if (cudaGraphLaunch(exec, s) != cudaSuccess) return PFSM_E_CUDA;
+    st = mark_use(ctx, s, pl.used.data(), pl.used.size());
+    if (st) return st;
     if (slot) {
         cudaEventRecord(slot->ev[2 * ev + 1], s);
         slot->ev_head = (slot->ev_head + 1) % kEventRing;

@@ -284,16 +284,43 @@ size_t device_bytes(const Machine &m) {
     return b;
 }
 
+// Frees a machine's device image once nothing can still read it: the host
+// waits for the machine's last uses on every stream and for its upload, then
+// returns the memory to the pool (API calls: evict, unload, new parameters).
 void release(pfsm_ctx *ctx, Machine &m) {
-    if (m.dev) {
-        cudaFree(m.dev);
-        m.dev = nullptr;
-        ctx->resident_bytes -= m.dev_bytes;
-        m.dev_bytes = 0;
-    }
+    if (!m.dev) return;
+    for (auto &u : m.uses) cudaEventSynchronize(u.second);
+    if (m.ready) cudaEventSynchronize(m.ready);
+    cudaFreeAsync(m.dev, nullptr);
+    m.dev = nullptr;
+    m.uses.clear();
+    ctx->resident_bytes -= m.dev_bytes;
+    m.dev_bytes = 0;
 }
 
-int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id) {
+void drop_host_image(Machine &m) {
+    if (m.host_img) cudaFreeHost(m.host_img);
+    m.host_img = nullptr;
+    m.img_bytes = 0;
+}
+
+// Eviction without a host or device synchronisation: stream `s` waits for
+// the victim's last use on every stream and for its upload, then frees it
+// into the pool at that point of `s`; a later allocation on `s` may reuse
+// the memory in stream order.
+static void release_async(pfsm_ctx *ctx, Machine &m, cudaStream_t s) {
+    if (!m.dev) return;
+    for (auto &u : m.uses)
+        if (u.first != s) cudaStreamWaitEvent(s, u.second, 0);
+    if (m.ready) cudaStreamWaitEvent(s, m.ready, 0);
+    cudaFreeAsync(m.dev, s);
+    m.dev = nullptr;
+    m.uses.clear();
+    ctx->resident_bytes -= m.dev_bytes;
+    m.dev_bytes = 0;
+}
+
+int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id, cudaStream_t s) {
     while (ctx->resident_bytes + need > ctx->budget) {
         Machine *victim = nullptr;
         for (auto &kv : ctx->machines) {
@@ -302,31 +329,55 @@ int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id) {
             if (!victim || kv.second.last_use < victim->last_use) victim = &kv.second;
         }
         if (!victim) return PFSM_E_NOMEM;
-        release(ctx, *victim);
+        release_async(ctx, *victim, s);
         ctx->n_evict++;
     }
     return PFSM_OK;
 }
 
-int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
-    m.last_use = ++ctx->clock;
-    if (m.dev) return PFSM_OK;
+// The device image of `m`, built once in pinned host memory: 256-byte
+// aligned sections (prefix table, short-gram table, survival bitmaps, then
+// the DFA table or the NFA CSR, records and band image).
+static int build_host_image(Machine &m) {
+    if (m.host_img) return PFSM_OK;
     const size_t bytes = device_bytes(m);
-    int st = evict_lru(ctx, bytes, id);
-    if (st) return st;
-    void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    void *h = nullptr;
+    if (cudaMallocHost(&h, bytes) != cudaSuccess) {
         cudaGetLastError();
         return PFSM_E_NOMEM;
     }
-    std::vector<uint8_t> img(bytes, 0);
+    uint8_t *img = static_cast<uint8_t *>(h);
+    memset(img, 0, bytes);
     size_t o = 0;
-    auto put = [&](const void *src, size_t n) {
+    auto put = [&](const void *src, size_t n, size_t pad) {
         const size_t at = o;
-        if (n) memcpy(img.data() + o, src, n);
-        o += align256(n + 4);
+        if (n) memcpy(img + o, src, n);
+        o += align256(n + pad);
         return at;
     };
+    m.o_memo = put(m.memo.data(), m.memo.size() * 2, 4);
+    m.o_tail = put(m.tail.data(), m.tail.size() * 2, 4);
+    m.o_surv = put(m.surv.data(), m.surv.size() * 4, 4);
+    m.o_surv2 = put(m.surv2.data(), m.surv2.size() * 4, 4);
+    if (m.kind == 0) {
+        m.o_tab = put(m.dtab.data(), m.dtab.size() * 2, 4);
+    } else {
+        m.o_off = put(m.off.data(), m.off.size() * 4, 0);
+        m.o_tgt = put(m.tgt.data(), m.tgt.size() * 2, 4);
+        m.o_pool = put(m.pool.data(), m.pool.size() * 4, 0);
+        m.o_band = put(m.band.data(), m.band.size() * 4, 0);
+    }
+    if (o > bytes) {   // layout and size disagree: a bug, fail loudly
+        cudaFreeHost(h);
+        return PFSM_E_INVAL;
+    }
+    m.host_img = img;
+    m.img_bytes = bytes;
+    return PFSM_OK;
+}
+
+// The kernels' view of a machine whose image starts at `base`.
+static DevMachine dev_view(const Machine &m, uint8_t *base) {
     DevMachine dm{};
     dm.kind = m.kind;
     dm.Q = m.Q;
@@ -336,53 +387,87 @@ int make_resident(pfsm_ctx *ctx, int id, Machine &m) {
     dm.sbits = m.sbits;
     dm.memo_n = m.k > 0 ? (1u << (m.k * m.sbits)) : 0;
     dm.Wq = (m.Q + 31) / 32;
-    uint8_t *base = static_cast<uint8_t *>(p);
-    const size_t o_memo = put(m.memo.data(), m.memo.size() * 2);
-    dm.memo = reinterpret_cast<const uint16_t *>(base + o_memo);
-    const size_t o_tail = put(m.tail.data(), m.tail.size() * 2);
-    dm.tail = m.tail.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + o_tail);
-    const size_t o_surv = put(m.surv.data(), m.surv.size() * 4);
-    dm.surv = m.surv.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv);
+    dm.memo = reinterpret_cast<const uint16_t *>(base + m.o_memo);
+    dm.tail = m.tail.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_tail);
+    dm.surv = m.surv.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_surv);
     dm.surv_m = m.sm_m;
     dm.surv_words = static_cast<uint32_t>(m.surv.size());
-    const size_t o_surv2 = put(m.surv2.data(), m.surv2.size() * 4);
-    dm.surv2 = m.surv2.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_surv2);
+    dm.surv2 = m.surv2.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_surv2);
     dm.surv2_m = m.sm_m2;
     if (m.kind == 0) {
-        const size_t o_tab = put(m.dtab.data(), m.dtab.size() * 2);
-        dm.dtab = reinterpret_cast<const uint16_t *>(base + o_tab);
+        dm.dtab = reinterpret_cast<const uint16_t *>(base + m.o_tab);
     } else {
-        o = align256(o);
-        const size_t o_off = o;
-        memcpy(img.data() + o, m.off.data(), m.off.size() * 4);
-        o += align256(m.off.size() * 4);
-        const size_t o_tgt = put(m.tgt.data(), m.tgt.size() * 2);
-        const size_t o_pool = o;
-        memcpy(img.data() + o, m.pool.data(), m.pool.size() * 4);
-        o += align256(m.pool.size() * 4);
-        const size_t o_band = o;
-        if (!m.band.empty()) memcpy(img.data() + o, m.band.data(), m.band.size() * 4);
-        o += align256(m.band.size() * 4);
-        dm.off = reinterpret_cast<const uint32_t *>(base + o_off);
-        dm.tgt = reinterpret_cast<const uint16_t *>(base + o_tgt);
-        dm.pool = reinterpret_cast<const uint32_t *>(base + o_pool);
+        dm.off = reinterpret_cast<const uint32_t *>(base + m.o_off);
+        dm.tgt = reinterpret_cast<const uint16_t *>(base + m.o_tgt);
+        dm.pool = reinterpret_cast<const uint32_t *>(base + m.o_pool);
         dm.pool_n = static_cast<uint32_t>(m.pool.size());
-        dm.band = m.band.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + o_band);
+        dm.band = m.band.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_band);
     }
-    if (o > bytes) {   // layout and size disagree: a bug, fail loudly
-        cudaFree(p);
-        return PFSM_E_INVAL;
+    return dm;
+}
+
+// Makes `m` resident for work enqueued on `s`: a resident machine only makes
+// `s` wait for its upload (when that has not finished yet); otherwise the
+// least recently used machines are evicted in stream order, an image is
+// taken from the pool and the pinned host image is copied in on `s`.
+int make_resident(pfsm_ctx *ctx, int id, Machine &m, cudaStream_t s) {
+    m.last_use = ++ctx->clock;
+    if (!m.ready && cudaEventCreateWithFlags(&m.ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return PFSM_E_CUDA;
     }
-    if (cudaMemcpy(p, img.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(p);
+    if (m.dev) {
+        if (cudaEventQuery(m.ready) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamWaitEvent(s, m.ready, 0);
+        }
+        return PFSM_OK;
+    }
+    int st = build_host_image(m);
+    if (st) return st;
+    const size_t bytes = m.img_bytes;
+    st = evict_lru(ctx, bytes, id, s);
+    if (st) return st;
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, ctx->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PFSM_E_NOMEM;
+    }
+    if (cudaMemcpyAsync(p, m.host_img, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(m.ready, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(p, s);
         return PFSM_E_CUDA;
     }
     m.dev = p;
     m.dev_bytes = bytes;
-    m.dm = dm;
+    m.dm = dev_view(m, static_cast<uint8_t *>(p));
     ctx->resident_bytes += bytes;
     if (m.was_resident) ctx->n_reload++;
     m.was_resident = true;
+    return PFSM_OK;
+}
+
+// Records that the work just enqueued on `s` reads the images of ms[0..k).
+int mark_use(pfsm_ctx *ctx, cudaStream_t s, Machine *const *ms, size_t k) {
+    UseRing &r = ctx->use_rings[s];
+    cudaEvent_t &ev = r.ev[r.head];
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return PFSM_E_CUDA;
+    }
+    r.head = (r.head + 1) % kUseRing;
+    if (cudaEventRecord(ev, s) != cudaSuccess) return PFSM_E_CUDA;
+    for (size_t i = 0; i < k; ++i) {
+        Machine &m = *ms[i];
+        bool found = false;
+        for (auto &u : m.uses)
+            if (u.first == s) {
+                u.second = ev;
+                found = true;
+            }
+        if (!found) m.uses.emplace_back(s, ev);
+    }
     return PFSM_OK;
 }
 
@@ -462,6 +547,7 @@ int apply_k(pfsm_ctx *ctx, Machine &m, bool may_lower) {
     if (k == m.k && (k == 0 || !m.memo.empty())) return PFSM_OK;
     const int old_k = m.k;
     release(ctx, m);
+    drop_host_image(m);   // the prefix tables change: rebuild the image
     m.k = k;
     while (!build_memo(m)) {
         if (!may_lower) {
@@ -606,7 +692,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     auto it = ctx->machines.find(aut);
     if (it == ctx->machines.end()) return PFSM_E_NOENT;
     Machine &m = it->second;
-    int st = make_resident(ctx, aut, m);
+    int st = make_resident(ctx, aut, m, s);
     if (st) return st;
     if (cudaMemsetAsync(status, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
         return PFSM_E_CUDA;
@@ -643,6 +729,11 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     if (m.kind == 0) {
         e = launch_carry(pl.a, 2 * ctx->nsm, s);
         if (e != cudaSuccess) return PFSM_E_CUDA;
+    }
+    {
+        Machine *mp = &m;
+        st = mark_use(ctx, s, &mp, 1);
+        if (st) return st;
     }
     return PFSM_OK;
 }
@@ -681,6 +772,20 @@ int pfsm_ctx_create(int device, uint64_t budget_bytes, pfsm_ctx **out) {
     c->nsm = prop.multiProcessorCount;
     c->smem_sm = static_cast<uint32_t>(prop.sharedMemPerMultiprocessor);
     c->smem_rsv = static_cast<uint32_t>(prop.reservedSharedMemPerBlock);
+    // machine images come from a pool of this context that keeps freed
+    // memory for reuse (evictions and reloads cost no allocator round trip)
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &pp) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PFSM_E_CUDA;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     *out = c;
     return PFSM_OK;
 }
@@ -689,7 +794,14 @@ int pfsm_ctx_destroy(pfsm_ctx *ctx) {
     if (!ctx) return PFSM_OK;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    for (auto &kv : ctx->machines) release(ctx, kv.second);
+    for (auto &kv : ctx->machines) {
+        release(ctx, kv.second);
+        drop_host_image(kv.second);
+        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+    }
+    for (auto &kv : ctx->use_rings)
+        for (int i = 0; i < kUseRing; ++i)
+            if (kv.second.ev[i]) cudaEventDestroy(kv.second.ev[i]);
     for (auto &kv : ctx->slots) {
         cudaFree(kv.second.coop);
         cudaFree(kv.second.status);
@@ -697,6 +809,8 @@ int pfsm_ctx_destroy(pfsm_ctx *ctx) {
         for (int i = 0; i < 2 * kEventRing; ++i) cudaEventDestroy(kv.second.ev[i]);
     }
     batch_free(ctx);
+    cudaDeviceSynchronize();
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return PFSM_OK;
 }
@@ -720,8 +834,11 @@ static int finish_load(pfsm_ctx *ctx, Machine &&m, pfsm_aut *out_id) {
     auto &slot = ctx->machines[id];
     slot = std::move(m);
     ctx->n_loads++;
-    int st = make_resident(ctx, id, slot);
+    int st = make_resident(ctx, id, slot, nullptr);
+    if (!st && cudaEventSynchronize(slot.ready) != cudaSuccess) st = PFSM_E_CUDA;
     if (st) {
+        drop_host_image(slot);
+        if (slot.ready) cudaEventDestroy(slot.ready);
         ctx->machines.erase(id);
         return st;
     }
@@ -829,12 +946,23 @@ int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut) {
     return PFSM_OK;
 }
 
+int pfsm_aut_bytes(pfsm_ctx *ctx, pfsm_aut aut, uint64_t *bytes, int32_t *resident) {
+    if (!ctx) return PFSM_E_INVAL;
+    auto it = ctx->machines.find(aut);
+    if (it == ctx->machines.end()) return PFSM_E_NOENT;
+    if (bytes) *bytes = device_bytes(it->second);
+    if (resident) *resident = it->second.dev ? 1 : 0;
+    return PFSM_OK;
+}
+
 int pfsm_unload(pfsm_ctx *ctx, pfsm_aut aut) {
     if (!ctx) return PFSM_E_INVAL;
     auto it = ctx->machines.find(aut);
     if (it == ctx->machines.end()) return PFSM_E_NOENT;
     DeviceGuard g(ctx->device);
     release(ctx, it->second);
+    drop_host_image(it->second);
+    if (it->second.ready) cudaEventDestroy(it->second.ready);
     ctx->machines.erase(it);
     return PFSM_OK;
 }

@@ -35,9 +35,18 @@ struct Machine {
     int sm_m = 0, sm_m2 = 0;
     std::vector<uint32_t> surv, surv2;   // shallow (shared memory) and deep (global) bitmaps
     pfsm_params params{};
-    // residency
+    // residency: the device image is built once in pinned host memory and
+    // copied in on the scan's stream whenever the machine becomes resident
     void *dev = nullptr;
     size_t dev_bytes = 0;
+    uint8_t *host_img = nullptr;      // pinned copy of the device image
+    size_t img_bytes = 0;
+    size_t o_memo = 0, o_tail = 0, o_surv = 0, o_surv2 = 0, o_tab = 0, o_off = 0,
+           o_tgt = 0, o_pool = 0, o_band = 0;   // section offsets in the image
+    cudaEvent_t ready = nullptr;      // recorded after the last upload
+    // last use per stream (an event recorded after a launch that read the
+    // image); an eviction orders its free after every one of them
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
     DevMachine dm{};
     uint64_t last_use = 0;
     uint64_t pin = 0;        // batch epoch that needs it resident
@@ -57,6 +66,12 @@ struct Slot {   // per-stream scratch
 };
 
 struct BatchState;   // batch.cu
+
+constexpr int kUseRing = 64;   // use events kept per stream
+struct UseRing {             // events marking launches that read machine images
+    cudaEvent_t ev[kUseRing] = {};
+    int head = 0;
+};
 
 // Launch shape of one batch class (batch.cu), fixed per context until the
 // batch parameters change: the layout of everything but the table arena,
@@ -94,6 +109,8 @@ struct pfsm_ctx {
     std::map<int, pfsm::Machine> machines;
     int next_id = 1;
     std::map<cudaStream_t, pfsm::Slot> slots;
+    cudaMemPool_t pool = nullptr;     // stream-ordered pool of machine images
+    std::map<cudaStream_t, pfsm::UseRing> use_rings;
     std::mutex mu;
     bool timing = false;
     double time_ms = 0.0;
@@ -116,7 +133,9 @@ bool build_memo(Machine &m);
 void build_survival(Machine &m);
 size_t align256(size_t x);
 void release(pfsm_ctx *ctx, Machine &m);
-int make_resident(pfsm_ctx *ctx, int id, Machine &m);
+void drop_host_image(Machine &m);
+int make_resident(pfsm_ctx *ctx, int id, Machine &m, cudaStream_t s);
+int mark_use(pfsm_ctx *ctx, cudaStream_t s, Machine *const *ms, size_t k);
 Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s);
 int ensure_words(uint32_t **buf, size_t *have, size_t need);
 void collect_timing(pfsm_ctx *ctx, Slot *slot, int keep);

@@ -27,8 +27,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import (PFSM_E_NOMEM, PFSM_OK, Pfsm, PfsmError, pfsm_get_stats, pfsm_scan_batch,
-               pfsm_scan_batch_async)
+from . import (PFSM_E_NOMEM, PFSM_OK, Pfsm, PfsmError, pfsm_aut_bytes, pfsm_get_stats,
+               pfsm_scan_batch, pfsm_scan_batch_async)
 
 
 class Request:
@@ -78,6 +78,10 @@ class Server:
         self.torch = torch
         self.pf = pf
         self.ids = [pf.load(a) for a in automata]
+        # device bytes of each machine and the context's budget: a batch
+        # takes requests only while its distinct machines fit together
+        self.aut_bytes = [pfsm_aut_bytes(pf.ctx, i)[0] for i in self.ids]
+        self.budget = pfsm_get_stats(pf.ctx)["budget_bytes"]
         dev = torch.device("cuda", pf.device)
         self.slots = [_Slot(torch, dev, slot_bytes, out_rows, max_jobs) for _ in range(slots)]
         self.pending = collections.deque()
@@ -127,21 +131,31 @@ class Server:
 
     # -------------------------------------------------------------- scheduler
     def _admit(self, slot: _Slot, one_machine: bool = False) -> bool:
-        """Pack pending requests into a free slot and launch its batch. With
-        `one_machine`, only requests for the first pending request's machine
-        are taken (used when the machines of a mixed batch do not fit the
-        residency budget together)."""
+        """Pack pending requests into a free slot and launch its batch, in
+        arrival order, skipping (for the next batch) requests whose machine
+        would take the batch's distinct machines over the residency budget.
+        With `one_machine`, only requests for the first pending request's
+        machine are taken (the fallback when the library still reports that
+        the machines do not fit)."""
         reqs, used, skipped = [], 0, []
+        machines, mbytes = set(), 0
         with self.lock:
             first = self.pending[0].aut if self.pending else None
-            while self.pending and len(reqs) < slot.max_jobs:
+            scanned = 0
+            while self.pending and len(reqs) < slot.max_jobs and scanned < 4 * slot.max_jobs:
                 r = self.pending[0]
                 if used + len(r.text) > slot.text_bytes:
                     break
                 self.pending.popleft()
-                if one_machine and r.aut != first:
+                scanned += 1
+                new = r.aut not in machines
+                if (one_machine and r.aut != first) or (
+                        new and machines and mbytes + self.aut_bytes[r.aut] > self.budget):
                     skipped.append(r)
                     continue
+                if new:
+                    machines.add(r.aut)
+                    mbytes += self.aut_bytes[r.aut]
                 reqs.append(r)
                 used += (len(r.text) + 15) & ~15
             for r in reversed(skipped):

@@ -334,6 +334,51 @@ def test_eviction_and_reload(pf):
         small.close()
 
 
+def test_eviction_orders_after_scans_in_flight_on_other_streams(pf):
+    """Room for one machine only: every scan evicts the other machine, whose
+    scan may still be running on the other stream. The eviction is ordered
+    after that scan (its use event) and the reload after the eviction, all
+    without a host synchronisation; both match sets stay exact."""
+    motifs = W.motif_set(61, n_motifs=64)
+    nfa = W.motif_nfa(motifs)[0]
+    dfa = W.dfa_random(62, Q=64, S=4)
+    t_n = W.text_dna(400_000, 63)
+    W.plant_motifs(t_n, motifs, 2_000, 64)
+    t_d = W.text_uniform(150_000, 4, 65)
+    want_n, want_d = oracle.scan(nfa, t_n), oracle.scan(dfa, t_d)
+    probe = P.Pfsm(0)
+    try:
+        sizes = [P.pfsm_aut_bytes(probe.ctx, probe.load(x))[0] for x in (nfa, dfa)]
+    finally:
+        probe.close()
+    small = P.Pfsm(0, budget_bytes=max(sizes) + 256)
+    try:
+        ids = [small.load(nfa), small.load(dfa)]
+        assert P.pfsm_aut_bytes(small.ctx, ids[0]) == (sizes[0], False)   # evicted by the second load
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        tn, td = small.to_device(t_n), small.to_device(t_d)
+        outs = [torch.empty((len(want_n) + 64, 3), dtype=torch.int32, device="cuda") for _ in range(3)]
+        outd = [torch.empty((len(want_d) + 64, 3), dtype=torch.int32, device="cuda") for _ in range(3)]
+        sts = torch.zeros((6, 2), dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        for r in range(3):
+            P.pfsm_scan_async(small.ctx, ids[0], tn, None, outs[r], sts[2 * r], stream=s1)
+            P.pfsm_scan_async(small.ctx, ids[1], td, None, outd[r], sts[2 * r + 1], stream=s2)
+        torch.cuda.synchronize()
+        st = sts.cpu().numpy()
+        for r in range(3):
+            assert st[2 * r, 1] == 0 and st[2 * r + 1, 1] == 0
+            got_n = oracle.sort_matches(outs[r][:st[2 * r, 0]].cpu().numpy().view(np.uint32))
+            got_d = oracle.sort_matches(outd[r][:st[2 * r + 1, 0]].cpu().numpy().view(np.uint32))
+            assert np.array_equal(got_n, want_n), r
+            assert np.array_equal(got_d, want_d), r
+        stats = P.pfsm_get_stats(small.ctx)
+        assert stats["evictions"] >= 5 and stats["reloads"] >= 5
+        assert stats["resident_bytes"] <= max(sizes) + 256
+    finally:
+        small.close()
+
+
 def test_async_status_and_stream(pf):
     d, t = W.workload_dna_dfa(2, n=200_000)
     a = pf.load(d)
