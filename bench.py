@@ -303,6 +303,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.only and not args.no_serve:
         others["serving"] = measure_serving(P, pf, torch, dev)
     if not args.only:
+        others["long_lived_dfa_16kib"] = measure_partitioning(P, pf, torch, dev)
+    if not args.only:
         for name in WORKLOADS:
             if name == args.workload:
                 continue
@@ -396,6 +398,39 @@ def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
             "device_gbps": total_bytes / (dev_ms / max(1, nlaunch) * 1e-3) / 1e9,
             "plain_loop_ms": plain_ms, "plain_gbps": total_bytes / (plain_ms * 1e-3) / 1e9,
             "speedup_vs_plain": plain_ms / batch_ms, "generate_s": gen_s}
+
+
+def measure_partitioning(P, pf, torch, dev, n=16 << 10, steps=10):
+    """Lazy against chained partitioning (Sec. III.D.2) where every instance
+    lives to the end of the text: a 6-state DFA without a dead state, so the
+    match count grows with n^2 (the paper's worst case)."""
+    d = W.dfa_random(18, Q=6, S=4, dead=-1, finals=[1, 4], p_dead=0.0)
+    t = W.text_uniform(n, 4, 19)
+    aid = pf.load(d)
+    tt = pf.to_device(t)
+    st, cnt = P.pfsm_scan(pf.ctx, aid, tt, None, None, 0)
+    out = torch.empty((int(cnt) + 1024, 3), dtype=torch.int32, device=dev)
+    status = torch.zeros(2, dtype=torch.int64, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    res = {"desc": "6-state DFA without a dead state, 16 KiB uniform DNA: every instance lives "
+                   "to the end of the text", "bytes": n, "matches": int(cnt)}
+    for name, part in (("lazy", 1), ("chained", 2)):
+        P.pfsm_set_params(pf.ctx, aid, {"partition": part, "tile": 4096})
+        ms = []
+        for i in range(steps + 2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            P.pfsm_scan_async(pf.ctx, aid, tt, None, out, status, stream=s)
+            e1.record(s)
+            s.synchronize()
+            if i >= 2:
+                ms.append(e0.elapsed_time(e1))
+        assert int(status[0].item()) == cnt and int(status[1].item()) == 0
+        m = float(np.median(ms))
+        res[name] = {"ms": m, "matches_per_s": cnt / (m * 1e-3)}
+    P.pfsm_unload(pf.ctx, aid)
+    return res
 
 
 def serve_texts(w, seed=0):

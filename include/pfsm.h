@@ -90,6 +90,12 @@ typedef struct {
     int32_t settle;     /* NFA: steps a surviving instance is advanced in the
                            filter before it is queued for the exact path
                            (0 = library default, -1 = queue at once) */
+    int32_t partition;  /* instances alive past their tile's staged text
+                           (Sec. III.D.2): 1 = lazy (continue in place on the
+                           global text), 2 = chained (DFA only: hand the
+                           (start, position, state) to a carry queue finished
+                           by a second kernel); 0 = default (DFA chained, NFA
+                           lazy). 2 for an NFA is E_INVAL. */
 } pfsm_params;
 
 /* Residency counters of a context. */
@@ -186,6 +192,24 @@ int pfsm_scan_async(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64
  * Blocks until done. Errors: as pfsm_scan, per job. */
 int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out_dev,
                     uint64_t cap, uint64_t *counts, uint64_t *total, void *stream);
+
+/* A union machine (Sec. III.A): automata auts[0..k), DFAs and NFAs mixed,
+ * over one device text. The union through an ancillary initial state with
+ * epsilon edges to each component's q0 has exactly the union of the
+ * components' match sets; here every component runs as one job of a batch
+ * over the same text, and a match's `text` field is the index of its
+ * component in auts (its `state` is that component's own state id).
+ * Components are the caller's loaded automata: adding or removing one is a
+ * pfsm_load_* or pfsm_unload between calls, and scans already enqueued keep
+ * the images they read (an unloaded automaton still in use is freed when
+ * its last scan completes). Arguments, output and errors as
+ * pfsm_scan_batch / pfsm_scan_batch_async. */
+int pfsm_scan_union(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k, const uint8_t *text_dev,
+                    uint64_t n, pfsm_bmatch *out_dev, uint64_t cap, uint64_t *counts,
+                    uint64_t *total, void *stream);
+int pfsm_scan_union_async(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k,
+                          const uint8_t *text_dev, uint64_t n, pfsm_bmatch *out_dev,
+                          uint64_t cap, uint64_t *status_dev, void *stream);
 
 /* Launch shape of batches on this context: `threads` (128, 256 or 512 per
  * CTA), `ctas_per_sm` (1 to 4) and `tile` (multiple of 4096, at most 32768)

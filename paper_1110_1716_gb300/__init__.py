@@ -32,14 +32,16 @@ PFSM_E_CUDA = 6
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
-           "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes")
+           "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes",
+           "pfsm_scan_union", "pfsm_scan_union_async")
 
 
 class pfsm_params(ctypes.Structure):
     _fields_ = [("prefix_k", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("halo", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("spt", ctypes.c_int32), ("table_smem", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("settle", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("settle", ctypes.c_int32),
+                ("partition", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +102,8 @@ def load_library(path: str = LIB_PATH):
         "pfsm_strerror": [ctypes.c_int],
         "pfsm_scan_dfa_noalloc": [P, I32, I32, I32, I32, P, P, U64, P, U64, P, P],
         "pfsm_aut_bytes": [P, I32, ctypes.POINTER(U64), ctypes.POINTER(I32)],
+        "pfsm_scan_union": [P, P, I32, P, U64, P, U64, P, ctypes.POINTER(U64), P],
+        "pfsm_scan_union_async": [P, P, I32, P, U64, P, U64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +276,34 @@ def pfsm_scan_batch_async(ctx: int, jobs: Sequence, out, status, cap: Optional[i
     _check(load_library().pfsm_scan_batch_async(ctx, ptr, k, _dev_ptr(out), cap,
                                                 _dev_ptr(status), _stream_ptr(stream)),
            "pfsm_scan_batch_async")
+
+
+def pfsm_scan_union(ctx: int, auts: Sequence[int], text, n: Optional[int], out,
+                    cap: Optional[int] = None, stream=None):
+    """Union machine over one CUDA text: (status, per-component counts,
+    total); `out` rows are (component index, start, end, state)."""
+    k = len(auts)
+    a = np.ascontiguousarray(auts, dtype=np.int32)
+    n = text.numel() if n is None else n
+    cap = (out.shape[0] if out is not None else 0) if cap is None else cap
+    counts = np.zeros(max(1, k), dtype=np.uint64)
+    total = ctypes.c_uint64()
+    st = load_library().pfsm_scan_union(ctx, a.ctypes.data, k, _dev_ptr(text), n, _dev_ptr(out), cap,
+                                        counts.ctypes.data, ctypes.byref(total), _stream_ptr(stream))
+    if st not in (PFSM_OK, PFSM_E_OVERFLOW):
+        _check(st, "pfsm_scan_union")
+    return st, counts[:k], total.value
+
+
+def pfsm_scan_union_async(ctx: int, auts: Sequence[int], text, n: Optional[int], out, status,
+                          cap: Optional[int] = None, stream=None) -> None:
+    """Enqueue a union scan; `status` as for pfsm_scan_batch_async."""
+    a = np.ascontiguousarray(auts, dtype=np.int32)
+    n = text.numel() if n is None else n
+    cap = (out.shape[0] if out is not None else 0) if cap is None else cap
+    _check(load_library().pfsm_scan_union_async(ctx, a.ctypes.data, len(a), _dev_ptr(text), n,
+                                                _dev_ptr(out), cap, _dev_ptr(status),
+                                                _stream_ptr(stream)), "pfsm_scan_union_async")
 
 
 def pfsm_set_batch_params(ctx: int, params: Optional[dict] = None) -> None:

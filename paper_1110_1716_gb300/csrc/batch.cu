@@ -5,12 +5,12 @@
 // The machines of a batch are grouped into classes, one specialised
 // persistent kernel each (batch_kernels.cu). Every class has a fixed launch
 // shape per context (threads, CTAs, shared-memory layout with a table arena
-// of fixed size), so the launch sequence of a batch depends only on which
-// classes it contains: counter and status resets, one branch per class
-// (the class kernels run side by side), then the DFA carry kernel. That
-// sequence is captured once per stream and class set as a CUDA graph and
-// replayed; the per-batch argument blocks, job table and machine table are
-// copied to a fixed device block before each replay.
+// of fixed size), so one launch sequence serves every batch: counter and
+// status resets, one branch per class (the class kernels run side by side;
+// a class with no work in the batch claims nothing and exits), then the DFA
+// carry kernel. That sequence is captured once per stream as a CUDA graph
+// and replayed; the per-batch argument blocks, job table and machine table
+// are copied to a fixed device block before each replay.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -28,6 +28,7 @@ constexpr uint32_t kBatchHalo = 2048;
 constexpr uint32_t kMinArena = 8192;     // smallest table arena worth a class shape
 constexpr int kUnitTilesMax = 8;        // tiles per work unit, at most
 constexpr int kCarryCtr = 15;           // counter word holding the carry count
+constexpr uint32_t kAllClasses = (1u << kBatchClasses) - 1;
 
 struct BatchGraph {
     cudaGraphExec_t exec = nullptr;
@@ -190,7 +191,7 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
 static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine &d) {
     d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = d.a_coop = kNotStaged;
     d.settle = m.params.settle > 0 ? m.params.settle : 0;
-    d.pad = 0;
+    d.lazy = m.params.partition == 1 ? 1 : 0;
     uint32_t used = 0;
     auto take = [&](uint32_t bytes) {
         const uint32_t at = (used + 15) & ~15u;
@@ -395,8 +396,9 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
     if (coop_need && ensure_words(&b->coop, &b->coop_words, coop_need)) return PFSM_E_NOMEM;
     BatchArgs args[kBatchClasses];
     memset(args, 0, sizeof(args));
+    // every class gets valid arguments: the graph launches all of them, and
+    // a class without units claims nothing and exits
     for (int c = 0; c < kBatchClasses; ++c) {
-        if (!(pl.mask & (1u << c))) continue;
         const BatchShape &sh = ctx->batch_shape[c];
         BatchArgs &A = args[c];
         A.sa = sh.layout;
@@ -429,7 +431,7 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
     cudaEventRecord(b->staged, s);
     b->staged_pending = true;
     cudaGraphExec_t exec = nullptr;
-    st = graph_for(ctx, b, pl.mask, &exec);
+    st = graph_for(ctx, b, kAllClasses, &exec);
     if (st) return st;
     int ev = -1;
     Slot *slot = ctx->timing ? get_slot(ctx, s) : nullptr;
@@ -503,4 +505,26 @@ extern "C" int pfsm_scan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k,
     if (counts)
         for (int32_t i = 0; i < k; ++i) counts[i] = b->host_status[2 + i];
     return finish_status(b->host_status, cap, total);
+}
+
+// A union machine (Sec. III.A): k automata over one text. The union through
+// an ancillary initial state with epsilon edges to every component's q0 has
+// exactly the union of the components' match sets, so it runs as a batch of
+// k jobs on the same text; a match's text field is its component's index.
+extern "C" int pfsm_scan_union_async(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k,
+                                     const uint8_t *text_dev, uint64_t n, pfsm_bmatch *out_dev,
+                                     uint64_t cap, uint64_t *status_dev, void *stream) {
+    if (!ctx || k < 0 || (k > 0 && !auts) || (n > 0 && !text_dev)) return PFSM_E_INVAL;
+    std::vector<pfsm_job> jobs(static_cast<size_t>(k));
+    for (int32_t i = 0; i < k; ++i) jobs[i] = pfsm_job{auts[i], 0u, text_dev, n};
+    return pfsm_scan_batch_async(ctx, jobs.data(), k, out_dev, cap, status_dev, stream);
+}
+
+extern "C" int pfsm_scan_union(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k,
+                               const uint8_t *text_dev, uint64_t n, pfsm_bmatch *out_dev,
+                               uint64_t cap, uint64_t *counts, uint64_t *total, void *stream) {
+    if (!ctx || k < 0 || (k > 0 && !auts) || (n > 0 && !text_dev)) return PFSM_E_INVAL;
+    std::vector<pfsm_job> jobs(static_cast<size_t>(k));
+    for (int32_t i = 0; i < k; ++i) jobs[i] = pfsm_job{auts[i], 0u, text_dev, n};
+    return pfsm_scan_batch(ctx, jobs.data(), k, out_dev, cap, counts, total, stream);
 }

@@ -167,15 +167,17 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
         if (misc->abort) break;
         const MView mv = mview_of(M);
         const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
+        OView ovm = ov;
+        if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
-        process_tile<KIND, SB, TAB, 4>(ov, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
+        process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
                                        static_cast<uint32_t>(M.settle));
         // the next tile continues this text: queued instances and staged
         // matches stay; otherwise drain and flush them now (per-text counts
         // need every staged match of a flush to belong to one text)
         const bool same_text = desc[buf ^ 1].valid && desc[buf ^ 1].job == d.job;
         if (!same_text) {
-            drain<KIND, TAB, 4>(ov, mv, tv, smi, wq_n, sn, lane, pol_keep);
+            drain<KIND, TAB, 4>(ovm, mv, tv, smi, wq_n, sn, lane, pol_keep);
             stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
         }
         // the staged buffer is refilled two tiles on: every warp must be done

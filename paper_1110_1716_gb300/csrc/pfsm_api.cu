@@ -320,7 +320,44 @@ static void release_async(pfsm_ctx *ctx, Machine &m, cudaStream_t s) {
     m.dev_bytes = 0;
 }
 
+static bool in_use(Machine &m) {
+    bool busy = false;
+    for (auto &u : m.uses)
+        if (cudaEventQuery(u.second) != cudaSuccess) busy = true;
+    if (m.ready && cudaEventQuery(m.ready) != cudaSuccess) busy = true;
+    cudaGetLastError();   // a pending event is not an error
+    return busy;
+}
+
+static void forget(pfsm_ctx *ctx, Machine &m) {
+    release(ctx, m);
+    drop_host_image(m);
+    if (m.ready) cudaEventDestroy(m.ready);
+    m.ready = nullptr;
+}
+
+// Frees the retired machines that nothing reads any more.
+void sweep_retired(pfsm_ctx *ctx) {
+    for (size_t i = 0; i < ctx->retired.size();) {
+        if (in_use(ctx->retired[i])) {
+            ++i;
+            continue;
+        }
+        forget(ctx, ctx->retired[i]);
+        ctx->retired.erase(ctx->retired.begin() + i);
+    }
+}
+
 int evict_lru(pfsm_ctx *ctx, uint64_t need, int keep_id, cudaStream_t s) {
+    sweep_retired(ctx);
+    // retired machines go first, freed in the order of stream `s`
+    while (ctx->resident_bytes + need > ctx->budget && !ctx->retired.empty()) {
+        Machine &r = ctx->retired.back();
+        release_async(ctx, r, s);
+        drop_host_image(r);
+        if (r.ready) cudaEventDestroy(r.ready);
+        ctx->retired.pop_back();
+    }
     while (ctx->resident_bytes + need > ctx->budget) {
         Machine *victim = nullptr;
         for (auto &kv : ctx->machines) {
@@ -522,6 +559,7 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
     if (p.spt == 0) p.spt = 8;
     if (p.table_smem == 0) p.table_smem = -1;
     if (p.settle == 0) p.settle = 16;
+    if (p.partition == 0) p.partition = m.kind == 0 ? 2 : 1;
 }
 
 int validate_params(const Machine &m, const pfsm_params &p) {
@@ -535,6 +573,8 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
     if (p.settle < -1 || p.settle > 63) return PFSM_E_INVAL;
+    if (p.partition < 0 || p.partition > 2 || (m.kind == 1 && p.partition == 2))
+        return PFSM_E_INVAL;
     return PFSM_OK;
 }
 
@@ -705,7 +745,8 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     pl.a.status = status;
     pl.a.carry = slot->carry;
     pl.a.carry_n = slot->carry_n;
-    pl.a.carry_cap = kCarryCap;
+    // lazy partitioning: no carry queue, instances continue in place
+    pl.a.carry_cap = m.params.partition == 1 ? 0u : kCarryCap;
     if (m.kind == 1 && !pl.a.coop_smem) {
         const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * m.dm.Wq;
         if (ensure_words(&slot->coop, &slot->coop_words, need)) return PFSM_E_NOMEM;
@@ -726,7 +767,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
         slot->ev_pending++;
     }
     if (e != cudaSuccess) return PFSM_E_CUDA;
-    if (m.kind == 0) {
+    if (m.kind == 0 && pl.a.carry_cap > 0) {
         e = launch_carry(pl.a, 2 * ctx->nsm, s);
         if (e != cudaSuccess) return PFSM_E_CUDA;
     }
@@ -794,11 +835,9 @@ int pfsm_ctx_destroy(pfsm_ctx *ctx) {
     if (!ctx) return PFSM_OK;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    for (auto &kv : ctx->machines) {
-        release(ctx, kv.second);
-        drop_host_image(kv.second);
-        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
-    }
+    for (auto &kv : ctx->machines) forget(ctx, kv.second);
+    for (auto &m : ctx->retired) forget(ctx, m);
+    ctx->retired.clear();
     for (auto &kv : ctx->use_rings)
         for (int i = 0; i < kUseRing; ++i)
             if (kv.second.ev[i]) cudaEventDestroy(kv.second.ev[i]);
@@ -960,10 +999,12 @@ int pfsm_unload(pfsm_ctx *ctx, pfsm_aut aut) {
     auto it = ctx->machines.find(aut);
     if (it == ctx->machines.end()) return PFSM_E_NOENT;
     DeviceGuard g(ctx->device);
-    release(ctx, it->second);
-    drop_host_image(it->second);
-    if (it->second.ready) cudaEventDestroy(it->second.ready);
+    Machine m = std::move(it->second);
     ctx->machines.erase(it);
+    // scans in flight may still read the image: retire it instead of waiting
+    if (m.dev && in_use(m)) ctx->retired.push_back(std::move(m));
+    else forget(ctx, m);
+    sweep_retired(ctx);
     return PFSM_OK;
 }
 
@@ -1025,6 +1066,10 @@ int pfsm_scan(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
 
 int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out) {
     if (!ctx || !out) return PFSM_E_INVAL;
+    {
+        DeviceGuard g(ctx->device);
+        sweep_retired(ctx);   // unloaded images whose scans have completed
+    }
     out->resident_bytes = ctx->resident_bytes;
     out->budget_bytes = ctx->budget;
     out->loads = ctx->n_loads;

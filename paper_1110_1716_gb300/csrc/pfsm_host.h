@@ -110,6 +110,9 @@ struct pfsm_ctx {
     int next_id = 1;
     std::map<cudaStream_t, pfsm::Slot> slots;
     cudaMemPool_t pool = nullptr;     // stream-ordered pool of machine images
+    // unloaded machines whose images scans in flight still read: freed when
+    // their last uses complete (or evicted in stream order when room is needed)
+    std::vector<pfsm::Machine> retired;
     std::map<cudaStream_t, pfsm::UseRing> use_rings;
     std::mutex mu;
     bool timing = false;
@@ -134,6 +137,7 @@ void build_survival(Machine &m);
 size_t align256(size_t x);
 void release(pfsm_ctx *ctx, Machine &m);
 void drop_host_image(Machine &m);
+void sweep_retired(pfsm_ctx *ctx);
 int make_resident(pfsm_ctx *ctx, int id, Machine &m, cudaStream_t s);
 int mark_use(pfsm_ctx *ctx, cudaStream_t s, Machine *const *ms, size_t k);
 Slot *get_slot(pfsm_ctx *ctx, cudaStream_t s);

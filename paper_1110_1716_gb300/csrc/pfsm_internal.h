@@ -165,7 +165,7 @@ struct DevMachine {
     uint32_t a_memo, a_tab, a_band, a_pool, a_surv;
     uint32_t a_coop;  // batch: NFA warp-wide bitsets, 2 * Wq words per warp
     int32_t settle;   // batch: NFA settling step cap (0 = no settling)
-    int32_t pad;
+    int32_t lazy;     // batch: instances past their tile continue in place
 };
 static_assert(sizeof(DevMachine) % 8 == 0, "DevMachine layout");
 

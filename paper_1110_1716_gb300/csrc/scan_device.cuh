@@ -356,7 +356,9 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
             if (pos >= n) {
                 act = false;
             } else if (pos >= tile_end && !gmode) {
-                const uint32_t ci = atomicAdd(ov.carry_n, 1u);
+                // chained: hand the instance to the carry queue; lazy (no
+                // queue) or a full queue: continue on the global text
+                const uint32_t ci = ov.carry_cap ? atomicAdd(ov.carry_n, 1u) : 0u;
                 if (ci < ov.carry_cap) {
                     uint32_t *c = ov.carry + 4 * ci;
                     c[0] = tv.job;

@@ -168,3 +168,24 @@ def test_batch_under_small_budget_reloads(pf):
         assert st["evictions"] > 0 and st["reloads"] > 0
     finally:
         small.close()
+
+
+def test_batch_mixes_lazy_and_chained_machines(pf):
+    """Long-lived DFA instances in one batch: one machine continues them in
+    place (lazy), the other through the carry queue (chained)."""
+    ms = [W.dfa_random(20 + i, Q=6, S=4, dead=-1, finals=[1, 3], p_dead=0.0) for i in range(2)]
+    ids = [pf.load(m) for m in ms]
+    P.pfsm_set_params(pf.ctx, ids[0], {"partition": 1})
+    P.pfsm_set_params(pf.ctx, ids[1], {"partition": 2})
+    texts = [W.text_uniform(5000 + 700 * i, 4, 30 + i) for i in range(4)]
+    jobs = [(ids[i % 2], t) for i, t in enumerate(texts)]
+    want = [oracle.scan(ms[i % 2], t) for i, t in enumerate(texts)]
+    P.pfsm_set_batch_params(pf.ctx, {"tile": 4096})
+    try:
+        got, counts = pf.scan_batch(jobs)
+    finally:
+        P.pfsm_set_batch_params(pf.ctx, None)
+    per = split_by_text(got.cpu().numpy().view(np.uint32), len(jobs))
+    for j in range(len(jobs)):
+        assert int(counts[j]) == len(want[j]), j
+        assert np.array_equal(per[j], want[j]), j

@@ -304,6 +304,27 @@ def test_instances_outliving_tiles_use_the_carry_queue(pf):
     assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
 
 
+@pytest.mark.parametrize("partition", [1, 2])
+def test_lazy_and_chained_partitioning(pf, partition):
+    """Sec. III.D.2 both ways on instances that never die: lazy (continue on
+    the global text in place) and chained (carry queue, second kernel)."""
+    d = W.dfa_random(18, Q=6, S=4, dead=-1, finals=[1, 4], p_dead=0.0)
+    a = pf.load(d)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "prefix_k": 2, "partition": partition})
+    assert P.pfsm_get_params(pf.ctx, a)["partition"] == partition
+    t = W.text_uniform(9000, 4, 19)
+    want = oracle.scan(d, t)
+    assert len(want) > 1_000_000
+    assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
+
+
+def test_nfa_partition_is_lazy_only(pf):
+    a = pf.load(W.eps_free(W.fig1_union()))
+    assert P.pfsm_get_params(pf.ctx, a)["partition"] == 1
+    with pytest.raises(P.PfsmError):
+        P.pfsm_set_params(pf.ctx, a, {"partition": 2})
+
+
 def test_eviction_and_reload(pf):
     autos = [W.dfa_random(50 + i, Q=64, S=4) for i in range(3)]
     autos.append(W.workload_motif_nfa(3, n=10, n_motifs=40)[0])
