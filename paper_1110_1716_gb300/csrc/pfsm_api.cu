@@ -51,9 +51,13 @@ void build_memo_dfa(Machine &m) {
     const uint32_t nent = 1u << (k * m.sbits);
     const uint32_t smask = (1u << m.sbits) - 1;
     m.memo.assign(nent + (nent & 1), PT_SKIP);
+    m.pool.clear();
+    std::map<std::vector<uint32_t>, uint32_t> recs;
+    std::vector<uint32_t> matches, rec;
     for (uint32_t w = 0; w < nent; ++w) {
         int s = m.q0;
-        bool fin_seen = false, died = false, bad = false;
+        bool died = false, bad = false;
+        matches.clear();
         for (int j = 0; j < k; ++j) {
             const int a = (w >> (j * m.sbits)) & smask;
             if (a >= m.S) {
@@ -66,13 +70,33 @@ void build_memo_dfa(Machine &m) {
                 break;
             }
             s = e & 0x7FFF;
-            if (e & FINAL_BIT) fin_seen = true;
+            if (e & FINAL_BIT) matches.push_back((static_cast<uint32_t>(j) << 16) | static_cast<uint32_t>(s));
         }
         if (bad) continue;   // such k-grams raise E_INVAL anyway
-        if (fin_seen) m.memo[w] = PT_WALK;
-        else if (died) m.memo[w] = PT_SKIP;
-        else m.memo[w] = static_cast<uint16_t>(s);
+        if (matches.empty()) {
+            m.memo[w] = died ? PT_SKIP : static_cast<uint16_t>(s);
+            continue;
+        }
+        // matches within the k steps: a record of them and the survivor
+        rec.assign(1, static_cast<uint32_t>(matches.size()) | ((died ? 0u : 1u) << 16));
+        rec.insert(rec.end(), matches.begin(), matches.end());
+        if (!died) rec.push_back(static_cast<uint32_t>(s));
+        auto it = recs.find(rec);
+        uint32_t at;
+        if (it != recs.end()) {
+            at = it->second;
+        } else {
+            at = static_cast<uint32_t>(m.pool.size());
+            if (at + rec.size() > PT_REC_MAX) {
+                m.memo[w] = PT_WALK;   // the pool is full: step from q0 instead
+                continue;
+            }
+            recs.emplace(rec, at);
+            m.pool.insert(m.pool.end(), rec.begin(), rec.end());
+        }
+        m.memo[w] = static_cast<uint16_t>(PT_REC | at);
     }
+    if (m.pool.empty()) m.pool.push_back(0);
 }
 
 // NFA: entry for k-gram w = record of the matches met within the first k
@@ -276,7 +300,7 @@ size_t device_bytes(const Machine &m) {
     size_t b = align256(m.memo.size() * 2 + 4) + align256(m.surv.size() * 4 + 4) +
                align256(m.surv2.size() * 4 + 4) + align256(m.tail.size() * 2 + 4);
     if (m.kind == 0) {
-        b += align256(m.dtab.size() * 2 + 4);
+        b += align256(m.dtab.size() * 2 + 4) + align256(m.pool.size() * 4);
     } else {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
              align256(m.pool.size() * 4) + align256(m.band.size() * 4);
@@ -398,6 +422,7 @@ static int build_host_image(Machine &m) {
     m.o_surv2 = put(m.surv2.data(), m.surv2.size() * 4, 4);
     if (m.kind == 0) {
         m.o_tab = put(m.dtab.data(), m.dtab.size() * 2, 4);
+        m.o_pool = put(m.pool.data(), m.pool.size() * 4, 0);
     } else {
         m.o_off = put(m.off.data(), m.off.size() * 4, 0);
         m.o_tgt = put(m.tgt.data(), m.tgt.size() * 2, 4);
@@ -433,6 +458,8 @@ static DevMachine dev_view(const Machine &m, uint8_t *base) {
     dm.surv2_m = m.sm_m2;
     if (m.kind == 0) {
         dm.dtab = reinterpret_cast<const uint16_t *>(base + m.o_tab);
+        dm.pool = reinterpret_cast<const uint32_t *>(base + m.o_pool);
+        dm.pool_n = static_cast<uint32_t>(m.pool.size());
     } else {
         dm.off = reinterpret_cast<const uint32_t *>(base + m.o_off);
         dm.tgt = reinterpret_cast<const uint16_t *>(base + m.o_tgt);

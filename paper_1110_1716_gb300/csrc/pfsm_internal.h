@@ -29,6 +29,12 @@ constexpr uint16_t FINAL_BIT = 0x8000;
 //              pool[o+1+n_match .. +n_surv] = surviving states after k steps
 constexpr uint16_t PT_SKIP = 0xFFFF;
 constexpr uint16_t PT_WALK = 0xFFFE;
+// DFA: an entry with bit 15 set (below PT_WALK) is PT_REC | o, the word
+// offset o of a record in `pool` in the NFA record format (the matches met
+// within the k steps, then the surviving state if there is one: n_surv is 0
+// or 1); a k-gram whose record does not fit stays PT_WALK.
+constexpr uint16_t PT_REC = 0x8000;
+constexpr uint32_t PT_REC_MAX = 0x7FFD;   // largest record offset
 
 // NFA short-gram table: a start with only j < k symbols left before the end
 // of its text has its whole future fixed by those j symbols: the matches it

@@ -326,6 +326,7 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
     bool act = false;
     bool gmode = false;   // past the staged text and the carry queue is full
     uint32_t start = 0, pos = 0, s = 0;
+    uint32_t pm_left = 0, pm_ptr = 0;   // matches of a prefix record still to report
     while (true) {
         const bool need = !act;
         const uint32_t m = __ballot_sync(FULLMASK, need);
@@ -337,19 +338,46 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
                 if (qi < qn) {
                     start = sm.wq_start[qi];
                     const uint32_t info = sm.wq_info[qi];
+                    act = true;
+                    gmode = false;
                     if (info == PT_WALK) {
                         s = mv.q0;
                         pos = start;
+                    } else if (info & PT_REC) {
+                        // the matches of the first k steps, then the survivor
+                        const uint32_t ro = info & 0x7FFFu;
+                        const uint32_t w0 = sm.pool[ro];
+                        pm_left = w0 & 0xFFFFu;
+                        pm_ptr = ro + 1;
+                        if (w0 >> 16) {
+                            s = sm.pool[ro + 1 + pm_left];
+                            pos = start + mv.k;
+                        } else {
+                            act = false;
+                        }
                     } else {
                         s = info;
                         pos = start + mv.k;
                     }
-                    act = true;
-                    gmode = false;
                 }
             }
         }
-        if (!__any_sync(FULLMASK, act)) break;
+        while (__any_sync(FULLMASK, pm_left > 0)) {
+            const bool has = pm_left > 0;
+            uint32_t o = 0, f = 0;
+            if (has) {
+                const uint32_t w = sm.pool[pm_ptr];
+                o = w >> 16;
+                f = w & 0xFFFFu;
+                ++pm_ptr;
+                --pm_left;
+            }
+            warp_emit<OUTW>(has, start, start + o, f, sm.stage, sn, ov, tv, lane);
+        }
+        if (!__any_sync(FULLMASK, act)) {
+            if (head >= qn) break;
+            continue;   // every refilled entry was a finished record
+        }
         bool hit = false;
         uint32_t hend = 0;
         if (act) {
