@@ -143,6 +143,22 @@ int pfsm_load_dfa(pfsm_ctx *ctx, const int16_t *delta, int32_t Q, int32_t S, int
 int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t S, int32_t q0,
                   const uint8_t *is_final, pfsm_aut *out_id);
 
+/* Load an NFA that keeps its epsilon edges for the scan to follow at run
+ * time (step 2 of Sec. III.B): after every symbol, and for the instance
+ * started at q0, the state set is closed under epsilon edges; a final state
+ * reached through them reports at the position of the symbol just consumed,
+ * and no empty match is reported. The union machine of Sec. III.A (an
+ * ancillary initial state with epsilon edges to each component) loads as it
+ * is. delta_bits as for pfsm_load_nfa; eps_bits host [Q][ceil(Q/32)], bit t
+ * of row q set iff q -epsilon-> t. delta itself is kept as given; the loader
+ * lists, for every state, the states its epsilon edges reach (the closure
+ * the scan applies). The prefix depth stays >= 1 for such a machine
+ * (prefix_k = -1 is E_INVAL). Result: the same match set as
+ * pfsm_load_nfa on the epsilon-free machine. Errors: E_INVAL, E_NOMEM. */
+int pfsm_load_nfa_eps(pfsm_ctx *ctx, const uint32_t *delta_bits, const uint32_t *eps_bits,
+                      int32_t Q, int32_t S, int32_t q0, const uint8_t *is_final,
+                      pfsm_aut *out_id);
+
 /* Drop the device copy of an automaton (its host copy stays); the next scan
  * that names it reloads it. Errors: E_NOENT. */
 int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut);

@@ -33,7 +33,7 @@ EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nf
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
            "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes",
-           "pfsm_scan_union", "pfsm_scan_union_async")
+           "pfsm_scan_union", "pfsm_scan_union_async", "pfsm_load_nfa_eps")
 
 
 class pfsm_params(ctypes.Structure):
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_ctx_destroy": [P],
         "pfsm_load_dfa": [P, P, I32, I32, I32, I32, P, ctypes.POINTER(I32)],
         "pfsm_load_nfa": [P, P, I32, I32, I32, P, ctypes.POINTER(I32)],
+        "pfsm_load_nfa_eps": [P, P, P, I32, I32, I32, P, ctypes.POINTER(I32)],
         "pfsm_evict": [P, I32],
         "pfsm_unload": [P, I32],
         "pfsm_set_params": [P, I32, ctypes.POINTER(pfsm_params)],
@@ -167,6 +168,22 @@ def pfsm_load_nfa(ctx: int, delta_bits: np.ndarray, q0: int, is_final: np.ndarra
     out = ctypes.c_int32()
     _check(load_library().pfsm_load_nfa(ctx, bits.ctypes.data, Q, S, q0, fin.ctypes.data,
                                         ctypes.byref(out)), "pfsm_load_nfa")
+    return out.value
+
+
+def pfsm_load_nfa_eps(ctx: int, delta_bits: np.ndarray, eps_bits: np.ndarray, q0: int,
+                      is_final: np.ndarray) -> int:
+    """An NFA whose epsilon edges (eps_bits [Q][ceil(Q/32)]) are followed at
+    scan time."""
+    bits = np.ascontiguousarray(delta_bits, dtype=np.uint32)
+    eps = np.ascontiguousarray(eps_bits, dtype=np.uint32)
+    fin = np.ascontiguousarray(is_final, dtype=np.uint8)
+    Q, S, W = bits.shape
+    if W != (Q + 31) // 32 or fin.shape != (Q,) or eps.shape != (Q, W):
+        raise ValueError("delta_bits [Q][S][W], eps_bits [Q][W] and is_final [Q] expected")
+    out = ctypes.c_int32()
+    _check(load_library().pfsm_load_nfa_eps(ctx, bits.ctypes.data, eps.ctypes.data, Q, S, q0,
+                                            fin.ctypes.data, ctypes.byref(out)), "pfsm_load_nfa_eps")
     return out.value
 
 
@@ -395,10 +412,12 @@ class Pfsm:
             pass
 
     def load(self, aut) -> int:
-        if getattr(aut, "eps", None) is not None:
-            raise ValueError("remove epsilon edges before loading")
+        """Load a workloads.Dfa or Nfa; an Nfa with epsilon edges keeps them
+        for the scan to follow (pfsm_load_nfa_eps)."""
         if hasattr(aut, "delta"):
             return pfsm_load_dfa(self.ctx, aut.delta, aut.q0, aut.dead, aut.final)
+        if getattr(aut, "eps", None) is not None:
+            return pfsm_load_nfa_eps(self.ctx, aut.bits, aut.eps, aut.q0, aut.final)
         return pfsm_load_nfa(self.ctx, aut.bits, aut.q0, aut.final)
 
     def to_device(self, text: np.ndarray):

@@ -101,6 +101,34 @@ void build_memo_dfa(Machine &m) {
 
 // NFA: entry for k-gram w = record of the matches met within the first k
 // steps from {q0} and the state set after them; equal records are shared.
+// delta(q, a) of an NFA as uint16 entries (state | FINAL_BIT), each target
+// followed by the states it reaches through epsilon edges when the machine
+// keeps them (step 2 of Sec. III.B applied after every symbol).
+template <class F>
+static void nfa_step(const Machine &m, uint32_t q, int a, F &&f) {
+    const uint32_t lo = m.off[(size_t)q * m.S + a], hi = m.off[(size_t)q * m.S + a + 1];
+    for (uint32_t e = lo; e < hi; ++e) {
+        const uint16_t t = m.tgt[e];
+        f(t);
+        if (!m.ecl_off.empty()) {
+            const uint32_t ts = t & 0x7FFF;
+            for (uint32_t x = m.ecl_off[ts]; x < m.ecl_off[ts + 1]; ++x) f(m.ecl_tgt[x]);
+        }
+    }
+}
+
+// The state set an instance starts with: q0 and what it reaches through
+// epsilon edges (a final state among them reports nothing: no empty matches).
+static std::vector<uint16_t> nfa_initial(const Machine &m) {
+    std::vector<uint16_t> s{static_cast<uint16_t>(m.q0)};
+    if (!m.ecl_off.empty())
+        for (uint32_t x = m.ecl_off[m.q0]; x < m.ecl_off[m.q0 + 1]; ++x)
+            s.push_back(static_cast<uint16_t>(m.ecl_tgt[x] & 0x7FFF));
+    std::sort(s.begin(), s.end());
+    s.erase(std::unique(s.begin(), s.end()), s.end());
+    return s;
+}
+
 struct NfaMemoBuilder {
     Machine &m;
     std::map<std::vector<uint32_t>, uint32_t> recs;
@@ -159,15 +187,13 @@ struct NfaMemoBuilder {
             std::vector<uint32_t> nm = matches;
             ++stamp;
             for (uint16_t q : set) {
-                const uint32_t lo = m.off[(size_t)q * m.S + a], hi = m.off[(size_t)q * m.S + a + 1];
-                for (uint32_t e = lo; e < hi; ++e) {
-                    const uint16_t t = m.tgt[e];
+                nfa_step(m, q, a, [&](uint16_t t) {
                     const uint16_t ts = t & 0x7FFF;
-                    if (mark[ts] == stamp) continue;
+                    if (mark[ts] == stamp) return;
                     mark[ts] = stamp;
                     next.push_back(ts);
                     if (t & FINAL_BIT) nm.push_back((static_cast<uint32_t>(depth) << 16) | ts);
-                }
+                });
             }
             std::sort(next.begin(), next.end());
             dfs(depth + 1, prefix | (static_cast<uint32_t>(a) << (depth * sb)), next, nm);
@@ -187,7 +213,7 @@ bool build_memo_nfa(Machine &m) {
     const uint32_t ntail = tail_base(m.k, m.sbits);
     m.tail.assign(ntail + (ntail & 1), PT_SKIP);
     NfaMemoBuilder b(m);
-    b.dfs(0, 0, {static_cast<uint16_t>(m.q0)}, {});
+    b.dfs(0, 0, nfa_initial(m), {});
     if (!b.ok) return false;
     if (m.pool.empty()) m.pool.push_back(0);
     return true;
@@ -254,22 +280,20 @@ static bool survival_bits(const Machine &m, int mm, std::vector<uint32_t> &bits)
                 bool hit = false;
                 ++stamp;
                 for (uint16_t q : S) {
-                    const uint32_t lo = m.off[(size_t)q * m.S + a], hi = m.off[(size_t)q * m.S + a + 1];
-                    for (uint32_t e = lo; e < hi; ++e) {
-                        const uint16_t t = m.tgt[e];
+                    nfa_step(m, q, a, [&](uint16_t t) {
                         const uint16_t ts = t & 0x7FFF;
                         if (t & FINAL_BIT) hit = true;
-                        if (mark[ts] == stamp) continue;
+                        if (mark[ts] == stamp) return;
                         mark[ts] = stamp;
                         N.push_back(ts);
-                    }
+                    });
                 }
                 const uint32_t p = prefix | (static_cast<uint32_t>(a) << (depth * m.sbits));
                 if (hit) set_range(p, depth + 1);
                 else if (!N.empty()) dfs(depth + 1, p);
             }
         };
-        lv[0] = {static_cast<uint16_t>(m.q0)};
+        lv[0] = nfa_initial(m);
         dfs(0, 0);
     }
     if (ones * 2 > nbits) {
@@ -303,7 +327,8 @@ size_t device_bytes(const Machine &m) {
         b += align256(m.dtab.size() * 2 + 4) + align256(m.pool.size() * 4);
     } else {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
-             align256(m.pool.size() * 4) + align256(m.band.size() * 4);
+             align256(m.pool.size() * 4) + align256(m.band.size() * 4) +
+             align256(m.ecl_off.size() * 4) + align256(m.ecl_tgt.size() * 2 + 4);
     }
     return b;
 }
@@ -428,6 +453,8 @@ static int build_host_image(Machine &m) {
         m.o_tgt = put(m.tgt.data(), m.tgt.size() * 2, 4);
         m.o_pool = put(m.pool.data(), m.pool.size() * 4, 0);
         m.o_band = put(m.band.data(), m.band.size() * 4, 0);
+        m.o_eoff = put(m.ecl_off.data(), m.ecl_off.size() * 4, 0);
+        m.o_etgt = put(m.ecl_tgt.data(), m.ecl_tgt.size() * 2, 4);
     }
     if (o > bytes) {   // layout and size disagree: a bug, fail loudly
         cudaFreeHost(h);
@@ -466,6 +493,8 @@ static DevMachine dev_view(const Machine &m, uint8_t *base) {
         dm.pool = reinterpret_cast<const uint32_t *>(base + m.o_pool);
         dm.pool_n = static_cast<uint32_t>(m.pool.size());
         dm.band = m.band.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_band);
+        dm.ecl_off = m.ecl_off.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_eoff);
+        dm.ecl_tgt = m.ecl_off.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_etgt);
     }
     return dm;
 }
@@ -602,6 +631,7 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.settle < -1 || p.settle > 63) return PFSM_E_INVAL;
     if (p.partition < 0 || p.partition > 2 || (m.kind == 1 && p.partition == 2))
         return PFSM_E_INVAL;
+    if (!m.ecl_off.empty() && p.prefix_k == -1) return PFSM_E_INVAL;   // see finish_load
     return PFSM_OK;
 }
 
@@ -613,21 +643,19 @@ int apply_k(pfsm_ctx *ctx, Machine &m, bool may_lower) {
     const int k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
     if (k == m.k && (k == 0 || !m.memo.empty())) return PFSM_OK;
     const int old_k = m.k;
+    // a machine with epsilon edges keeps k >= 1: no start steps from a bare q0
+    const int floor_k = m.ecl_off.empty() ? 0 : 1;
     release(ctx, m);
     drop_host_image(m);   // the prefix tables change: rebuild the image
-    m.k = k;
+    m.k = std::max(k, floor_k);
     while (!build_memo(m)) {
-        if (!may_lower) {
+        if (!may_lower || m.k - 1 < floor_k) {
             m.k = old_k;
             build_memo(m);
             m.params.prefix_k = old_k > 0 ? old_k : -1;
             return PFSM_E_INVAL;
         }
-        if (--m.k <= 0) {
-            m.k = 0;
-            build_memo(m);
-            break;
-        }
+        --m.k;   // k = 0 always builds (no table)
     }
     m.params.prefix_k = m.k > 0 ? m.k : -1;
     return PFSM_OK;
@@ -675,6 +703,8 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.memo_n = m.dm.memo_n;
     a.memo = m.dm.memo;
     a.tail = m.dm.tail;
+    a.ecl_off = m.dm.ecl_off;
+    a.ecl_tgt = m.dm.ecl_tgt;
     a.dtab = m.dm.dtab;
     a.off = m.dm.off;
     a.tgt = m.dm.tgt;
@@ -886,8 +916,10 @@ static int finish_load(pfsm_ctx *ctx, Machine &&m, pfsm_aut *out_id) {
     fill_defaults(m, m.params);
     m.k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
     if (m.k * m.sbits > 16) m.k = 16 / m.sbits;
+    if (!m.ecl_off.empty() && m.k < 1) m.k = 1;   // epsilon edges: no start steps from a bare q0
     while (!build_memo(m)) {
         if (--m.k <= 0) {
+            if (!m.ecl_off.empty()) return PFSM_E_INVAL;
             m.k = 0;
             build_memo(m);
             break;
@@ -941,8 +973,8 @@ int pfsm_load_dfa(pfsm_ctx *ctx, const int16_t *delta, int32_t Q, int32_t S, int
     return finish_load(ctx, std::move(m), out_id);
 }
 
-int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t S, int32_t q0,
-                  const uint8_t *is_final, pfsm_aut *out_id) {
+static int load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, const uint32_t *eps_bits,
+                    int32_t Q, int32_t S, int32_t q0, const uint8_t *is_final, pfsm_aut *out_id) {
     if (!ctx || !delta_bits || !is_final || !out_id) return PFSM_E_INVAL;
     if (Q < 1 || Q > 32767 || S < 1 || S > 256) return PFSM_E_INVAL;
     if (q0 < 0 || q0 >= Q) return PFSM_E_INVAL;
@@ -973,9 +1005,47 @@ int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t 
         if (e > 0xFFFFFFFFull) return PFSM_E_INVAL;
     }
     m.off[(size_t)Q * S] = static_cast<uint32_t>(e);
+    // epsilon edges kept for run time: the states each state reaches through
+    // them (breadth first; the state itself excluded)
+    bool has_eps = false;
+    if (eps_bits) {
+        for (size_t x = 0; x < (size_t)Q * W; ++x) has_eps |= eps_bits[x] != 0;
+        if (eps_bits[(size_t)(Q - 1) * W + W - 1] & ~lastmask) return PFSM_E_INVAL;
+        for (int q = 0; q < Q && has_eps; ++q)
+            if (eps_bits[(size_t)q * W + W - 1] & ~lastmask) return PFSM_E_INVAL;
+    }
+    if (has_eps) {
+        m.ecl_off.assign(static_cast<size_t>(Q) + 1, 0);
+        std::vector<int> seen(Q, -1), queue;
+        for (int q = 0; q < Q; ++q) {
+            m.ecl_off[q] = static_cast<uint32_t>(m.ecl_tgt.size());
+            queue.assign(1, q);
+            seen[q] = q;
+            std::vector<uint16_t> reach;
+            for (size_t h = 0; h < queue.size(); ++h) {
+                const uint32_t *row = eps_bits + (size_t)queue[h] * W;
+                for (int w = 0; w < W; ++w) {
+                    uint32_t x = row[w];
+                    while (x) {
+                        const int t = w * 32 + __builtin_ctz(x);
+                        x &= x - 1;
+                        if (seen[t] == q) continue;
+                        seen[t] = q;
+                        queue.push_back(t);
+                        reach.push_back(static_cast<uint16_t>(t | (is_final[t] ? FINAL_BIT : 0)));
+                    }
+                }
+            }
+            std::sort(reach.begin(), reach.end());
+            m.ecl_tgt.insert(m.ecl_tgt.end(), reach.begin(), reach.end());
+        }
+        m.ecl_off[Q] = static_cast<uint32_t>(m.ecl_tgt.size());
+        if (m.ecl_tgt.empty()) m.ecl_tgt.push_back(0);
+    }
     // band rows: delta(q, a) inside q+1..q+8 for every symbol (alphabets of
-    // at most 4 symbols), with the finality of each target beside it
-    if (S <= 4) {
+    // at most 4 symbols), with the finality of each target beside it; a
+    // machine with epsilon edges reads the CSR rows and their closures
+    if (S <= 4 && !has_eps) {
         m.band.assign(static_cast<size_t>(Q) + W, 0u);
         for (int q = 0; q < Q; ++q) {
             uint32_t row = 0;
@@ -998,6 +1068,18 @@ int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t 
     }
     if (m.tgt.empty()) m.tgt.push_back(0);
     return finish_load(ctx, std::move(m), out_id);
+}
+
+int pfsm_load_nfa(pfsm_ctx *ctx, const uint32_t *delta_bits, int32_t Q, int32_t S, int32_t q0,
+                  const uint8_t *is_final, pfsm_aut *out_id) {
+    return load_nfa(ctx, delta_bits, nullptr, Q, S, q0, is_final, out_id);
+}
+
+int pfsm_load_nfa_eps(pfsm_ctx *ctx, const uint32_t *delta_bits, const uint32_t *eps_bits,
+                      int32_t Q, int32_t S, int32_t q0, const uint8_t *is_final,
+                      pfsm_aut *out_id) {
+    if (!eps_bits) return PFSM_E_INVAL;
+    return load_nfa(ctx, delta_bits, eps_bits, Q, S, q0, is_final, out_id);
 }
 
 int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut) {

@@ -25,6 +25,11 @@ struct Machine {
     std::vector<uint16_t> dtab;       // DFA [Q][S]
     std::vector<uint32_t> off;        // NFA CSR [Q*S+1]
     std::vector<uint16_t> tgt;        // NFA targets
+    // NFA with epsilon edges kept (step 2 of Sec. III.B at run time): the
+    // states each state reaches through epsilon edges (itself excluded),
+    // CSR by state, final bit as in tgt; empty without epsilon edges
+    std::vector<uint32_t> ecl_off;
+    std::vector<uint16_t> ecl_tgt;
     // start-prefix table
     int k = 0, sbits = 1;
     std::vector<uint16_t> memo;
@@ -42,7 +47,7 @@ struct Machine {
     uint8_t *host_img = nullptr;      // pinned copy of the device image
     size_t img_bytes = 0;
     size_t o_memo = 0, o_tail = 0, o_surv = 0, o_surv2 = 0, o_tab = 0, o_off = 0,
-           o_tgt = 0, o_pool = 0, o_band = 0;   // section offsets in the image
+           o_tgt = 0, o_pool = 0, o_band = 0, o_eoff = 0, o_etgt = 0;   // section offsets
     cudaEvent_t ready = nullptr;      // recorded after the last upload
     // last use per stream (an event recorded after a launch that read the
     // image); an eviction orders its free after every one of them

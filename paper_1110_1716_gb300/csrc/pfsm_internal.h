@@ -92,6 +92,8 @@ struct ScanArgs {
     uint32_t memo_n;        // entries of the prefix table (0 when k == 0)
     const uint16_t *memo;   // prefix table (global copy, staged to smem)
     const uint16_t *tail;   // NFA: short-gram table for starts within k of the end, or null
+    const uint32_t *ecl_off;// NFA with epsilon edges: closure lists (CSR by state), or null
+    const uint16_t *ecl_tgt;
     const uint16_t *dtab;   // DFA: [Q][S]
     const uint32_t *off;    // NFA: [Q*S + 1] CSR offsets
     const uint16_t *tgt;    // NFA: targets
@@ -154,6 +156,8 @@ struct DevMachine {
     int32_t Wq;
     const uint16_t *memo;
     const uint16_t *tail;   // NFA: short-gram table (see tail_base), or null
+    const uint32_t *ecl_off;// NFA with epsilon edges: closure lists, or null
+    const uint16_t *ecl_tgt;
     const uint16_t *dtab;
     const uint32_t *off;
     const uint16_t *tgt;

@@ -211,6 +211,8 @@ struct MView {
     const uint32_t *off;
     const uint16_t *tgt;
     const uint16_t *tail;   // NFA short-gram table, or null
+    const uint32_t *ecl_off;// NFA with epsilon edges: epsilon closure lists, or null
+    const uint16_t *ecl_tgt;
 };
 
 // Where matches and carried instances go.
@@ -440,7 +442,17 @@ __device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *ban
     }
     const uint32_t lo = ldg_u32_keep(mv.off + q * mv.S + c, pol_keep);
     const uint32_t hi = ldg_u32_keep(mv.off + q * mv.S + c + 1, pol_keep);
-    for (uint32_t e = lo; e < hi; ++e) f(static_cast<uint32_t>(ldg_u16_keep(mv.tgt + e, pol_keep)));
+    for (uint32_t e = lo; e < hi; ++e) {
+        const uint32_t t = ldg_u16_keep(mv.tgt + e, pol_keep);
+        f(t);
+        if (mv.ecl_off) {
+            // step 2 of Sec. III.B: the states t reaches through epsilon edges
+            const uint32_t ts = t & 0x7FFFu;
+            const uint32_t a = ldg_u32_keep(mv.ecl_off + ts, pol_keep);
+            const uint32_t z = ldg_u32_keep(mv.ecl_off + ts + 1, pol_keep);
+            for (uint32_t x = a; x < z; ++x) f(static_cast<uint32_t>(ldg_u16_keep(mv.ecl_tgt + x, pol_keep)));
+        }
+    }
 }
 
 // Settling of surviving NFA starts, one warp at a time. The instances of a
