@@ -184,10 +184,10 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
 
 // Chooses which of a machine's tables go to the table arena (in order of
 // use per start: survival bitmap, prefix table, DFA table, NFA band rows,
-// the warp-wide NFA bitsets of `warps` warps, NFA prefix records) and
+// NFA prefix records, the warp-wide NFA bitsets of `warps` warps) and
 // returns the machine's class. With a deep bitmap in global memory few
-// starts reach the prefix table, so the prefix table and records stay in
-// global memory and leave the arena to the rest.
+// starts reach the prefix table, so it stays in global memory and leaves
+// the arena to the rest.
 static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine &d) {
     d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = d.a_coop = kNotStaged;
     d.settle = m.params.settle > 0 ? m.params.settle : 0;
@@ -206,8 +206,8 @@ static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine 
         d.a_tab = take(((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4);
     } else {
         if (!m.band.empty()) d.a_band = take(static_cast<uint32_t>(m.band.size() * 4));
+        if (!m.pool.empty()) d.a_pool = take(static_cast<uint32_t>(m.pool.size() * 4));
         d.a_coop = take(static_cast<uint32_t>(warps * 2 * d.Wq * 4));
-        if (!deep && !m.pool.empty()) d.a_pool = take(static_cast<uint32_t>(m.pool.size() * 4));
     }
     return batch_class(m.kind, m.sbits, m.k, m.kind == 0 && d.a_tab != kNotStaged);
 }

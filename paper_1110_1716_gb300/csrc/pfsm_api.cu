@@ -728,14 +728,16 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     const int kmask = m.kind == 0 ? 1 : 2;
     a.stage_n = m.kind == 0 ? STAGE : 32;
     SmemNeed need{};
-    // with a deep filter few starts reach the prefix table: leave it (and the
-    // NFA records) in global memory and keep shared memory for occupancy
+    // with a deep filter few starts reach the prefix table: leave it in
+    // global memory and keep shared memory for occupancy
     const bool deep = !m.surv2.empty();
     need.memo_bytes = deep ? 0u : static_cast<uint32_t>(((m.memo.size() + 1) / 2) * 4 + 4);
     if (m.memo.empty()) need.memo_bytes = 0;
     need.tab_bytes = a.tab_smem ? tab_bytes : 0;
     need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 4) : 0;
-    need.pool_bytes = (m.kind == 1 && !deep && m.pool.size() * 4 <= 64 * 1024)
+    // the NFA records are read by every start that reaches settling: shared
+    // memory when they fit
+    need.pool_bytes = (m.kind == 1 && m.pool.size() * 4 <= 64 * 1024)
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
     a.settle_steps = m.params.settle > 0 ? m.params.settle : 0;
     need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
@@ -751,9 +753,9 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         // shrink, cheapest loss first: match staging, then table copies
         // (largest first)
         if (a.stage_n > 32) a.stage_n = 32;
+        else if (need.coop_bytes) need.coop_bytes = 0;   // rare: sets of more than 8 states
         else if (need.pool_bytes) need.pool_bytes = 0;
         else if (need.memo_bytes) need.memo_bytes = 0;
-        else if (need.coop_bytes) need.coop_bytes = 0;
         else if (need.band_bytes) need.band_bytes = 0;
         else if (need.tab_bytes && p.table_smem == -1) { need.tab_bytes = 0; a.tab_smem = 0; }
         else break;
