@@ -165,6 +165,11 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
         if (d.sh) realign_tile(tsm, d.sh, d.len, tid, NT);   // ends with a barrier
         else __syncthreads();
         if (misc->abort) break;
+        if (SB == 2) {   // 2-bit symbols: pack the tile once for every gram read
+            pack_tile(tsm, sm.pk, d.len, min(d.b + A.sa.tile, d.n) - d.b,
+                      static_cast<uint32_t>(M.S), bad_symbol, tid, NT);
+            __syncthreads();
+        }
         const MView mv = mview_of(M);
         const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
         OView ovm = ov;

@@ -121,6 +121,7 @@ struct ScanArgs {
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
     int32_t coop_smem;      // NFA: warp-wide bitsets at sm_coop (else in coop_g)
+    uint32_t sm_pack;       // the staged tile as 2-bit symbols (alphabets of <= 4 symbols)
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t qcap;
     uint32_t stage_n;       // staged matches per warp before a flush

@@ -187,6 +187,38 @@ __device__ __forceinline__ uint32_t gram_at16(const uint8_t *tsm, uint32_t off, 
     return memo_index<SB>(lo, hi, p2, static_cast<int>(r), m, sbits, mask);
 }
 
+// Symbols p .. p + 15 of the packed tile (2 bits each, symbol p lowest):
+// the index of any gram of up to 16 symbols starting at p, after a mask.
+__device__ __forceinline__ uint32_t pk_gram(const uint32_t *pk, uint32_t p) {
+    return __funnelshift_r(pk[p >> 4], pk[(p >> 4) + 1], (p & 15u) * 2u);
+}
+
+// Packs the staged tile (len bytes at tsm) to 2-bit symbols, 16 per word,
+// and checks the bytes of the tile's own starts [0, own) against the
+// alphabet. Every thread of the CTA calls it after the tile's barrier; the
+// caller synchronises before the packed words are read.
+__device__ __forceinline__ void pack_tile(const uint8_t *tsm, uint32_t *pk, uint32_t len,
+                                          uint32_t own, uint32_t S, bool &bad_symbol, int tid,
+                                          int nt) {
+    const uint32_t nwords = (len + 15) / 16 + 1;
+    const uint4 *t4 = reinterpret_cast<const uint4 *>(tsm);
+    for (uint32_t w = tid; w < nwords; w += nt) {
+        const uint4 v = t4[w];
+        const uint64_t lo = v.x | (static_cast<uint64_t>(v.y) << 32);
+        const uint64_t hi = v.z | (static_cast<uint64_t>(v.w) << 32);
+        pk[w] = pack2(lo) | (pack2(hi) << 16);
+        const uint32_t b0 = 16 * w;
+        if (b0 < own) {
+            const uint32_t nb = min(16u, own - b0);
+            uint64_t bl = bytes_ge(lo, S), bh = bytes_ge(hi, S);
+            if (nb < 8) bl &= (1ull << (8 * nb)) - 1;
+            if (nb <= 8) bh = 0;
+            else if (nb < 16) bh &= (1ull << (8 * (nb - 8))) - 1;
+            if (bl | bh) bad_symbol = true;
+        }
+    }
+}
+
 // Prefix-table index of the start at offset `off` of the staged tile (k
 // symbols read from three aligned words; k <= 8).
 template <int SB>
@@ -253,6 +285,7 @@ struct Smem {
     uint32_t *stage;   // this warp's staging buffer
     uint16_t *slots;   // this warp's NFA slots
     uint32_t *coop;    // this warp's two bitsets of Wq words
+    uint32_t *pk;      // the staged tile as 2-bit symbols (2-bit kernels)
 };
 
 __device__ __forceinline__ uint32_t text_at(const TileView &tv, uint32_t pos) {
@@ -842,19 +875,24 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
 #pragma unroll
             for (int g = 0; g < SPT / 8; ++g) {
                 if (static_cast<uint32_t>(8 * g) < nown) {
-                    const uint8_t *tp = tv.sm + (i0 - b) + 8 * g;
-                    const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-                    const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-                    const uint64_t lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-                    const uint64_t hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                    // 2-bit kernels read the packed tile (symbols checked
+                    // when it was packed); others the bytes of the window
+                    uint64_t lo = 0, hi = 0;
+                    if (SB != 2) {
+                        const uint8_t *tp = tv.sm + (i0 - b) + 8 * g;
+                        const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                        const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                        lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                        hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                    }
                     const uint32_t gown = min(8u, nown - 8 * g);
-                    if (mv.S < 256) {
+                    if (SB != 2 && mv.S < 256) {
                         uint64_t badm = bytes_ge(lo, mv.S);
                         if (gown < 8) badm &= (1ull << (8 * gown)) - 1;
                         if (badm) bad_symbol = true;
                     }
                     if (sm.surv) {
-                        const uint32_t p2 = SB == 2 ? (pack2(lo) | (pack2(hi) << 16)) : 0u;
+                        const uint32_t p2 = SB == 2 ? pk_gram(sm.pk, i0 - b + 8 * g) : 0u;
                         if ((SB == 2 || SB == 8) && gown == 8 && i0 + 8 * g + 7 + mm <= n) {
                             // all eight starts have their m-gram: branch-free
                             // indices and keep bits
@@ -916,7 +954,8 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                     off = sm.list[j];
                     keep = true;
                     if (b + off + m2 <= n) {
-                        const uint32_t i2 = gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
+                        const uint32_t i2 = SB == 2 ? pk_gram(sm.pk, off) & m2mask
+                                                    : gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
                         keep = (ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep) >> (i2 & 31)) & 1u;
                     }
                 }
@@ -942,13 +981,14 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 off = sm.list[j];
                 e = PT_WALK;
                 if (kk != 0 && b + off + kk <= n) {
-                    e = sm.memo[kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                    e = sm.memo[SB == 2 ? pk_gram(sm.pk, off) & mask
+                                        : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
                 } else if (kk != 0 && mv.tail) {
                     // fewer than k symbols left: their matches are the whole result
                     const int jl = static_cast<int>(n - (b + off));
                     const uint32_t jm = (1u << (jl * mv.sbits)) - 1;
                     e = __ldg(mv.tail + tail_base(jl, mv.sbits) +
-                              (kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask) & jm));
+                              ((SB == 2 ? pk_gram(sm.pk, off) : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)) & jm));
                 }
             }
             bool push = e != PT_SKIP;
@@ -988,6 +1028,7 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
            : a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
                       : nullptr;
     s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
+    s.pk = reinterpret_cast<uint32_t *>(base + a.sm_pack);
     s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;
     uint8_t *wl = base + a.sm_list + wid * WARP_LIST_BYTES;
     s.list = reinterpret_cast<uint16_t *>(wl);

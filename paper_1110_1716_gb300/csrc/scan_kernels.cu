@@ -70,6 +70,11 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
         if (a.shift) realign_tile(tsm, a.shift, len, tid, NT);   // ends with a barrier
         else __syncthreads();
         if (misc->abort) break;
+        if (SB == 2) {   // 2-bit symbols: pack the tile once for every gram read
+            pack_tile(tsm, sm.pk, len, min(b + a.tile, n) - b, static_cast<uint32_t>(a.S),
+                      bad_symbol, tid, NT);
+            __syncthreads();
+        }
         const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
         process_tile<KIND, SB, TAB_SMEM, 3>(ov, mv, tv, sm, min(b + a.tile, n), wq_n, sn,
                                             bad_symbol, pol_keep, static_cast<uint32_t>(a.settle_steps));
@@ -140,6 +145,8 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     a.pool_smem = need.pool_bytes > 0;
     a.sm_list = take(nw * WARP_LIST_BYTES, 16);
     a.sm_text = take(2 * a.text_buf, 128);
+    // the current tile packed to 2-bit symbols, 16 per word (+1 word read past)
+    a.sm_pack = take(((a.text_buf + 15) / 16 + 2) * 4, 16);
     a.sm_queue = take(nw * WARP_QUEUE * 6, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
