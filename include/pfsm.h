@@ -76,7 +76,8 @@ typedef struct {
                            every instance are looked up once per k-gram;
                            -1 = off (every instance steps from q0); 0 = the
                            deepest table of 16 bits of k-gram index for an
-                           NFA (14 for a DFA), lowered when an NFA's records
+                           NFA (12 for a DFA over fewer than 256 symbols,
+                           16 for bytes), lowered when an NFA's records
                            outgrow 16-bit offsets; an explicit k that does
                            not fit fails with E_INVAL, keeping the old table */
     int32_t tile;       /* starts owned by one CTA tile (multiple of 4096, at

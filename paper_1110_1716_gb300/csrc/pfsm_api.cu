@@ -33,9 +33,10 @@ int ceil_log2(int S) {
 // fits beside the rest, else L2). An NFA takes the deepest table (16 bits):
 // every prefix step it covers is a set union the scan no longer performs
 // per start (a record pool too large for 16-bit offsets lowers k at load).
+// A DFA step is a single lookup: 12 bits keep its table and records small.
 int default_k(const Machine &m) {
     if (m.sbits >= 8) return 2;
-    const int max_bits = m.kind == 0 ? 14 : 16;   // 32 KB / 128 KB of entries
+    const int max_bits = m.kind == 0 ? 12 : 16;   // 8 KB / 128 KB of entries
     int k = std::max(1, max_bits / m.sbits);
     return std::min(k, 8);
 }

@@ -991,6 +991,32 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                               ((SB == 2 ? pk_gram(sm.pk, off) : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)) & jm));
                 }
             }
+            // a record without survivors (its matches end the instance) is
+            // reported here instead of going through the queue
+            {
+                uint32_t pm_left = 0, pm_ptr = 0;
+                if (j < total && e != PT_SKIP && e != PT_WALK && (KIND == 1 || (e & PT_REC))) {
+                    const uint32_t ro = KIND == 1 ? e : (e & 0x7FFFu);
+                    const uint32_t hdr = sm.pool[ro];
+                    if ((hdr >> 16) == 0) {
+                        pm_left = hdr & 0xFFFFu;
+                        pm_ptr = ro + 1;
+                        e = PT_SKIP;
+                    }
+                }
+                while (__any_sync(FULLMASK, pm_left > 0)) {
+                    const bool has = pm_left > 0;
+                    uint32_t o = 0, f = 0;
+                    if (has) {
+                        const uint32_t w = sm.pool[pm_ptr];
+                        o = w >> 16;
+                        f = w & 0xFFFFu;
+                        ++pm_ptr;
+                        --pm_left;
+                    }
+                    warp_emit<OUTW>(has, b + off, b + off + o, f, sm.stage, sn, ov, tv, lane);
+                }
+            }
             bool push = e != PT_SKIP;
             if (settle) {
                 nfa_settle_chunk(mv, sm, tv, j0, total, e, lane, settle_steps);
