@@ -160,7 +160,6 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
         a.tile = tile;
         a.halo = kBatchHalo;
         a.text_buf = (tile + kBatchHalo + 32 + 127) & ~127u;
-        a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;
         base = layout_smem(a, kind ? 2 : 1, threads, SmemNeed{0u, 0u, 0u, 0u, 0u, 0u});
         if (base + kMinArena <= budget) break;
         if (a.stage_n > 32) a.stage_n = 32;

@@ -154,7 +154,6 @@ extern "C" int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_
         a.carry_cap = static_cast<uint32_t>(kNoAllocCarry / 16);
         a.stage_n = STAGE;
         const int threads = 512;
-        a.qcap = static_cast<uint32_t>(FILTER_SPT) * threads;   // one filter round
         SmemNeed need{0u, a.tab_smem ? tab_bytes : 0u, 0u, 0u, 0u, 0u};
         const uint32_t smem = layout_smem(a, 1, threads, need);
         if (smem > kSmemMax - kSmemStatic) return PFSM_E_INVAL;

@@ -718,7 +718,6 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.surv2 = m.dm.surv2;
     a.surv2_m = m.dm.surv2_m;
     a.Wq = m.kind == 1 ? m.dm.Wq : 0;
-    const uint32_t round = static_cast<uint32_t>(FILTER_SPT) * threads;
     uint32_t tab_bytes = m.kind == 0 ? ((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4 : 0;
     // table placement: shared memory when asked, or (auto) when small
     a.tab_smem = 0;
@@ -747,7 +746,6 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     need.coop_bytes = m.kind == 1 ? static_cast<uint32_t>((threads / 32) * 2 * m.dm.Wq * 4) : 0u;
     uint32_t smem = 0;
     bool fit = false;
-    a.qcap = round;   // a filter round may queue every start it owns
     for (int attempt = 0; attempt < 8 && !fit; ++attempt) {
         smem = layout_smem(a, kmask, threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }

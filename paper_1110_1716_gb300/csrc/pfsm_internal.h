@@ -123,7 +123,6 @@ struct ScanArgs {
     int32_t coop_smem;      // NFA: warp-wide bitsets at sm_coop (else in coop_g)
     uint32_t sm_pack;       // the staged tile as 2-bit symbols (alphabets of <= 4 symbols)
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
-    uint32_t qcap;
     uint32_t stage_n;       // staged matches per warp before a flush
     int32_t memo_smem;      // prefix table staged to smem (else read from global)
     int32_t settle_steps;   // NFA: settling step cap (0 = no settling)
