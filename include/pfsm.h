@@ -85,8 +85,9 @@ typedef struct {
                            texts) */
     int32_t halo;       /* text staged past the tile end (multiple of 16) */
     int32_t threads;    /* threads per CTA: 128, 256 or 512 */
-    int32_t spt;        /* reserved: 0 or 8 (the filter takes 32 consecutive
-                           starts per thread per round) */
+    int32_t spt;        /* consecutive starts each thread filters per round:
+                           8 or 32; 0 = automatic (8 for texts too short to
+                           give every SM 16 warps at 32, else 32) */
     int32_t table_smem; /* delta table in shared memory: 1 yes, 0 no, -1 auto */
     int32_t ctas_per_sm;/* persistent CTAs per SM (0 = occupancy maximum) */
     int32_t settle;     /* NFA: steps a surviving instance is advanced in the

@@ -613,7 +613,7 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
     // tile 0 = automatic: 16 KiB, smaller for texts too short to fill the GPU
     if (p.halo == 0) p.halo = 2048;
     // threads 0 = automatic: 512, fewer for texts too short to fill the GPU
-    if (p.spt == 0) p.spt = 8;
+
     if (p.table_smem == 0) p.table_smem = -1;
     if (p.settle == 0) p.settle = 16;
     if (p.partition == 0) p.partition = m.kind == 0 ? 2 : 1;
@@ -626,7 +626,7 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.halo < 16 || p.halo > 16384 || p.halo % 16) return PFSM_E_INVAL;
     if (p.threads != 0 && p.threads != 128 && p.threads != 256 && p.threads != 512)
         return PFSM_E_INVAL;
-    if (p.spt != 8) return PFSM_E_INVAL;
+    if (p.spt != 0 && p.spt != 8 && p.spt != 32) return PFSM_E_INVAL;
     if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
     if (p.settle < -1 || p.settle > 63) return PFSM_E_INVAL;
@@ -675,21 +675,27 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     memset(&a, 0, sizeof(a));
     a.text = text;
     a.n = static_cast<uint32_t>(n);
+    // starts per thread per filter round: 32 for long texts; 8 for texts too
+    // short to give every SM 16 warps of 32-start threads (four times the
+    // warps, so more latency is hidden)
+    int spt = p.spt;
+    if (spt == 0) spt = n < 16ull * ctx->nsm * 32 * FILTER_SPT ? 8 : FILTER_SPT;
+    a.spt = spt;
     int threads = p.threads;
     if (threads == 0) {
-        // a filter round covers FILTER_SPT starts per thread: keep at least
-        // two rounds' worth of tiles per SM
+        // keep at least two filter rounds' worth of tiles per SM
         threads = 512;
-        while (threads > 128 &&
-               n < 2ull * ctx->nsm * static_cast<uint64_t>(FILTER_SPT) * threads)
+        while (threads > 128 && n < 2ull * ctx->nsm * static_cast<uint64_t>(spt) * threads)
             threads /= 2;
     }
     uint32_t tile = static_cast<uint32_t>(p.tile);
-    if (tile == 0) {
+    if (tile == 0 && spt == 8) {
+        tile = static_cast<uint32_t>(spt) * threads;   // one filter round: the most CTAs
+    } else if (tile == 0) {
         // at least two tiles per SM when the text allows it
         const uint64_t want = n / (2ull * ctx->nsm);
         tile = static_cast<uint32_t>(std::min<uint64_t>(16384, std::max<uint64_t>(4096, (want + 4095) & ~4095ull)));
-        tile = std::max<uint32_t>(tile, static_cast<uint32_t>(FILTER_SPT) * threads);
+        tile = std::max<uint32_t>(tile, static_cast<uint32_t>(spt) * threads);
     }
     a.tile = tile;
     a.halo = p.halo;
@@ -760,7 +766,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         else break;
     }
     if (!fit) return PFSM_E_INVAL;
-    int occ = max_ctas_per_sm(m.kind, m.sbits, threads, smem, a.tab_smem != 0);
+    int occ = max_ctas_per_sm(m.kind, m.sbits, threads, smem, a.tab_smem != 0, spt);
     if (occ <= 0) return PFSM_E_INVAL;
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);
     pl.threads = threads;

@@ -126,6 +126,7 @@ struct ScanArgs {
     uint32_t stage_n;       // staged matches per warp before a flush
     int32_t memo_smem;      // prefix table staged to smem (else read from global)
     int32_t settle_steps;   // NFA: settling step cap (0 = no settling)
+    int32_t spt;            // starts per thread per filter round: 8 or 32 (0 = 32)
 };
 
 // ---- batch executor ------------------------------------------------------
@@ -209,7 +210,11 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
 cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
                         cudaStream_t s);
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s);
-int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem);
+int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem, int spt = 32);
+// the kernel instantiated for 8 starts per thread (scan_kernels_spt8.cu)
+cudaError_t launch_scan_spt8(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
+                             cudaStream_t s);
+int max_ctas_per_sm_spt8(int kind, int sbits, int threads, uint32_t smem, bool tab_smem);
 
 // ---- batch launch helpers (batch_kernels.cu) -----------------------------
 int batch_class(int kind, int sbits, int k, bool tab_smem);

@@ -846,11 +846,12 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
 // ------------------------------------------------------------ one tile
 // Filter phase over the tile's own starts [b, own_end), then the
 // continuation of every queued instance. All threads of the CTA call this.
-template <int KIND, int SB, bool TAB_SMEM, int OUTW>
+// SPT: starts per thread per filter round (SPT / 8 windows of 8; 8 or 32).
+template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
                              bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps) {
-    constexpr int SPT = 32;   // starts per thread per filter round (4 windows of 8)
+    static_assert(SPT == 8 || SPT == 32, "SPT");
     const int tid = threadIdx.x, lane = tid & 31;
     const int NT = blockDim.x;
     const uint32_t n = tv.n, b = tv.b;

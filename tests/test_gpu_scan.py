@@ -134,6 +134,9 @@ PARAMS = [
     {"threads": 512, "tile": 32768, "halo": 4096, "ctas_per_sm": 1},
     {"settle": -1},
     {"settle": 2, "prefix_k": 4},
+    {"spt": 32},                                # 32 starts per thread on a short text
+    {"spt": 8, "threads": 512, "tile": 4096},   # 8 per thread, several rounds per tile
+    {"spt": 8, "partition": 1},
 ]
 
 
@@ -145,7 +148,7 @@ def test_params_do_not_change_dfa_result(pf, params):
     assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(d, t))
 
 
-@pytest.mark.parametrize("params", PARAMS[:4] + PARAMS[-2:],
+@pytest.mark.parametrize("params", PARAMS[:4] + PARAMS[6:],
                          ids=lambda p: ",".join("%s=%s" % kv for kv in p.items()))
 def test_params_do_not_change_nfa_result(pf, params):
     nfa, t, _, _ = W.workload_motif_nfa(5, n=150_000, n_motifs=64, every=1500)
