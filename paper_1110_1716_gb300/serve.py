@@ -43,6 +43,43 @@ class Request:
         self.t_done = None
 
 
+def pack_batch(pending, max_jobs: int, text_bytes: int, aut_bytes, budget: int,
+               one_machine: bool = False):
+    """Take requests from the front of `pending` (a deque of objects with
+    .aut and .text) for one batch, in arrival order: at most `max_jobs`, their
+    texts (each padded to 16 bytes) within `text_bytes` (the first one that
+    does not fit ends the batch), and only while the batch's distinct
+    machines fit the residency `budget` together (`aut_bytes[aut]` device
+    bytes each; a request whose machine would not fit is left at the front
+    for the next batch; the first machine is always taken). With
+    `one_machine`, only requests for the first pending request's machine are
+    taken. At most 4 * max_jobs requests are examined. Returns (requests,
+    arena bytes used)."""
+    reqs, used, skipped = [], 0, []
+    machines, mbytes = set(), 0
+    first = pending[0].aut if pending else None
+    scanned = 0
+    while pending and len(reqs) < max_jobs and scanned < 4 * max_jobs:
+        r = pending[0]
+        if used + len(r.text) > text_bytes:
+            break
+        pending.popleft()
+        scanned += 1
+        new = r.aut not in machines
+        if (one_machine and r.aut != first) or (
+                new and machines and mbytes + aut_bytes[r.aut] > budget):
+            skipped.append(r)
+            continue
+        if new:
+            machines.add(r.aut)
+            mbytes += aut_bytes[r.aut]
+        reqs.append(r)
+        used += (len(r.text) + 15) & ~15
+    for r in reversed(skipped):
+        pending.appendleft(r)
+    return reqs, used
+
+
 class _Slot:
     def __init__(self, torch, dev, text_bytes, out_rows, max_jobs):
         self.stream = torch.cuda.Stream(device=dev)
@@ -131,35 +168,11 @@ class Server:
 
     # -------------------------------------------------------------- scheduler
     def _admit(self, slot: _Slot, one_machine: bool = False) -> bool:
-        """Pack pending requests into a free slot and launch its batch, in
-        arrival order, skipping (for the next batch) requests whose machine
-        would take the batch's distinct machines over the residency budget.
-        With `one_machine`, only requests for the first pending request's
-        machine are taken (the fallback when the library still reports that
-        the machines do not fit)."""
-        reqs, used, skipped = [], 0, []
-        machines, mbytes = set(), 0
+        """Pack pending requests into a free slot (``pack_batch``) and launch
+        its batch."""
         with self.lock:
-            first = self.pending[0].aut if self.pending else None
-            scanned = 0
-            while self.pending and len(reqs) < slot.max_jobs and scanned < 4 * slot.max_jobs:
-                r = self.pending[0]
-                if used + len(r.text) > slot.text_bytes:
-                    break
-                self.pending.popleft()
-                scanned += 1
-                new = r.aut not in machines
-                if (one_machine and r.aut != first) or (
-                        new and machines and mbytes + self.aut_bytes[r.aut] > self.budget):
-                    skipped.append(r)
-                    continue
-                if new:
-                    machines.add(r.aut)
-                    mbytes += self.aut_bytes[r.aut]
-                reqs.append(r)
-                used += (len(r.text) + 15) & ~15
-            for r in reversed(skipped):
-                self.pending.appendleft(r)
+            reqs, used = pack_batch(self.pending, slot.max_jobs, slot.text_bytes, self.aut_bytes,
+                                    self.budget, one_machine)
         if not reqs:
             return False
         torch = self.torch

@@ -54,3 +54,52 @@ def test_tuner_candidates_and_cache(tmp_path, monkeypatch):
     assert all(x["threads"] in (256, 512) for x in c)
     tune._store("nfa/Q10/S4/gpu", {"prefix_k": 6}, 1.5)
     assert json.load(open(tmp_path / "cache.json"))["nfa/Q10/S4/gpu"]["params"] == {"prefix_k": 6}
+
+
+# ---------------------------------------------------------------- serving: batch packing
+class _Req:
+    def __init__(self, aut, n):
+        self.aut = aut
+        self.text = bytes(n)
+
+
+def _pack(reqs, **kw):
+    import collections
+    from paper_1110_1716_gb300.serve import pack_batch
+    q = collections.deque(reqs)
+    args = dict(max_jobs=8, text_bytes=1 << 20, aut_bytes=[100] * 8, budget=1 << 30,
+                one_machine=False)
+    args.update(kw)
+    got, used = pack_batch(q, **args)
+    return got, used, list(q)
+
+
+def test_pack_batch_in_order_with_job_and_arena_limits():
+    rs = [_Req(i % 3, 10 + i) for i in range(12)]
+    got, used, left = _pack(rs, max_jobs=5)
+    assert got == rs[:5] and left == rs[5:]
+    assert used == sum((len(r.text) + 15) & ~15 for r in rs[:5])
+    # texts start on 16-byte boundaries; the first one that does not fit the
+    # arena ends the batch (10, 11, 12, 13 bytes fill 64; 14 more do not fit)
+    got, used, left = _pack(rs, text_bytes=64)
+    assert got == rs[:4] and left == rs[4:] and used == 64
+
+
+def test_pack_batch_keeps_machines_within_the_budget():
+    sizes = [60, 50, 30, 10]
+    rs = [_Req(0, 5), _Req(1, 5), _Req(0, 5), _Req(2, 5), _Req(3, 5), _Req(1, 5)]
+    got, used, left = _pack(rs, aut_bytes=sizes, budget=100)
+    # machine 0 (60) then 2 (30) then 3 (10) fit; machine 1 (50) does not: its
+    # requests stay at the front, in order, for the next batch
+    assert [r.aut for r in got] == [0, 0, 2, 3]
+    assert left == [rs[1], rs[5]]
+    # a machine larger than the budget alone is still taken (the library
+    # reports E_NOMEM if it cannot be made resident)
+    got, used, left = _pack([_Req(1, 5), _Req(0, 5)], aut_bytes=sizes, budget=40)
+    assert [r.aut for r in got] == [1] and [r.aut for r in left] == [0]
+
+
+def test_pack_batch_one_machine():
+    rs = [_Req(2, 5), _Req(1, 5), _Req(2, 5), _Req(3, 5), _Req(2, 5)]
+    got, used, left = _pack(rs, one_machine=True)
+    assert [r.aut for r in got] == [2, 2, 2] and [r.aut for r in left] == [1, 3]
