@@ -616,6 +616,9 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+        # the scaling runs measure the main workload only: every GPU is held
+        # for the whole run
+        args.only = True
     line = run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch
