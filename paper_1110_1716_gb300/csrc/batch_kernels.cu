@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
         tma_uses[0] = tma_uses[1] = 0;
     }
     __syncthreads();
-    const Smem sm = smem_regions(smem, A.sa, wid);
+    const Smem sm = smem_regions(smem, A.sa, wid, NT >> 5);
     Misc *misc = sm.misc;
     uint8_t *text_sm = smem + A.sa.sm_text;
     uint8_t *arena = smem + A.sm_arena;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
         process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
-                                       static_cast<uint32_t>(M.settle));
+                                       static_cast<uint32_t>(M.settle), NT);
         // the next tile continues this text: queued instances and staged
         // matches stay; otherwise drain and flush them now (per-text counts
         // need every staged match of a flush to belong to one text)

@@ -137,6 +137,7 @@ extern "C" int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_
         a.halo = 2048;
         a.ntiles = static_cast<uint32_t>((n + a.tile - 1) / a.tile);
         a.text_buf = (a.tile + a.halo + 32 + 127) & ~127u;
+        a.nbuf = 3;
         a.shift = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text_dev) & 15);
         a.Q = Q;
         a.S = S;

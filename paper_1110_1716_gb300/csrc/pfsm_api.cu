@@ -701,6 +701,10 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.halo = p.halo;
     a.ntiles = static_cast<uint32_t>((n + tile - 1) / tile);
     a.text_buf = (tile + p.halo + 32 + 127) & ~127u;
+    // staged tiles: one in use, one being prepared, one in flight; a short
+    // text gives a CTA one or two tiles, and two buffers leave more shared
+    // memory for CTAs
+    a.nbuf = spt == 8 ? 2 : 3;
     a.shift = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15);
     a.Q = m.Q;
     a.S = m.S;

@@ -121,7 +121,9 @@ struct ScanArgs {
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
     int32_t coop_smem;      // NFA: warp-wide bitsets at sm_coop (else in coop_g)
-    uint32_t sm_pack;       // the staged tile as 2-bit symbols (alphabets of <= 4 symbols)
+    uint32_t sm_pack;       // the staged tiles as 2-bit symbols (alphabets of <= 4 symbols)
+    uint32_t pk_words;      // words of one packed tile
+    uint32_t nbuf;          // staged tile buffers, 2 or 3 (layout_smem turns 0 into 2)
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t stage_n;       // staged matches per warp before a flush
     int32_t memo_smem;      // prefix table staged to smem (else read from global)

@@ -102,6 +102,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 // Bounded wait on a bulk-copy barrier: gives up after ~2 s of wall time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -113,8 +116,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // Shared-memory control words of a CTA.
+constexpr int kTileBufs = 3;   // staged tiles in flight in the single-text kernel
 struct Misc {
-    uint64_t bar[2];
+    uint64_t bar[2];              // batch kernel: copy of buffer 0 / 1 landed
+    uint64_t full[kTileBufs];     // single-text kernel: copy landed
+    uint64_t ready[kTileBufs];    //   realigned and packed by the producer warp
+    uint64_t empty[kTileBufs];    //   every consumer warp is done with it
     uint32_t q_count;
     uint32_t q_head;
     uint32_t abort;
@@ -847,13 +854,13 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
 // Filter phase over the tile's own starts [b, own_end), then the
 // continuation of every queued instance. All threads of the CTA call this.
 // SPT: starts per thread per filter round (SPT / 8 windows of 8; 8 or 32).
+// NT consumer threads (ids 0 .. NT - 1) call it together.
 template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
-                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps) {
+                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps, int NT) {
     static_assert(SPT == 8 || SPT == 32, "SPT");
     const int tid = threadIdx.x, lane = tid & 31;
-    const int NT = blockDim.x;
     const uint32_t n = tv.n, b = tv.b;
     const uint32_t kk = static_cast<uint32_t>(mv.k);
     const uint32_t kbits = static_cast<uint32_t>(mv.k * mv.sbits);
@@ -1041,18 +1048,19 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
     }
 }
 
-__device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid) {
+// `nw` = the warps that own per-warp regions (the layout's thread count / 32).
+__device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, int wid, int nw) {
     Smem s;
     s.misc = reinterpret_cast<Misc *>(base + a.sm_misc);
     s.memo = a.memo_smem ? reinterpret_cast<const uint16_t *>(base + a.sm_memo) : a.memo;
     s.tab = reinterpret_cast<const uint16_t *>(base + a.sm_tab);
     s.wq_start = reinterpret_cast<uint32_t *>(base + a.sm_queue) + wid * WARP_QUEUE;
-    s.wq_info = reinterpret_cast<uint16_t *>(base + a.sm_queue + (blockDim.x >> 5) * WARP_QUEUE * 4) +
+    s.wq_info = reinterpret_cast<uint16_t *>(base + a.sm_queue + nw * WARP_QUEUE * 4) +
                 wid * WARP_QUEUE;
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
     s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
     s.coop = a.coop_smem ? reinterpret_cast<uint32_t *>(base + a.sm_coop) + wid * 2 * a.Wq
-           : a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + wid) * 2 * a.Wq
+           : a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * nw + wid) * 2 * a.Wq
                       : nullptr;
     s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
     s.pk = reinterpret_cast<uint32_t *>(base + a.sm_pack);
@@ -1113,6 +1121,42 @@ __device__ __forceinline__ void realign_tile(uint8_t *buf, uint32_t sh, uint32_t
         }
     }
     __syncthreads();
+}
+
+// realign_tile for one warp that owns the buffer (the producer warp of the
+// single-text kernel): the same chunked shift with warp synchronisation.
+__device__ __forceinline__ void realign_tile_warp(uint8_t *buf, uint32_t sh, uint32_t len,
+                                                  int lane) {
+    constexpr int PER = 8;
+    uint4 *b4 = reinterpret_cast<uint4 *>(buf);
+    const uint32_t q = (len + 15) >> 4;
+    const uint32_t ws = sh >> 2, bs = (sh & 3u) * 8u;
+    for (uint32_t c0 = 0; c0 < q; c0 += PER * 32) {
+        uint4 o[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t i = c0 + j * 32 + lane;
+            if (i < q) {
+                const uint4 x = b4[i], y = b4[i + 1];
+                const uint32_t w0 = ws == 0 ? x.x : ws == 1 ? x.y : ws == 2 ? x.z : x.w;
+                const uint32_t w1 = ws == 0 ? x.y : ws == 1 ? x.z : ws == 2 ? x.w : y.x;
+                const uint32_t w2 = ws == 0 ? x.z : ws == 1 ? x.w : ws == 2 ? y.x : y.y;
+                const uint32_t w3 = ws == 0 ? x.w : ws == 1 ? y.x : ws == 2 ? y.y : y.z;
+                const uint32_t w4 = ws == 0 ? y.x : ws == 1 ? y.y : ws == 2 ? y.z : y.w;
+                o[j].x = __funnelshift_r(w0, w1, bs);
+                o[j].y = __funnelshift_r(w1, w2, bs);
+                o[j].z = __funnelshift_r(w2, w3, bs);
+                o[j].w = __funnelshift_r(w3, w4, bs);
+            }
+        }
+        __syncwarp();   // this chunk's reads precede its writes
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t i = c0 + j * 32 + lane;
+            if (i < q) b4[i] = o[j];
+        }
+        __syncwarp();
+    }
 }
 
 // Copies an NFA's band rows and prefix records into shared memory (either

@@ -53,9 +53,12 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     a.band_smem = need.band_bytes > 0;
     a.pool_smem = need.pool_bytes > 0;
     a.sm_list = take(nw * WARP_LIST_BYTES, 16);
-    a.sm_text = take(2 * a.text_buf, 128);
-    // the current tile packed to 2-bit symbols, 16 per word (+1 word read past)
-    a.sm_pack = take(((a.text_buf + 15) / 16 + 2) * 4, 16);
+    if (a.nbuf == 0) a.nbuf = 2;   // the kernels index the buffers by this count
+    const uint32_t nbuf = a.nbuf;
+    a.sm_text = take(nbuf * a.text_buf, 128);
+    // each staged tile packed to 2-bit symbols, 16 per word (+1 word read past)
+    a.pk_words = (a.text_buf + 15) / 16 + 2;
+    a.sm_pack = take(nbuf * a.pk_words * 4, 16);
     a.sm_queue = take(nw * WARP_QUEUE * 6, 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);

@@ -9,14 +9,37 @@
 namespace pfsm {
 
 // ------------------------------------------------------------ single-text kernel
+// Long texts (SPT = 32, many tiles per CTA) run a producer/consumer pipeline.
+// Warps 0 .. NC/32 - 1 are consumers (filter, settling, queues; NC =
+// blockDim.x - 32), the last warp is the producer. The producer copies the
+// CTA's tiles into a.nbuf (3) buffers by TMA, realigns and packs each one and
+// releases it to the consumers (mbarrier `ready`); every consumer warp
+// releases a buffer when it is done with it (`empty`, one arrival per warp),
+// and the producer refills it a.nbuf - 1 tiles on. No CTA-wide barrier
+// holds the warps between tiles: a warp that finished its part of a tile
+// starts on the next one.
+//
+// Short texts (SPT = 8) give a CTA one or two tiles, where a pipeline has
+// nothing to overlap and the producer warp's registers would cost a CTA per
+// SM: every warp filters, two buffers alternate and the CTA synchronises once
+// per tile. Every wait is bounded (2 s) in both forms.
 template <int KIND, int SB, bool TAB_SMEM, int SPT>
-__global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
+__global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const ScanArgs a) {
+    constexpr bool PIPE = SPT != 8;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (PIPE ? (a.nbuf < 2 || a.nbuf > kTileBufs) : a.nbuf != 2) {   // the layout's buffers
+        if (tid == 0) atomicOr(&a.status[1], ERR_SYMBOL);
+        return;
+    }
     const int NT = blockDim.x;
-    const Smem sm = smem_regions(smem, a, wid);
+    const int NC = PIPE ? NT - 32 : NT;   // consumer threads
+    const int ncw = NC >> 5;              // consumer warps
+    const bool producer = PIPE && wid == ncw;
+    const Smem sm = smem_regions(smem, a, producer ? 0 : wid, ncw);
     Misc *misc = sm.misc;
     uint8_t *text_sm = smem + a.sm_text;
+    uint32_t *pk_sm = reinterpret_cast<uint32_t *>(smem + a.sm_pack);
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
@@ -32,56 +55,132 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
         for (uint32_t i = tid; i < a.surv_words; i += NT) d[i] = __ldg(a.surv + i);
     }
     if (tid == 0) {
-        mbar_init(&misc->bar[0], 1);
-        mbar_init(&misc->bar[1], 1);
+        for (int i = 0; i < kTileBufs; ++i) {
+            mbar_init(&misc->full[i], 1);
+            mbar_init(&misc->ready[i], 1);
+            mbar_init(&misc->empty[i], static_cast<uint32_t>(ncw));
+        }
         misc->q_count = 0;
         misc->q_head = 0;
         misc->abort = 0;
         fence_mbar_init();
     }
-    __syncthreads();
+    __syncthreads();   // tables staged, barriers initialised
 
-    uint32_t sn = 0;
-    uint32_t wq_n = 0;   // entries in this warp's queue
-    bool bad_symbol = false;
     const uint32_t n = a.n;
-    // tile `tile` into buffer `buf`: one bulk copy from the 16-byte boundary
-    // at or below its first byte (a 16-byte block never crosses a page, so
-    // the bytes around the text that it covers are readable)
-    auto issue = [&](uint32_t tile, int buf) {
+    const uint32_t nb = a.nbuf;   // staged tile buffers, <= kTileBufs
+    // this CTA's k-th tile is blockIdx.x + k * gridDim.x
+    const uint32_t my_tiles = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0u;
+    bool bad_symbol = false;
+    // tile k into buffer k % nb: one bulk copy from the 16-byte boundary at
+    // or below its first byte (a 16-byte block never crosses a page, so the
+    // bytes around the text that it covers are readable)
+    auto issue = [&](uint32_t k) {
+        const uint32_t tile = blockIdx.x + k * gridDim.x;
+        const int buf = static_cast<int>(k % nb);
         const uint32_t b = tile * a.tile;
         const uint32_t len = min(a.tile + a.halo, n - b);
         const uint32_t bytes = (a.shift + len + 15) & ~15u;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&misc->bar[buf], bytes);
+        mbar_arrive_expect_tx(&misc->full[buf], bytes);
         tma_load_1d(text_sm + buf * a.text_buf,
                     reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(a.text) + b - a.shift),
-                    bytes, &misc->bar[buf], pol_stream);
+                    bytes, &misc->full[buf], pol_stream);
     };
+    uint32_t sn = 0;
+    uint32_t wq_n = 0;   // entries in this warp's queue
+    uint32_t abort_at = ~0u;   // CTA-synchronous form: the tile whose copy failed
 
-    uint32_t it = 0;
-    if (tid == 0 && blockIdx.x < a.ntiles) issue(blockIdx.x, 0);
-    for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
-        const uint32_t parity = (it >> 1) & 1;
-        const uint32_t b = tile * a.tile;
-        const uint32_t len = min(a.tile + a.halo, n - b);
-        uint8_t *tsm = text_sm + buf * a.text_buf;
-        if (tid == 0 && tile + gridDim.x < a.ntiles) issue(tile + gridDim.x, buf ^ 1);
-        if (!mbar_wait_bounded(&misc->bar[buf], parity)) misc->abort = 1;
-        if (a.shift) realign_tile(tsm, a.shift, len, tid, NT);   // ends with a barrier
-        else __syncthreads();
-        if (misc->abort) break;
-        if (SB == 2) {   // 2-bit symbols: pack the tile once for every gram read
-            pack_tile(tsm, sm.pk, len, min(b + a.tile, n) - b, static_cast<uint32_t>(a.S),
-                      bad_symbol, tid, NT);
-            __syncthreads();
+    if constexpr (PIPE) {
+        if (producer) {
+            bool ok = true;
+            uint32_t issued = 0, landed = 0;   // tiles copied / waited for
+            for (; issued < my_tiles && issued < nb - 1; ++issued)
+                if (lane == 0) issue(issued);
+            for (uint32_t k = 0; k < my_tiles; ++k) {
+                const int buf = static_cast<int>(k % nb);
+                const uint32_t tile = blockIdx.x + k * gridDim.x;
+                const uint32_t b = tile * a.tile;
+                const uint32_t len = min(a.tile + a.halo, n - b);
+                uint8_t *tsm = text_sm + buf * a.text_buf;
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->full[buf], (k / nb) & 1));
+                if (!ok) break;
+                landed = k + 1;
+                if (a.shift) realign_tile_warp(tsm, a.shift, len, lane);
+                if (SB == 2)
+                    pack_tile(tsm, pk_sm + buf * a.pk_words, len, min(b + a.tile, n) - b,
+                              static_cast<uint32_t>(a.S), bad_symbol, lane, 32);
+                // the realigned bytes are rewritten by a later bulk copy
+                if (a.shift) fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&misc->ready[buf]);
+                // tile k + nb - 1 goes to the buffer of tile k - 1 once every
+                // consumer warp is done with tile k - 1
+                if (issued < my_tiles) {
+                    if (issued >= nb)
+                        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->empty[issued % nb],
+                                                                       (issued / nb - 1) & 1));
+                    if (!ok) break;
+                    if (lane == 0) issue(issued);
+                    ++issued;
+                }
+            }
+            if (!ok && lane == 0) {
+                misc->abort = 1;
+                atomicOr(&a.status[1], ERR_TIMEOUT);
+                // copies still in flight: wait for them (bounded) before exit
+                for (uint32_t t = landed; t < issued; ++t)
+                    mbar_wait_bounded(&misc->full[t % nb], (t / nb) & 1);
+            }
+            if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
+            return;
         }
-        const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
-        process_tile<KIND, SB, TAB_SMEM, 3, SPT>(ov, mv, tv, sm, min(b + a.tile, n), wq_n, sn,
-                                            bad_symbol, pol_keep, static_cast<uint32_t>(a.settle_steps));
-        // the staged buffer is refilled two tiles on: every warp must be done
-        __syncthreads();
+        Smem smk = sm;
+        for (uint32_t k = 0; k < my_tiles; ++k) {
+            const int buf = static_cast<int>(k % nb);
+            const uint32_t tile = blockIdx.x + k * gridDim.x;
+            const uint32_t b = tile * a.tile;
+            const uint32_t len = min(a.tile + a.halo, n - b);
+            const bool go = mbar_wait_bounded(&misc->ready[buf], (k / nb) & 1) &&
+                            !*reinterpret_cast<volatile uint32_t *>(&misc->abort);
+            if (!__all_sync(0xffffffffu, go)) {
+                if (lane == 0) atomicOr(&a.status[1], ERR_TIMEOUT);
+                break;
+            }
+            smk.pk = pk_sm + buf * a.pk_words;
+            const TileView tv{text_sm + buf * a.text_buf, a.text, b, len, n, 0u, 0u};
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT>(ov, mv, tv, smk, min(b + a.tile, n), wq_n, sn,
+                                                      bad_symbol, pol_keep,
+                                                      static_cast<uint32_t>(a.settle_steps), NC);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&misc->empty[buf]);
+        }
+    } else {
+        if (tid == 0 && my_tiles > 0) issue(0);
+        for (uint32_t k = 0; k < my_tiles; ++k) {
+            const int buf = static_cast<int>(k & 1);
+            const uint32_t tile = blockIdx.x + k * gridDim.x;
+            const uint32_t b = tile * a.tile;
+            const uint32_t len = min(a.tile + a.halo, n - b);
+            uint8_t *tsm = text_sm + buf * a.text_buf;
+            // the other buffer's tile was finished by every warp before the
+            // barrier that ended the previous iteration
+            if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+            if (!mbar_wait_bounded(&misc->full[buf], (k >> 1) & 1)) misc->abort = 1;
+            if (a.shift) realign_tile(tsm, a.shift, len, tid, NT);   // ends with a barrier
+            else __syncthreads();
+            if (misc->abort) { abort_at = k; break; }
+            if (SB == 2) {   // 2-bit symbols: pack the tile once for every gram read
+                pack_tile(tsm, pk_sm, len, min(b + a.tile, n) - b, static_cast<uint32_t>(a.S),
+                          bad_symbol, tid, NT);
+                __syncthreads();
+            }
+            const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT>(ov, mv, tv, sm, min(b + a.tile, n), wq_n, sn,
+                                                      bad_symbol, pol_keep,
+                                                      static_cast<uint32_t>(a.settle_steps), NT);
+            __syncthreads();   // the buffer is refilled next tile: every warp must be done
+        }
     }
     // instances queued across tiles run now, reading the text from global
     // memory (the staged tiles are gone)
@@ -91,11 +190,11 @@ __global__ void __launch_bounds__(512, 1) scan_tiles(const ScanArgs a) {
     }
     stage_flush<3>(sm.stage, sn, ov, 0u, lane);
     if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
-    if (tid == 0 && misc->abort) {
+    if (!PIPE && tid == 0 && abort_at != ~0u) {
         atomicOr(&a.status[1], ERR_TIMEOUT);
-        // a copy may still be in flight: wait for it (bounded) before exit
-        mbar_wait_bounded(&misc->bar[0], 0);
-        mbar_wait_bounded(&misc->bar[1], 0);
+        // copies still in flight: wait for them (bounded) before exit
+        for (uint32_t t = abort_at; t < my_tiles && t < abort_at + 2; ++t)
+            mbar_wait_bounded(&misc->full[t & 1], (t >> 1) & 1);
     }
 }
 
@@ -105,7 +204,7 @@ static cudaError_t launch_t(const ScanArgs &a, int threads, int grid, uint32_t s
     auto k = scan_tiles<KIND, SB, TAB, SPT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, threads, smem, s>>>(a);
+    k<<<grid, threads + (SPT == 8 ? 0 : 32), smem, s>>>(a);   // + the producer warp
     return cudaGetLastError();
 }
 
@@ -122,13 +221,16 @@ static int occ_t(int threads, uint32_t smem) {
     int nb = 0;
     cudaFuncSetAttribute(scan_tiles<KIND, SB, TAB, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_tiles<KIND, SB, TAB, SPT>, threads,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_tiles<KIND, SB, TAB, SPT>,
+                                                      threads + (SPT == 8 ? 0 : 32), smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
 
-// Launch and occupancy of the kernel instantiated for SPT starts per thread.
+// Launch and occupancy of the kernel instantiated for SPT starts per thread;
+// `threads` counts the filtering threads (the pipelined form's producer warp
+// is added here).
 template <int SPT>
 static cudaError_t launch_scan_spt(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
                                    cudaStream_t s) {
