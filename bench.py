@@ -17,6 +17,9 @@ Printed: ONE JSON line (rank 0) with
              written) over its CUDA-event duration, against the measured HBM
              copy bandwidth
   cpu_baseline  the CPU oracle on a bounded sample of the same text
+  work       the paper's work unit, (start, state) pairs advanced over a
+             symbol, counted by the oracle over the whole text, per second of
+             the scan kernel, against the integer-issue peak
   clocks     SM clocks and throttle reasons sampled during the timed region
   workloads  the other scan shapes measured the same way (DNA DFA, byte trie)
 
@@ -191,6 +194,43 @@ def oracle_parallel(aut, text, n, threads):
     return time.perf_counter() - t0, sum(len(p) for p in parts)
 
 
+def oracle_work(aut, text, threads):
+    """The work of the paper's per-symbol procedure (Sec. III.B) over the
+    whole text, counted by the oracle: (start, state) pairs advanced over a
+    symbol, start windows split over `threads` host threads. Returns
+    (pair_steps, matches, seconds)."""
+    import concurrent.futures
+    import oracle
+    n = len(text)
+    bounds = [n * i // threads for i in range(threads + 1)]
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda i: oracle.pair_steps(aut, text, bounds[i], bounds[i + 1]),
+                            range(threads)))
+    return sum(p[0] for p in parts), sum(p[1] for p in parts), time.perf_counter() - t0
+
+
+# INT32 lanes per SM (Blackwell: 128 cores, each able to take a 32-bit integer op per clock)
+INT_LANES_PER_SM = 128
+
+
+def work_rate(res, nsm, sm_mhz):
+    """Pair-steps per second of the scan kernel against the integer-issue
+    peak (one 32-bit integer op per pair-step on every lane of every SM)."""
+    cores = max(1, os.cpu_count() or 1)
+    steps, cnt, secs = oracle_work(res["aut"], res["text"], cores)
+    rate = steps / (res["kernel_ms"] * 1e-3)
+    peak = nsm * INT_LANES_PER_SM * sm_mhz * 1e6
+    return {"unit": "pair-steps/s", "bound": "alu", "achieved": rate, "peak": peak,
+            "frac": rate / peak, "pair_steps": steps,
+            "pair_steps_per_byte": steps / max(1, len(res["text"])),
+            "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz, one op per pair-step"
+                          % (nsm, INT_LANES_PER_SM, sm_mhz),
+            "source": "oracle count over the whole text, %d start windows on %d threads, %.1f s"
+                      % (cores, cores, secs),
+            "oracle_matches": cnt, "matches_agree": cnt == res["matches"]}
+
+
 def cpu_baseline(aut, text, seconds_target=12.0):
     """The oracle as it is on a prefix of the text sized to take roughly
     `seconds_target` on one thread (probe on 256 KiB first): the prefix on
@@ -321,6 +361,8 @@ def run_ours(args, rank, world, local_rank):
         return res
 
     main = measure(args.workload, args.steps, args.warmup, args.seed)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(main["clocks"].get("sm_max_mhz") or 2070.0)
     others = {}
     if not args.only and not args.no_batch:
         others["batch_10k_texts"] = measure_batch(P, pf, torch, dev)
@@ -337,6 +379,8 @@ def run_ours(args, rank, world, local_rank):
             others[name] = {k: r[k] for k in ("desc", "bytes", "matches", "ms_per_step", "gbps",
                                               "matches_per_s", "kernel_ms", "roofline", "e2e",
                                               "params")}
+            if name == "dna_dfa_1mib" and rank == 0 and not args.no_cpu_baseline:
+                others[name]["work"] = work_rate(r, nsm, sm_mhz)
     if rank != 0:
         return None
     line = {
@@ -360,6 +404,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(main["aut"], main["text"])
+        line["work"] = work_rate(main, nsm, sm_mhz)
     return line
 
 

@@ -15,6 +15,10 @@ M(t, A) = {(i, j, f) : i <= j < n, f in F, f in delta^({q0}, t[i..j])}:
 * ``literal_occurrences``: for a set of literal strings, M is the set of all
   their occurrences; found here with ``bytes.find``.
 
+``pair_steps`` gives the work of the tagged-state procedure: the number of
+(start, state) pairs it advances over a symbol, summed over the text
+(``brute_force_pair_steps`` computes the same number by definition).
+
 Matches are returned as uint32 arrays of shape (m, 3) holding
 (start, end, state) rows sorted lexicographically; ``end`` is inclusive
 (Fig. 2 of the paper lists "c" at [2-2]).
@@ -52,6 +56,8 @@ def _bind(lib):
     lib.oracle_run_segment.restype = I64
     lib.oracle_run_segment.argtypes = [P, P, I, I, I, I, P, P, U64, U64, U64, U64,
                                        P, U64, P, I64, P, I64, P, P]
+    lib.oracle_pair_steps.restype = I64
+    lib.oracle_pair_steps.argtypes = [P, P, I, I, I, I, P, P, U64, U64, U64, P, P]
 
 
 def _load():
@@ -191,6 +197,37 @@ def run_segment(aut, text: np.ndarray, j_begin: int, j_end: int, reinit_lo: int,
         acap = max(acap, int(n_act.value))
 
 
+def pair_steps(aut, text: np.ndarray, s_lo: int = 0, s_hi: Optional[int] = None):
+    """Work of the tagged-state procedure (Sec. III.B) for the starts in
+    [s_lo, s_hi): (pair_steps, matches), where pair_steps counts the (tag,
+    state) pairs advanced over a symbol, summed over the positions, and
+    matches is the size of the match set (not stored)."""
+    text = np.ascontiguousarray(text, dtype=np.uint8)
+    final = np.ascontiguousarray(aut.final, dtype=np.uint8)
+    if getattr(aut, "eps", None) is not None:
+        raise ValueError("the oracle takes epsilon-free machines; remove epsilon edges first")
+    if hasattr(aut, "delta"):
+        delta = np.ascontiguousarray(aut.delta, dtype=np.int16)
+        bits = None
+        Q, S = delta.shape
+        dead = aut.dead
+    else:
+        delta = None
+        bits = np.ascontiguousarray(aut.bits, dtype=np.uint32)
+        Q, S, _ = bits.shape
+        dead = -1
+    n = len(text)
+    s_hi = n if s_hi is None else s_hi
+    work = ctypes.c_uint64(0)
+    err = ctypes.c_int(0)
+    cnt = _load().oracle_pair_steps(_ptr(delta), _ptr(bits), Q, S, aut.q0, dead, _ptr(final),
+                                    _ptr(text), n, s_lo, s_hi, ctypes.byref(work),
+                                    ctypes.byref(err))
+    if cnt < 0:
+        raise ValueError("oracle error %d" % err.value)
+    return int(work.value), int(cnt)
+
+
 # ----------------------------------------------------------------------------
 # The definition, read directly (Sec. II, acalculia by exhaustive restarts)
 # ----------------------------------------------------------------------------
@@ -255,6 +292,33 @@ def brute_force(aut, text: Sequence[int]) -> np.ndarray:
             if not cur:
                 break
     return sort_matches(np.array(out, dtype=np.uint32).reshape(-1, 3))
+
+
+def brute_force_pair_steps(aut, text: Sequence[int], s_lo: int = 0,
+                           s_hi: Optional[int] = None) -> int:
+    """The work count by definition: for every start i in [s_lo, s_hi), the
+    size of the instance's state set before each symbol t[j] ({q0} before
+    t[i], then delta^({q0}, t[i..j-1])), summed over j = i .. n - 1 while the
+    set is non-empty. The DFA form's dead state and missing transitions hold
+    no instance. Epsilon-free machines; quadratic in n: tiny inputs only."""
+    Q, S, succ, eps = _succ_sets(aut)
+    if any(eps):
+        raise ValueError("epsilon-free machines only")
+    dead = getattr(aut, "dead", -1)
+    n = len(text)
+    s_hi = n if s_hi is None else s_hi
+    total = 0
+    for i in range(s_lo, s_hi):
+        cur = {aut.q0}
+        for j in range(i, n):
+            total += len(cur)
+            nxt = set()
+            for q in cur:
+                nxt |= succ[q][int(text[j])]
+            cur = {q for q in nxt if 0 <= q < Q and q != dead}
+            if not cur:
+                break
+    return total
 
 
 def literal_occurrences(sigs: Iterable[bytes], final_of: dict, text: np.ndarray) -> np.ndarray:

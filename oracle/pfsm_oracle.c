@@ -39,6 +39,11 @@
  * of tagged active states and hand back the tagged active states left at its
  * end, so a segment's survivors can be continued on the next segment.
  *
+ * Work (Sec. III.B): each position advances every (tag, state) pair active
+ * after step 1 over one symbol; the number of such pair-steps, summed over
+ * the positions, is the work of the procedure (a DFA instance is one pair;
+ * an NFA instance is one pair per state of its set).
+ *
  * Data structures are deliberately naive: one sorted, duplicate-free array of
  * tags per state, and a list of the active states. Transitions are read from
  * per-(state, symbol) successor lists built once from the caller's table (for
@@ -107,13 +112,15 @@ static int ts_union(tagset *dst, const tagset *src, uint32_t **scratch, uint32_t
  *   out_active if not NULL, receives up to active_cap (tag, state) pairs left
  *              active after the last processed position; *n_active gets the
  *              full number
+ *   pair_steps if not NULL, gets the number of (tag, state) pairs advanced
+ *              over a symbol, summed over the processed positions
  * Returns the number of matches (which may exceed cap), or -1 on error with
  * *err set (OR_EINVAL: a symbol >= S; OR_ENOMEM).
  */
 static int64_t run(const machine *m, const uint8_t *text, uint64_t j_begin, uint64_t j_end,
                    uint64_t reinit_lo, uint64_t reinit_hi, const uint32_t *in_pairs,
                    uint64_t n_in, uint32_t *out, int64_t cap, uint32_t *out_active,
-                   int64_t active_cap, int64_t *n_active, int *err) {
+                   int64_t active_cap, int64_t *n_active, uint64_t *pair_steps, int *err) {
     int Q = m->Q;
     tagset *cur = (tagset *)calloc((size_t)Q, sizeof(tagset));
     tagset *nxt = (tagset *)calloc((size_t)Q, sizeof(tagset));
@@ -121,6 +128,7 @@ static int64_t run(const machine *m, const uint8_t *text, uint64_t j_begin, uint
     int32_t *act2 = (int32_t *)malloc((size_t)Q * sizeof(int32_t));
     uint32_t *scratch = NULL, scap = 0;
     int64_t count = 0;
+    uint64_t work = 0;
     int na = 0;
     *err = OR_OK;
     if (!cur || !nxt || !act || !act2) { *err = OR_ENOMEM; count = -1; goto done; }
@@ -154,6 +162,7 @@ static int64_t run(const machine *m, const uint8_t *text, uint64_t j_begin, uint
         int nb = 0;
         for (int k = 0; k < na; k++) {
             int q = act[k];
+            work += cur[q].n; /* every tag on q is advanced over t[j] */
             uint32_t lo = m->off[(size_t)q * m->S + a], hi = m->off[(size_t)q * m->S + a + 1];
             for (uint32_t e = lo; e < hi; e++) {
                 int t = m->succ[e];
@@ -200,6 +209,7 @@ static int64_t run(const machine *m, const uint8_t *text, uint64_t j_begin, uint
     }
 
 done:
+    if (pair_steps) *pair_steps = work;
     if (cur) for (int q = 0; q < Q; q++) free(cur[q].v);
     if (nxt) for (int q = 0; q < Q; q++) free(nxt[q].v);
     free(cur); free(nxt); free(act); free(act2); free(scratch);
@@ -259,7 +269,7 @@ int64_t oracle_scan_dfa(const int16_t *delta, int Q, int S, int q0, int dead, co
                         uint32_t *out, int64_t cap, int *err) {
     machine m;
     if (machine_from_dfa(&m, delta, Q, S, q0, dead, fin)) { machine_free(&m); *err = OR_ENOMEM; return -1; }
-    int64_t r = run(&m, text, s_lo, n, s_lo, s_hi, NULL, 0, out, cap, NULL, 0, NULL, err);
+    int64_t r = run(&m, text, s_lo, n, s_lo, s_hi, NULL, 0, out, cap, NULL, 0, NULL, NULL, err);
     machine_free(&m);
     return r;
 }
@@ -270,7 +280,7 @@ int64_t oracle_scan_nfa(const uint32_t *bits, int Q, int S, int q0, const uint8_
                         uint32_t *out, int64_t cap, int *err) {
     machine m;
     if (machine_from_nfa(&m, bits, Q, S, q0, fin)) { machine_free(&m); *err = OR_ENOMEM; return -1; }
-    int64_t r = run(&m, text, s_lo, n, s_lo, s_hi, NULL, 0, out, cap, NULL, 0, NULL, err);
+    int64_t r = run(&m, text, s_lo, n, s_lo, s_hi, NULL, 0, out, cap, NULL, 0, NULL, NULL, err);
     machine_free(&m);
     return r;
 }
@@ -289,7 +299,24 @@ int64_t oracle_run_segment(const int16_t *delta, const uint32_t *bits, int Q, in
                    : machine_from_dfa(&m, delta, Q, S, q0, dead, fin);
     if (bad) { machine_free(&m); *err = OR_ENOMEM; return -1; }
     int64_t r = run(&m, text, j_begin, j_end, reinit_lo, reinit_hi, in_pairs, n_in, out, cap,
-                    out_active, active_cap, n_active, err);
+                    out_active, active_cap, n_active, NULL, err);
+    machine_free(&m);
+    return r;
+}
+
+/* The work of the scan of either table form (bits == NULL selects the DFA
+ * form) for the starts in [s_lo, s_hi): *pair_steps gets the number of
+ * (tag, state) pairs advanced over a symbol. The matches are counted, not
+ * stored; the count is returned (or -1 with *err set). */
+int64_t oracle_pair_steps(const int16_t *delta, const uint32_t *bits, int Q, int S, int q0,
+                          int dead, const uint8_t *fin, const uint8_t *text, uint64_t n,
+                          uint64_t s_lo, uint64_t s_hi, uint64_t *pair_steps, int *err) {
+    machine m;
+    int bad = bits ? machine_from_nfa(&m, bits, Q, S, q0, fin)
+                   : machine_from_dfa(&m, delta, Q, S, q0, dead, fin);
+    if (bad) { machine_free(&m); *err = OR_ENOMEM; return -1; }
+    int64_t r = run(&m, text, s_lo, n, s_lo, s_hi, NULL, 0, NULL, 0, NULL, 0, NULL, pair_steps,
+                    err);
     machine_free(&m);
     return r;
 }

@@ -291,3 +291,55 @@ def test_empty_and_invalid_inputs():
     assert oracle.scan(d, np.zeros(0, dtype=np.uint8)).shape == (0, 3)
     with pytest.raises(ValueError):
         oracle.scan(d, np.array([0, 7], dtype=np.uint8))
+
+
+# ---------------------------------------------------------------- work (pair-steps)
+def test_pair_steps_closed_forms():
+    """Closed forms of the number of (start, state) pairs advanced over a
+    symbol (Sec. III.B): a complete DFA keeps every start alive, so position
+    j advances j + 1 pairs (n(n+1)/2 in all); a DFA whose every move enters
+    the dead state advances only the new start (n); an NFA with
+    q0 -> {q0, q1}, q1 -> {q1} on every symbol holds two states per older
+    start (1 + 2j at position j, n^2 in all)."""
+    for n in (0, 1, 7, 300):
+        t = W.text_uniform(n, 3, n + 1)
+        full = W.dfa_random(5, Q=7, S=3, dead=-1, finals=[1, 2], p_dead=0.0)
+        assert oracle.pair_steps(full, t)[0] == n * (n + 1) // 2
+        delta = np.full((4, 3), 3, dtype=np.int16)
+        alldead = W.Dfa(delta=delta, q0=0, dead=3, final=np.array([0, 1, 0, 0], np.uint8))
+        assert oracle.pair_steps(alldead, t) == (n, 0)
+        two = W.nfa_from_edges(2, 3, 0, [(0, a, 0) for a in range(3)] + [(0, a, 1) for a in range(3)]
+                               + [(1, a, 1) for a in range(3)], [1])
+        # every start i reaches the final q1 at every end j >= i
+        assert oracle.pair_steps(two, t) == (n * n, n * (n + 1) // 2)
+
+
+@pytest.mark.parametrize("name,m", small_machines(), ids=lambda x: x if isinstance(x, str) else "")
+def test_pair_steps_equal_definition(name, m):
+    """The tagged-state procedure's count equals the count by definition
+    (per start, the size of its set before every symbol), on every short
+    text and on random longer ones, for whole texts and start windows."""
+    maxlen = 4 if m.S >= 4 else 5
+    for n in range(0, maxlen + 1):
+        for t in itertools.product(range(m.S), repeat=n):
+            t = np.array(t, dtype=np.uint8)
+            assert oracle.pair_steps(m, t)[0] == oracle.brute_force_pair_steps(m, t), t.tolist()
+    rng = np.random.default_rng(13)
+    for n in (40, 150):
+        t = rng.integers(0, m.S, size=n, dtype=np.uint8)
+        w, cnt = oracle.pair_steps(m, t)
+        assert w == oracle.brute_force_pair_steps(m, t)
+        assert cnt == len(oracle.brute_force(m, t))
+        lo, hi = 13, 101
+        assert oracle.pair_steps(m, t, lo, hi)[0] == oracle.brute_force_pair_steps(m, t, lo, hi)
+
+
+def test_pair_steps_additive_over_start_windows():
+    """Lazy data partitioning (Sec. III.D.2) splits the work exactly: the
+    windows' counts add up to the whole text's."""
+    nfa, text, _, _ = W.workload_motif_nfa(3, n=1 << 14, n_motifs=24)
+    whole = oracle.pair_steps(nfa, text)
+    cuts = [0, 1, 999, 5000, 5001, 1 << 14]
+    parts = [oracle.pair_steps(nfa, text, cuts[i], cuts[i + 1]) for i in range(len(cuts) - 1)]
+    assert whole == (sum(p[0] for p in parts), sum(p[1] for p in parts))
+    assert whole[1] == len(oracle.scan(nfa, text))

@@ -30,6 +30,10 @@ MUTANTS = {
     # report rule tests the source state instead of the target
     "report_source": ("if (!m->fin[t]) continue;", "if (!m->fin[t] || !m->fin[act[0]]) continue;"),
     # successor row read for the wrong symbol (previous one)
+    # the work count takes one per active state instead of one per (tag, state) pair
+    "work_counts_states": ("work += cur[q].n;", "work += 1;"),
+    # the work count misses the pairs of the first active state
+    "work_skips_first": ("work += cur[q].n;", "work += k ? cur[q].n : 0;"),
     "symbol_index": ("uint32_t lo = m->off[(size_t)q * m->S + a], hi = m->off[(size_t)q * m->S + a + 1];",
                      "uint32_t a2 = j ? text[j - 1] : a; uint32_t lo = m->off[(size_t)q * m->S + a2], "
                      "hi = m->off[(size_t)q * m->S + a2 + 1];"),
@@ -69,6 +73,18 @@ def battery():
         ok = False
     if not ok:
         failed.append("literal")
+    # the work count against its closed form and its definition
+    try:
+        full = W.dfa_random(5, Q=7, S=3, dead=-1, finals=[1, 2], p_dead=0.0)
+        t3 = W.text_uniform(50, 3, 2)
+        ok = oracle.pair_steps(full, t3)[0] == 50 * 51 // 2
+        nfa = W.nfa_from_edges(4, 2, 0, [(0, 0, 1), (0, 0, 2), (1, 1, 3), (2, 1, 0), (3, 0, 3)], [3])
+        t2 = W.text_uniform(60, 2, 4)
+        ok = ok and oracle.pair_steps(nfa, t2)[0] == oracle.brute_force_pair_steps(nfa, t2)
+    except Exception:
+        ok = False
+    if not ok:
+        failed.append("pair_steps")
     return failed
 
 
