@@ -41,7 +41,7 @@ __device__ __forceinline__ uint32_t find_unit_job(const BatchJob *jobs, uint32_t
 
 __device__ __forceinline__ MView mview_of(const DevMachine &m) {
     return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.surv2_m, m.surv2, m.dtab, m.off, m.tgt,
-                 m.tail, m.ecl_off, m.ecl_tgt};
+                 m.tail, m.ecl_off, m.ecl_tgt, m.l2tab, m.pool2};
 }
 
 // Copies `words` 32-bit words (16-byte aligned source and destination).

@@ -132,19 +132,44 @@ static std::vector<uint16_t> nfa_initial(const Machine &m) {
 
 struct NfaMemoBuilder {
     Machine &m;
-    std::map<std::vector<uint32_t>, uint32_t> recs;
+    std::map<std::vector<uint32_t>, uint32_t> recs, recs2;
     std::vector<uint32_t> mark;
     uint32_t stamp = 0;
     bool ok = true;
+    // second level: the survivor sets of first-level records without
+    // matches, indexed in order of appearance, and where their index words
+    // sit in the pool
+    bool l2 = false;
+    std::map<std::vector<uint16_t>, uint32_t> set_index;
+    std::vector<std::vector<uint16_t>> l2sets;
+    std::vector<size_t> index_words;
 
     explicit NfaMemoBuilder(Machine &mm) : m(mm), mark(mm.Q, 0) {}
 
-    uint16_t record(const std::vector<uint32_t> &matches, const std::vector<uint16_t> &set) {
+    static std::vector<uint32_t> encode(const std::vector<uint32_t> &matches,
+                                        const std::vector<uint16_t> &set) {
         std::vector<uint32_t> rec;
         rec.push_back(static_cast<uint32_t>(matches.size()) |
                       (static_cast<uint32_t>(set.size()) << 16));
         rec.insert(rec.end(), matches.begin(), matches.end());
         for (uint16_t q : set) rec.push_back(q);
+        return rec;
+    }
+
+    uint16_t record(const std::vector<uint32_t> &matches, const std::vector<uint16_t> &set) {
+        std::vector<uint32_t> rec = encode(matches, set);
+        const bool indexed = l2 && matches.empty() && !set.empty();
+        if (indexed) {
+            auto si = set_index.find(set);
+            uint32_t x = static_cast<uint32_t>(l2sets.size());
+            if (si == set_index.end()) {
+                set_index.emplace(set, x);
+                l2sets.push_back(set);
+            } else {
+                x = si->second;
+            }
+            rec.push_back(x < L2_MAX_SETS ? x : L2_NONE);
+        }
         auto it = recs.find(rec);
         if (it != recs.end()) return static_cast<uint16_t>(it->second);
         const uint32_t at = static_cast<uint32_t>(m.pool.size());
@@ -154,7 +179,82 @@ struct NfaMemoBuilder {
         }
         recs.emplace(rec, at);
         m.pool.insert(m.pool.end(), rec.begin(), rec.end());
+        if (indexed) index_words.push_back(m.pool.size() - 1);
         return static_cast<uint16_t>(at);
+    }
+
+    // second-level record: word offset in pool2, or L2_EMPTY (and ok2 false)
+    // when pool2 is full
+    bool ok2 = true;
+    uint16_t record2(const std::vector<uint32_t> &matches, const std::vector<uint16_t> &set) {
+        std::vector<uint32_t> rec = encode(matches, set);
+        auto it = recs2.find(rec);
+        if (it != recs2.end()) return static_cast<uint16_t>(it->second);
+        const uint32_t at = static_cast<uint32_t>(m.pool2.size());
+        if (at >= L2_EMPTY || matches.size() > 0xFFFF || set.size() > 0xFFFF) {
+            ok2 = false;
+            return L2_EMPTY;
+        }
+        recs2.emplace(rec, at);
+        m.pool2.insert(m.pool2.end(), rec.begin(), rec.end());
+        return static_cast<uint16_t>(at);
+    }
+
+    // One step of a set on symbol a: the next set (sorted) and the finals met,
+    // recorded as (index of the symbol from the start) << 16 | state.
+    void step(const std::vector<uint16_t> &set, int a, uint32_t sym_index,
+              std::vector<uint16_t> &next, std::vector<uint32_t> &nm) {
+        ++stamp;
+        for (uint16_t q : set) {
+            nfa_step(m, q, a, [&](uint16_t t) {
+                const uint16_t ts = t & 0x7FFF;
+                if (mark[ts] == stamp) return;
+                mark[ts] = stamp;
+                next.push_back(ts);
+                if (t & FINAL_BIT) nm.push_back((sym_index << 16) | ts);
+            });
+        }
+        std::sort(next.begin(), next.end());
+    }
+
+    // second level of set x: d of its L2_SYMS symbols consumed (g holds them)
+    void dfs2(uint32_t x, int d, uint32_t g, const std::vector<uint16_t> &set,
+              const std::vector<uint32_t> &matches) {
+        if (!ok2) return;
+        uint16_t *tab = m.l2tab.data() + static_cast<size_t>(x) * L2_GRAMS;
+        if (d == L2_SYMS) {
+            if (!matches.empty() || !set.empty()) tab[g] = record2(matches, set);
+            return;
+        }
+        if (set.empty()) {
+            // every extension of these d symbols has the same record
+            if (matches.empty()) return;   // L2_EMPTY already
+            const uint16_t id = record2(matches, set);
+            for (uint32_t hiw = 0; hiw < (1u << (2 * (L2_SYMS - d))); ++hiw)
+                tab[g | (hiw << (2 * d))] = id;
+            return;
+        }
+        for (int a = 0; a < 4; ++a) {
+            if (a >= m.S) continue;   // such grams raise E_INVAL anyway
+            std::vector<uint16_t> next;
+            std::vector<uint32_t> nm = matches;
+            step(set, a, static_cast<uint32_t>(m.k + d), next, nm);
+            dfs2(x, d + 1, g | (static_cast<uint32_t>(a) << (2 * d)), next, nm);
+        }
+    }
+
+    // The second-level tables of the indexed sets; without them (too many
+    // records) every index word becomes L2_NONE.
+    void build_l2() {
+        const uint32_t nsets = static_cast<uint32_t>(std::min<size_t>(l2sets.size(), L2_MAX_SETS));
+        m.l2tab.assign(static_cast<size_t>(nsets) * L2_GRAMS, L2_EMPTY);
+        m.pool2.clear();
+        for (uint32_t x = 0; x < nsets && ok2; ++x) dfs2(x, 0, 0, l2sets[x], {});
+        if (!ok2 || nsets == 0) {
+            m.l2tab.clear();
+            m.pool2.clear();
+            for (size_t w : index_words) m.pool[w] = L2_NONE;
+        }
     }
 
     // depth symbols consumed (index bits below depth*sbits fixed to prefix)
@@ -186,17 +286,7 @@ struct NfaMemoBuilder {
             if (a >= m.S) continue;   // such k-grams raise E_INVAL anyway
             std::vector<uint16_t> next;
             std::vector<uint32_t> nm = matches;
-            ++stamp;
-            for (uint16_t q : set) {
-                nfa_step(m, q, a, [&](uint16_t t) {
-                    const uint16_t ts = t & 0x7FFF;
-                    if (mark[ts] == stamp) return;
-                    mark[ts] = stamp;
-                    next.push_back(ts);
-                    if (t & FINAL_BIT) nm.push_back((static_cast<uint32_t>(depth) << 16) | ts);
-                });
-            }
-            std::sort(next.begin(), next.end());
+            step(set, a, static_cast<uint32_t>(depth), next, nm);
             dfs(depth + 1, prefix | (static_cast<uint32_t>(a) << (depth * sb)), next, nm);
         }
     }
@@ -205,6 +295,8 @@ struct NfaMemoBuilder {
 bool build_memo_nfa(Machine &m) {
     m.pool.clear();
     m.tail.clear();
+    m.l2tab.clear();
+    m.pool2.clear();
     if (m.k <= 0) {
         m.memo.clear();
         return true;
@@ -214,8 +306,11 @@ bool build_memo_nfa(Machine &m) {
     const uint32_t ntail = tail_base(m.k, m.sbits);
     m.tail.assign(ntail + (ntail & 1), PT_SKIP);
     NfaMemoBuilder b(m);
+    // second level where one packed 16-symbol gram covers k + L2_SYMS symbols
+    b.l2 = m.sbits == 2 && m.k + L2_SYMS <= 16;
     b.dfs(0, 0, nfa_initial(m), {});
     if (!b.ok) return false;
+    if (b.l2) b.build_l2();
     if (m.pool.empty()) m.pool.push_back(0);
     return true;
 }
@@ -329,7 +424,8 @@ size_t device_bytes(const Machine &m) {
     } else {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
              align256(m.pool.size() * 4) + align256(m.band.size() * 4) +
-             align256(m.ecl_off.size() * 4) + align256(m.ecl_tgt.size() * 2 + 4);
+             align256(m.ecl_off.size() * 4) + align256(m.ecl_tgt.size() * 2 + 4) +
+             align256(m.l2tab.size() * 2) + align256(m.pool2.size() * 4);
     }
     return b;
 }
@@ -456,6 +552,8 @@ static int build_host_image(Machine &m) {
         m.o_band = put(m.band.data(), m.band.size() * 4, 0);
         m.o_eoff = put(m.ecl_off.data(), m.ecl_off.size() * 4, 0);
         m.o_etgt = put(m.ecl_tgt.data(), m.ecl_tgt.size() * 2, 4);
+        m.o_l2tab = put(m.l2tab.data(), m.l2tab.size() * 2, 0);
+        m.o_pool2 = put(m.pool2.data(), m.pool2.size() * 4, 0);
     }
     if (o > bytes) {   // layout and size disagree: a bug, fail loudly
         cudaFreeHost(h);
@@ -496,6 +594,8 @@ static DevMachine dev_view(const Machine &m, uint8_t *base) {
         dm.band = m.band.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_band);
         dm.ecl_off = m.ecl_off.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_eoff);
         dm.ecl_tgt = m.ecl_off.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_etgt);
+        dm.l2tab = m.l2tab.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_l2tab);
+        dm.pool2 = m.l2tab.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_pool2);
     }
     return dm;
 }
@@ -720,6 +820,8 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.off = m.dm.off;
     a.tgt = m.dm.tgt;
     a.pool = m.dm.pool;
+    a.l2tab = m.dm.l2tab;
+    a.pool2 = m.dm.pool2;
     a.pool_n = m.dm.pool_n;
     a.band = m.dm.band;
     a.surv = m.dm.surv;

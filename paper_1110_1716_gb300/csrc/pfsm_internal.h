@@ -36,6 +36,23 @@ constexpr uint16_t PT_WALK = 0xFFFE;
 constexpr uint16_t PT_REC = 0x8000;
 constexpr uint32_t PT_REC_MAX = 0x7FFD;   // largest record offset
 
+// NFA second-level records (2-bit alphabets with k + L2_SYMS <= 16): they
+// carry a start L2_SYMS symbols past the prefix table. A first-level record
+// with survivors and no matches holds one more word after its survivors,
+// the index x of its survivor set (L2_NONE: no second level). Entry
+// l2tab[x * 4^L2_SYMS + g], for the next L2_SYMS symbols g of the text
+// (g = sum g[i] << 2i), is L2_EMPTY when no state of the set survives them
+// and none meets a final state on the way, else the word offset in `pool2`
+// of a record in the first-level format whose match steps count from the
+// start (k .. k + L2_SYMS - 1) and whose survivors are the states after
+// k + L2_SYMS symbols.
+constexpr int L2_SYMS = 5;
+constexpr uint32_t L2_GRAMS = 1u << (2 * L2_SYMS);
+constexpr uint16_t L2_NONE = 0xFFFF;
+constexpr uint16_t L2_EMPTY = 0xFFFF;
+constexpr uint32_t L2_MAX_SETS = 4096;   // at most 8 MB of second-level tables
+constexpr uint32_t L2_NO_REC = 0xFFFFFFFFu;   // (device) a start without a second-level record
+
 // NFA short-gram table: a start with only j < k symbols left before the end
 // of its text has its whole future fixed by those j symbols: the matches it
 // meets within them. Entry tail_base(j) + (index of the j-gram) holds
@@ -98,6 +115,8 @@ struct ScanArgs {
     const uint32_t *off;    // NFA: [Q*S + 1] CSR offsets
     const uint16_t *tgt;    // NFA: targets
     const uint32_t *pool;   // NFA: prefix records
+    const uint16_t *l2tab;  // NFA: second-level tables (see L2_SYMS), or null
+    const uint32_t *pool2;  // NFA: second-level records
     const uint32_t *band;   // NFA: band image (rows, then final bitmap) or null
     uint32_t pool_n;        // NFA: words of pool
     int32_t pool_smem;      // NFA: pool staged to smem
@@ -165,6 +184,8 @@ struct DevMachine {
     const uint32_t *off;
     const uint16_t *tgt;
     const uint32_t *pool;
+    const uint16_t *l2tab;  // NFA: second-level tables, or null
+    const uint32_t *pool2;
     const uint32_t *band;
     uint32_t pool_n;
     int32_t surv_m;

@@ -252,6 +252,8 @@ struct MView {
     const uint16_t *tail;   // NFA short-gram table, or null
     const uint32_t *ecl_off;// NFA with epsilon edges: epsilon closure lists, or null
     const uint16_t *ecl_tgt;
+    const uint16_t *l2tab;  // NFA second-level tables (see L2_SYMS), or null
+    const uint32_t *pool2;  // NFA second-level records
 };
 
 // Where matches and carried instances go.
@@ -515,24 +517,28 @@ __device__ __forceinline__ bool marked(const uint32_t *marks, uint32_t j) {
 }
 
 static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const TileView &tv,
-                                 uint32_t j0, uint32_t total, uint32_t e, int lane,
+                                 uint32_t j0, uint32_t total, uint32_t e, uint32_t r2, int lane,
                                  uint32_t max_steps) {
     uint32_t *pairs = sm.pairs;
     uint32_t *pcount = sm.pcount;
     uint32_t *marks = sm.marks;
     const uint32_t b = tv.b, n = tv.n, tile_end = tv.b + tv.len;
     const uint32_t *fin = sm.band + mv.Q;
-    // 1. pairs from the prefix records of entries j0 + lane
+    // 1. pairs from the prefix records of entries j0 + lane: the first-level
+    //    record (its survivors at step 0, k symbols past the start) or, where
+    //    the lane has one (r2 != L2_NO_REC), the second-level record (its
+    //    survivors at step L2_SYMS)
     {
         const uint32_t j = j0 + lane;
         uint32_t ns = 0, rec = 0;
+        const bool lvl2 = r2 != L2_NO_REC;
         if (j < total) {
             if (e == PT_WALK) {
                 mark_entry(marks, j);
             } else if (e != PT_SKIP) {
-                const uint32_t hdr = sm.pool[e];
+                const uint32_t hdr = lvl2 ? __ldg(mv.pool2 + r2) : sm.pool[e];
                 if (hdr & 0xFFFFu) mark_entry(marks, j);   // matches inside the prefix
-                else ns = hdr >> 16, rec = e;
+                else ns = hdr >> 16, rec = lvl2 ? r2 : e;
             }
         }
         uint32_t incl = ns;
@@ -544,9 +550,16 @@ static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const T
         const uint32_t base = *pcount + incl - ns;
         const bool fits = base + ns <= static_cast<uint32_t>(SETTLE_PAIRS);
         if (ns && !fits) mark_entry(marks, j);
-        if (ns && fits)
-            for (uint32_t x = 0; x < ns; ++x)
-                pairs[base + x] = (j << 21) | sm.pool[rec + 1 + x];   // step 0
+        if (ns && fits) {
+            if (lvl2) {
+                for (uint32_t x = 0; x < ns; ++x)
+                    pairs[base + x] = (j << 21) | (static_cast<uint32_t>(L2_SYMS) << 15) |
+                                      __ldg(mv.pool2 + rec + 1 + x);
+            } else {
+                for (uint32_t x = 0; x < ns; ++x)
+                    pairs[base + x] = (j << 21) | sm.pool[rec + 1 + x];   // step 0
+            }
+        }
         const uint32_t end = __reduce_max_sync(FULLMASK, (ns && fits) ? base + ns : 0u);
         __syncwarp();
         if (lane == 0 && end > *pcount) *pcount = end;
@@ -985,12 +998,30 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
         for (uint32_t j0 = 0; j0 < total; j0 += 32) {
             const uint32_t j = j0 + lane;
             uint32_t e = PT_SKIP, off = 0;
+            uint32_t r2 = L2_NO_REC;   // second-level record of this lane's start
             if (j < total) {
                 off = sm.list[j];
                 e = PT_WALK;
                 if (kk != 0 && b + off + kk <= n) {
-                    e = sm.memo[SB == 2 ? pk_gram(sm.pk, off) & mask
+                    const uint32_t gram = SB == 2 ? pk_gram(sm.pk, off) : 0u;
+                    e = sm.memo[SB == 2 ? gram & mask
                                         : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                    // an NFA record with survivors and no matches carries the
+                    // start L2_SYMS symbols further through the second level
+                    if (KIND == 1 && SB == 2 && mv.l2tab && e < PT_WALK &&
+                        b + off + kk + L2_SYMS <= n) {
+                        const uint32_t hdr = sm.pool[e];
+                        if ((hdr & 0xFFFFu) == 0) {
+                            const uint32_t x = sm.pool[e + 1 + (hdr >> 16)];
+                            if (x != L2_NONE) {
+                                const uint32_t o2 = ldg_u16_keep(
+                                    mv.l2tab + x * L2_GRAMS + ((gram >> (2 * kk)) & (L2_GRAMS - 1)),
+                                    pol_keep);
+                                if (o2 == L2_EMPTY) e = PT_SKIP;   // nothing left: no match
+                                else r2 = o2;
+                            }
+                        }
+                    }
                 } else if (kk != 0 && mv.tail) {
                     // fewer than k symbols left: their matches are the whole result
                     const int jl = static_cast<int>(n - (b + off));
@@ -1027,7 +1058,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             }
             bool push = e != PT_SKIP;
             if (settle) {
-                nfa_settle_chunk(mv, sm, tv, j0, total, e, lane, settle_steps);
+                nfa_settle_chunk(mv, sm, tv, j0, total, e, r2, lane, settle_steps);
                 push = j < total && marked(sm.marks, j);
             }
             const uint32_t pmask = __ballot_sync(FULLMASK, push);

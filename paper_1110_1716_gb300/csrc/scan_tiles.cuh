@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
     const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
-                   a.tail, a.ecl_off, a.ecl_tgt};
+                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2};
 
     if (a.memo_smem) stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
     if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);

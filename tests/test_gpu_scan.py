@@ -417,3 +417,68 @@ def test_async_status_and_stream(pf):
     cnt, err = status.tolist()
     assert err == 0 and cnt == len(want)
     assert np.array_equal(oracle.sort_matches(out[:cnt].cpu().numpy().view(np.uint32)), want)
+
+
+# ---------------------------------------------------------------- second-level prefix records
+def twin_chain_nfa(seed, H=100, L=16, p_die=0.08, p_fin=0.04):
+    """Two independent chains run side by side from q0: chain c has states
+    (c, d, h) for depth d = 1..L and hash h < H, and symbol a moves (c, d, h)
+    to (c, d + 1, f_c(d, h, a)) or nowhere (probability p_die). The state set
+    after d symbols holds at most one state per chain, so the sets met after
+    8 symbols are pairs of hashes: about H^2 of them, more than the 4096 sets
+    that get second-level tables. Finals are scattered over depths 9..L.
+    Returns the machine and the set of (h1, h2) pairs met after 8 symbols by
+    starts that have met no final state (counted by direct simulation)."""
+    rng = np.random.default_rng(seed)
+    S = 4
+    Q = 1 + 2 * L * H
+    sid = lambda c, d, h: 1 + (c * L + (d - 1)) * H + h
+    f = rng.integers(0, H, size=(2, L + 1, H, S))
+    die = rng.random((2, L + 1, H, S)) < p_die
+    edges = []
+    for c in range(2):
+        for a in range(S):
+            h0 = int(f[c, 0, 0, a])
+            if not die[c, 0, 0, a]:
+                edges.append((0, a, sid(c, 1, h0)))
+            for d in range(1, L):
+                for h in range(H):
+                    if not die[c, d, h, a]:
+                        edges.append((sid(c, d, h), a, sid(c, d + 1, int(f[c, d, h, a]))))
+    fins = [sid(c, d, h) for c in range(2) for d in range(9, L + 1) for h in range(H)
+            if rng.random() < p_fin]
+    m = W.nfa_from_edges(Q, S, 0, edges, fins)
+    # the sets after 8 symbols, over every 8-gram (no final before depth 9)
+    grams = np.arange(1 << 16)
+    hs, alive = [], []
+    for c in range(2):
+        h = np.zeros(len(grams), dtype=np.int64)
+        ok = np.ones(len(grams), dtype=bool)
+        for d in range(8):
+            a = (grams >> (2 * d)) & 3
+            ok &= ~die[c, d, h if d else 0, a]
+            h = f[c, d, h if d else 0, a]
+        hs.append(np.where(ok, h, -1))
+    pairs = {(int(x), int(y)) for x, y in zip(hs[0], hs[1]) if x >= 0 or y >= 0}
+    return m, pairs
+
+
+def test_second_level_records_beyond_the_table_cap(pf):
+    """More survivor sets after k = 8 symbols than get second-level tables:
+    starts on the first 4096 sets take the second level (empty entries
+    dismiss them, others settle from k + 5 symbols or take the exact path),
+    the rest settle from k symbols. Every start must still report exactly
+    the oracle's matches, near text ends too."""
+    m, pairs = twin_chain_nfa(7)
+    assert len(pairs) > 4096
+    a = pf.load(m)
+    for n, seed in ((200_000, 1), (16_399, 2), (13, 3), (9, 4)):
+        t = W.text_uniform(n, 4, 900 + seed)
+        want = oracle.scan(m, t)
+        if n > 1000:
+            assert len(want) > 100
+        assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 8), want), n
+    for k in (3, 7):
+        P.pfsm_set_params(pf.ctx, a, {"prefix_k": k})
+        t = W.text_uniform(50_000, 4, 950 + k)
+        assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), k
