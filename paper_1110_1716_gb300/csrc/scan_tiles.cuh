@@ -15,7 +15,7 @@ namespace pfsm {
 // CTA's tiles into a.nbuf (3) buffers by TMA, realigns and packs each one and
 // releases it to the consumers (mbarrier `ready`); every consumer warp
 // releases a buffer when it is done with it (`empty`, one arrival per warp),
-// and the producer refills it a.nbuf - 1 tiles on. No CTA-wide barrier
+// and the producer refills it a.nbuf tiles on. No CTA-wide barrier
 // holds the warps between tiles: a warp that finished its part of a tile
 // starts on the next one.
 //
@@ -93,43 +93,61 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
 
     if constexpr (PIPE) {
         if (producer) {
+            // Two duties, polled without blocking so that neither waits on
+            // the other: a tile whose copy landed is realigned, packed and
+            // handed over at once; a buffer every consumer warp released is
+            // refilled at once. A fast warp can thus run a whole tile ahead
+            // of the slowest one.
             bool ok = true;
-            uint32_t issued = 0, landed = 0;   // tiles copied / waited for
-            for (; issued < my_tiles && issued < nb - 1; ++issued)
+            uint32_t issued = 0, prepped = 0;   // copies issued / tiles handed over
+            for (; issued < my_tiles && issued < nb; ++issued)
                 if (lane == 0) issue(issued);
-            for (uint32_t k = 0; k < my_tiles; ++k) {
-                const int buf = static_cast<int>(k % nb);
-                const uint32_t tile = blockIdx.x + k * gridDim.x;
-                const uint32_t b = tile * a.tile;
-                const uint32_t len = min(a.tile + a.halo, n - b);
-                uint8_t *tsm = text_sm + buf * a.text_buf;
-                ok = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->full[buf], (k / nb) & 1));
-                if (!ok) break;
-                landed = k + 1;
-                if (a.shift) realign_tile_warp(tsm, a.shift, len, lane);
-                if (SB == 2)
-                    pack_tile(tsm, pk_sm + buf * a.pk_words, len, min(b + a.tile, n) - b,
-                              static_cast<uint32_t>(a.S), bad_symbol, lane, 32);
-                // the realigned bytes are rewritten by a later bulk copy
-                if (a.shift) fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&misc->ready[buf]);
-                // tile k + nb - 1 goes to the buffer of tile k - 1 once every
-                // consumer warp is done with tile k - 1
-                if (issued < my_tiles) {
-                    if (issued >= nb)
-                        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->empty[issued % nb],
-                                                                       (issued / nb - 1) & 1));
-                    if (!ok) break;
+            uint64_t idle_since = global_ns();
+            while (prepped < my_tiles) {
+                bool progress = false;
+                const int buf = static_cast<int>(prepped % nb);
+                if (prepped < issued &&
+                    __all_sync(0xffffffffu, mbar_test_wait(&misc->full[buf], (prepped / nb) & 1))) {
+                    const uint32_t tile = blockIdx.x + prepped * gridDim.x;
+                    const uint32_t b = tile * a.tile;
+                    const uint32_t len = min(a.tile + a.halo, n - b);
+                    uint8_t *tsm = text_sm + buf * a.text_buf;
+                    if (a.shift) realign_tile_warp(tsm, a.shift, len, lane);
+                    if (SB == 2)
+                        pack_tile(tsm, pk_sm + buf * a.pk_words, len, min(b + a.tile, n) - b,
+                                  static_cast<uint32_t>(a.S), bad_symbol, lane, 32);
+                    // the realigned bytes are rewritten by a later bulk copy
+                    if (a.shift) fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&misc->ready[buf]);
+                    ++prepped;
+                    progress = true;
+                }
+                // tile `issued` goes to the buffer of tile issued - nb once
+                // every consumer warp is done with that tile
+                if (issued < my_tiles &&
+                    __all_sync(0xffffffffu, mbar_test_wait(&misc->empty[issued % nb],
+                                                           (issued / nb - 1) & 1))) {
                     if (lane == 0) issue(issued);
                     ++issued;
+                    progress = true;
+                }
+                if (progress) {
+                    idle_since = global_ns();
+                } else {
+                    // give up after 2 s without progress (one decision per warp)
+                    if (__shfl_sync(0xffffffffu, global_ns() - idle_since > 2000000000ull ? 1 : 0, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
                 }
             }
             if (!ok && lane == 0) {
                 misc->abort = 1;
                 atomicOr(&a.status[1], ERR_TIMEOUT);
                 // copies still in flight: wait for them (bounded) before exit
-                for (uint32_t t = landed; t < issued; ++t)
+                for (uint32_t t = prepped; t < issued; ++t)
                     mbar_wait_bounded(&misc->full[t % nb], (t / nb) & 1);
             }
             if (bad_symbol) atomicOr(&a.status[1], ERR_SYMBOL);
