@@ -146,12 +146,25 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
     BatchShape &sh = ctx->batch_shape[cls];
     if (sh.ready) return PFSM_OK;
     const int kind = cls >= 6 ? 1 : 0;
+    // filtering threads per CTA (the kernel adds its producer warp): an NFA
+    // class keeps 512 threads in all, so 15 filtering warps
     int threads = ctx->batch_threads ? ctx->batch_threads : (kind ? 512 : 256);
+    if (kind && threads + 32 > 512) threads = 480;
     const int ctas = ctx->batch_ctas ? ctx->batch_ctas : (kind ? 1 : 2);
     uint32_t tile = ctx->batch_tile ? ctx->batch_tile : kBatchTile;
+    // whole filter rounds (32 starts per filtering thread) per tile
+    auto whole_rounds = [&](uint32_t t, int th) {
+        const uint32_t round = 32u * static_cast<uint32_t>(th);
+        return std::max(round, t / round * round);
+    };
+    tile = whole_rounds(tile, threads);
     ScanArgs a;
     memset(&a, 0, sizeof(a));
     a.stage_n = kind ? 32 : STAGE;
+    // staged tiles: three for the NFA classes (one CTA per SM); two for the
+    // DFA classes, whose two CTAs per SM share the shared memory with their
+    // table arenas
+    a.nbuf = kind ? 3 : 2;
     const uint32_t share = ctx->smem_sm / static_cast<uint32_t>(ctas);
     const uint32_t budget =
         std::min<uint32_t>(kSmemMax, share > ctx->smem_rsv ? share - ctx->smem_rsv : 0) - kSmemStatic;
@@ -163,9 +176,13 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
         base = layout_smem(a, kind ? 2 : 1, threads, SmemNeed{0u, 0u, 0u, 0u, 0u, 0u});
         if (base + kMinArena <= budget) break;
         if (a.stage_n > 32) a.stage_n = 32;
-        else if (tile > 8192) tile = 8192;
-        else if (threads > 128) threads /= 2;
-        else return PFSM_E_INVAL;
+        else if (tile > 8192) tile = whole_rounds(8192, threads);
+        else if (threads > 128) {
+            threads /= 2;
+            tile = whole_rounds(tile, threads);
+        } else {
+            return PFSM_E_INVAL;
+        }
     }
     if (base + kMinArena > budget) return PFSM_E_INVAL;
     const uint32_t arena = (budget - base) & ~15u;

@@ -25,7 +25,7 @@ namespace pfsm {
 // One claimed tile of a unit.
 struct UnitDesc {
     const uint8_t *text;
-    uint32_t valid, job, orig, mach, b, len, n, sh, parity;
+    uint32_t valid, job, orig, mach, b, len, n, sh;
 };
 
 // Last job of [lo, hi) whose unit_begin <= u.
@@ -56,100 +56,228 @@ __device__ __forceinline__ void stage_words(uint8_t *dst, const void *src, uint3
     for (uint32_t i = 4 * quads + tid; i < words; i += nt) d1[i] = __ldg(s1 + i);
 }
 
+// Warps 0 .. NC/32 - 1 filter (NC = blockDim.x - 32; at most 15 warps for
+// the NFA classes, which keeps their 128 registers per thread); the last
+// warp is the producer. The producer claims work units through the class's atomic
+// cursor, copies their tiles by TMA into A.sa.nbuf buffers, realigns and
+// packs each one and hands it over with its descriptor (mbarrier `ready`);
+// each filtering warp releases a buffer when it is done with it (`empty`,
+// one arrival per warp). A descriptor that is not valid ends the work. The
+// producer polls both duties, so a landed tile is handed over while older
+// tiles are still in use. Filtering warps meet only when the machine
+// changes (two meetings on a bounded mbarrier around the restaging of the
+// table arena); a warp whose next tile belongs to another text first drains
+// its queue and flushes its staged matches (per-text counts need every
+// flush to belong to one text). Every wait is bounded (2 s).
 template <int KIND, int SB, bool TAB>
-__global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict__ gargs) {
+__global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const BatchArgs *__restrict__ gargs) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ BatchArgs A;
-    __shared__ UnitDesc desc[2];
-    __shared__ uint32_t tma_uses[2];
+    __shared__ UnitDesc desc[kTileBufs];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int NT = blockDim.x;
-    if (tid == 0) {
-        A = *gargs;
-        tma_uses[0] = tma_uses[1] = 0;
-    }
+    const int NC = NT - 32;   // filtering threads
+    const int ncw = NC >> 5;
+    const bool producer = wid == ncw;
+    if (tid == 0) A = *gargs;
     __syncthreads();
-    const Smem sm = smem_regions(smem, A.sa, wid, NT >> 5);
+    const uint32_t nb = A.sa.nbuf;
+    if (nb < 2 || nb > static_cast<uint32_t>(kTileBufs)) {   // the layout's buffers
+        if (tid == 0) atomicOr(&A.sa.status[1], ERR_SYMBOL);
+        return;
+    }
+    const Smem sm = smem_regions(smem, A.sa, producer ? 0 : wid, ncw);
     Misc *misc = sm.misc;
     uint8_t *text_sm = smem + A.sa.sm_text;
+    uint32_t *pk_sm = reinterpret_cast<uint32_t *>(smem + A.sa.sm_pack);
     uint8_t *arena = smem + A.sm_arena;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{A.sa.out, A.sa.cap, A.sa.status, A.job_counts, A.sa.carry, A.sa.carry_n,
                    A.sa.carry_cap, A.sa.stage_n};
     if (tid == 0) {
-        mbar_init(&misc->bar[0], 1);
-        mbar_init(&misc->bar[1], 1);
+        for (int i = 0; i < kTileBufs; ++i) {
+            mbar_init(&misc->full[i], 1);
+            mbar_init(&misc->ready[i], 1);
+            mbar_init(&misc->empty[i], static_cast<uint32_t>(ncw));
+        }
+        mbar_init(&misc->bar[0], static_cast<uint32_t>(ncw));   // filtering warps' meetings
         misc->q_count = 0;
         misc->q_head = 0;
         misc->abort = 0;
         fence_mbar_init();
     }
-
-    // thread 0's cursor: the tiles [cur_tile, cur_end) of job cur_job remain
-    // in its current unit
-    uint32_t cur_job = 0, cur_tile = 0, cur_end = 0;
-    // thread 0: take the next tile (claiming a new unit when the current one
-    // is used up) and start its copy into buffer `buf`
-    auto claim = [&](int buf) {
-        UnitDesc &d = desc[buf];
-        if (cur_tile >= cur_end) {
-            const uint32_t u = atomicAdd(A.unit_counter, 1u);
-            if (u >= A.nunits) {
-                d.valid = 0;
-                return;
-            }
-            cur_job = find_unit_job(A.jobs, A.job_lo, A.job_hi, u);
-            const BatchJob &J = A.jobs[cur_job];
-            cur_tile = (u - J.unit_begin) * A.unit_tiles;
-            cur_end = min(cur_tile + A.unit_tiles, J.ntiles);
-        }
-        const BatchJob &J = A.jobs[cur_job];
-        d.valid = 1;
-        d.job = cur_job;
-        d.text = J.text;
-        d.n = J.n;
-        d.orig = J.orig;
-        d.mach = J.mach;
-        d.b = cur_tile * A.sa.tile;
-        ++cur_tile;
-        d.len = min(A.sa.tile + A.sa.halo, d.n - d.b);
-        // one bulk copy from the 16-byte boundary at or below the tile's
-        // first byte (the block it starts in lies in the text's page)
-        const uintptr_t src = reinterpret_cast<uintptr_t>(d.text) + d.b;
-        d.sh = static_cast<uint32_t>(src & 15u);
-        const uint32_t bytes = (d.sh + d.len + 15) & ~15u;
-        d.parity = tma_uses[buf] & 1;
-        tma_uses[buf]++;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&misc->bar[buf], bytes);
-        tma_load_1d(text_sm + buf * A.sa.text_buf, reinterpret_cast<const void *>(src - d.sh), bytes,
-                    &misc->bar[buf], pol_stream);
-    };
-    if (tid == 0) claim(0);
     __syncthreads();
+
+    if (producer) {
+        // lane 0's cursor: the tiles [cur_tile, cur_end) of job cur_job remain
+        // in its current unit
+        uint32_t cur_job = 0, cur_tile = 0, cur_end = 0;
+        // tile k into buffer k % nb (lane 0 claims it and starts its copy);
+        // returns whether there was one
+        auto claim = [&](uint32_t k) -> bool {
+            uint32_t valid = 0;
+            if (lane == 0) {
+                UnitDesc &d = desc[k % nb];
+                valid = 1;
+                if (cur_tile >= cur_end) {
+                    const uint32_t u = atomicAdd(A.unit_counter, 1u);
+                    if (u >= A.nunits) {
+                        valid = 0;
+                    } else {
+                        cur_job = find_unit_job(A.jobs, A.job_lo, A.job_hi, u);
+                        const BatchJob &J = A.jobs[cur_job];
+                        cur_tile = (u - J.unit_begin) * A.unit_tiles;
+                        cur_end = min(cur_tile + A.unit_tiles, J.ntiles);
+                    }
+                }
+                d.valid = valid;
+                if (valid) {
+                    const BatchJob &J = A.jobs[cur_job];
+                    d.job = cur_job;
+                    d.text = J.text;
+                    d.n = J.n;
+                    d.orig = J.orig;
+                    d.mach = J.mach;
+                    d.b = cur_tile * A.sa.tile;
+                    ++cur_tile;
+                    d.len = min(A.sa.tile + A.sa.halo, d.n - d.b);
+                    // one bulk copy from the 16-byte boundary at or below the
+                    // tile's first byte (the block it starts in lies in the
+                    // text's page)
+                    const uintptr_t src = reinterpret_cast<uintptr_t>(d.text) + d.b;
+                    d.sh = static_cast<uint32_t>(src & 15u);
+                    const uint32_t bytes = (d.sh + d.len + 15) & ~15u;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&misc->full[k % nb], bytes);
+                    tma_load_1d(text_sm + (k % nb) * A.sa.text_buf,
+                                reinterpret_cast<const void *>(src - d.sh), bytes, &misc->full[k % nb],
+                                pol_stream);
+                }
+            }
+            return __shfl_sync(0xffffffffu, valid, 0) != 0;
+        };
+        bool ok = true;
+        uint32_t issued = 0, prepped = 0;   // tiles claimed / handed over
+        uint32_t total = 0xFFFFFFFFu;       // index of the closing (invalid) descriptor
+        while (issued < nb && total == 0xFFFFFFFFu) {
+            if (!claim(issued)) total = issued;
+            ++issued;
+        }
+        uint64_t idle_since = global_ns();
+        while (true) {
+            bool progress = false;
+            if (prepped < issued) {
+                const int buf = static_cast<int>(prepped % nb);
+                if (prepped == total) {   // the closing descriptor: no copy
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&misc->ready[buf]);
+                    break;
+                }
+                if (__all_sync(0xffffffffu, mbar_test_wait(&misc->full[buf], (prepped / nb) & 1))) {
+                    __syncwarp();   // lane 0's descriptor writes are visible
+                    const UnitDesc d = desc[buf];
+                    uint8_t *tsm = text_sm + buf * A.sa.text_buf;
+                    if (d.sh) realign_tile_warp(tsm, d.sh, d.len, lane);
+                    if (SB == 2) {
+                        bool bad = false;
+                        pack_tile(tsm, pk_sm + buf * A.sa.pk_words, d.len, min(d.b + A.sa.tile, d.n) - d.b,
+                                  static_cast<uint32_t>(A.machs[d.mach].S), bad, lane, 32);
+                        if (bad) atomicOr(&A.sa.status[1], ERR_SYMBOL);
+                    }
+                    // the realigned bytes are rewritten by a later bulk copy
+                    if (d.sh) fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&misc->ready[buf]);
+                    ++prepped;
+                    progress = true;
+                }
+            }
+            // tile `issued` goes to the buffer of tile issued - nb once every
+            // filtering warp is done with that tile
+            if (total == 0xFFFFFFFFu &&
+                __all_sync(0xffffffffu, mbar_test_wait(&misc->empty[issued % nb], (issued / nb - 1) & 1))) {
+                if (!claim(issued)) total = issued;
+                ++issued;
+                progress = true;
+            }
+            if (progress) {
+                idle_since = global_ns();
+            } else {
+                // give up after 2 s without progress (one decision per warp)
+                if (__shfl_sync(0xffffffffu, global_ns() - idle_since > 2000000000ull ? 1 : 0, 0)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (!ok && lane == 0) {
+            misc->abort = 1;
+            atomicOr(&A.sa.status[1], ERR_TIMEOUT);
+            // copies still in flight: wait for them (bounded) before exit
+            for (uint32_t t = prepped; t < issued; ++t)
+                if (t != total) mbar_wait_bounded(&misc->full[t % nb], (t / nb) & 1);
+        }
+        return;
+    }
 
     uint32_t sn = 0;
     uint32_t wq_n = 0;
     bool bad_symbol = false;
-    uint32_t cur_mach = 0xFFFFFFFFu;
+    bool aborted = false;
+    uint32_t cur_mach = 0xFFFFFFFFu;   // machine whose tables the arena holds
+    uint32_t meet = 0;                 // meetings so far
     Smem smi = sm;
-    for (uint32_t it = 0;; ++it) {
-        const int buf = it & 1;
+    // the previous tile's text: its queue is drained when the text changes
+    bool have_prev = false;
+    UnitDesc prev{};
+    OView prev_ov = ov;
+    // every filtering warp arrives and waits (bounded)
+    auto meet_all = [&]() -> bool {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&misc->bar[0]);
+        const bool okm = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->bar[0], meet & 1));
+        ++meet;
+        return okm;
+    };
+    // drains this warp's queue of the previous text (reading it from global
+    // memory: its staged tile may be gone) and flushes its staged matches
+    auto drain_prev = [&]() {
+        const MView pmv = mview_of(A.machs[prev.mach]);
+        const TileView ptv{text_sm, prev.text, 0u, 0u, prev.n, prev.job, prev.orig};
+        drain<KIND, TAB, 4>(prev_ov, pmv, ptv, smi, wq_n, sn, lane, pol_keep);
+        stage_flush<4>(sm.stage, sn, ov, prev.orig, lane);
+    };
+    for (uint32_t k = 0;; ++k) {
+        const int buf = static_cast<int>(k % nb);
+        const bool go = mbar_wait_bounded(&misc->ready[buf], (k / nb) & 1) &&
+                        !*reinterpret_cast<volatile uint32_t *>(&misc->abort);
+        if (!__all_sync(0xffffffffu, go)) {
+            if (lane == 0) atomicOr(&A.sa.status[1], ERR_TIMEOUT);
+            aborted = true;
+            break;
+        }
         const UnitDesc d = desc[buf];
         if (!d.valid) break;
-        if (tid == 0) claim(buf ^ 1);   // prefetch the next tile
+        if (have_prev && d.job != prev.job) drain_prev();
         const DevMachine &M = A.machs[d.mach];
         if (d.mach != cur_mach) {
-            // a new machine: every warp drained the previous one's queues and
-            // passed the barrier that ended its last tile
-            if (M.a_surv != kNotStaged) stage_words(arena + M.a_surv, M.surv, M.surv_words, tid, NT);
-            if (M.a_memo != kNotStaged) stage_words(arena + M.a_memo, M.memo, (M.memo_n + 1) / 2, tid, NT);
-            if (TAB) stage_words(arena + M.a_tab, M.dtab, (static_cast<uint32_t>(M.Q) * M.S + 1) / 2, tid, NT);
+            // a new machine: every warp is done with the old one's tables
+            // (its queue drained above) before the arena is rewritten, and
+            // the new tables are complete before any warp reads them
+            if (!meet_all()) {
+                if (lane == 0) atomicOr(&A.sa.status[1], ERR_TIMEOUT);
+                aborted = true;
+                break;
+            }
+            if (M.a_surv != kNotStaged) stage_words(arena + M.a_surv, M.surv, M.surv_words, tid, NC);
+            if (M.a_memo != kNotStaged) stage_words(arena + M.a_memo, M.memo, (M.memo_n + 1) / 2, tid, NC);
+            if (TAB) stage_words(arena + M.a_tab, M.dtab, (static_cast<uint32_t>(M.Q) * M.S + 1) / 2, tid, NC);
             if (KIND == 1) {
                 if (M.a_band != kNotStaged)
-                    stage_words(arena + M.a_band, M.band, static_cast<uint32_t>(M.Q + (M.Q + 31) / 32), tid, NT);
-                if (M.a_pool != kNotStaged) stage_words(arena + M.a_pool, M.pool, M.pool_n, tid, NT);
+                    stage_words(arena + M.a_band, M.band, static_cast<uint32_t>(M.Q + (M.Q + 31) / 32), tid, NC);
+                if (M.a_pool != kNotStaged) stage_words(arena + M.a_pool, M.pool, M.pool_n, tid, NC);
             }
             smi.surv = M.a_surv != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_surv) : nullptr;
             smi.memo = M.a_memo != kNotStaged ? reinterpret_cast<const uint16_t *>(arena + M.a_memo) : M.memo;
@@ -159,42 +287,28 @@ __global__ void __launch_bounds__(512, 1) scan_units(const BatchArgs *__restrict
             smi.coop = M.a_coop != kNotStaged
                            ? reinterpret_cast<uint32_t *>(arena + M.a_coop) + wid * 2 * M.Wq : sm.coop;
             cur_mach = d.mach;
-        }
-        uint8_t *tsm = text_sm + buf * A.sa.text_buf;
-        if (!mbar_wait_bounded(&misc->bar[buf], d.parity)) misc->abort = 1;
-        if (d.sh) realign_tile(tsm, d.sh, d.len, tid, NT);   // ends with a barrier
-        else __syncthreads();
-        if (misc->abort) break;
-        if (SB == 2) {   // 2-bit symbols: pack the tile once for every gram read
-            pack_tile(tsm, sm.pk, d.len, min(d.b + A.sa.tile, d.n) - d.b,
-                      static_cast<uint32_t>(M.S), bad_symbol, tid, NT);
-            __syncthreads();
+            if (!meet_all()) {
+                if (lane == 0) atomicOr(&A.sa.status[1], ERR_TIMEOUT);
+                aborted = true;
+                break;
+            }
         }
         const MView mv = mview_of(M);
-        const TileView tv{tsm, d.text, d.b, d.len, d.n, d.job, d.orig};
+        const TileView tv{text_sm + buf * A.sa.text_buf, d.text, d.b, d.len, d.n, d.job, d.orig};
         OView ovm = ov;
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
+        smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
         process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
-                                       static_cast<uint32_t>(M.settle), NT);
-        // the next tile continues this text: queued instances and staged
-        // matches stay; otherwise drain and flush them now (per-text counts
-        // need every staged match of a flush to belong to one text)
-        const bool same_text = desc[buf ^ 1].valid && desc[buf ^ 1].job == d.job;
-        if (!same_text) {
-            drain<KIND, TAB, 4>(ovm, mv, tv, smi, wq_n, sn, lane, pol_keep);
-            stage_flush<4>(sm.stage, sn, ov, d.orig, lane);
-        }
-        // the staged buffer is refilled two tiles on: every warp must be done
-        __syncthreads();
+                                       static_cast<uint32_t>(M.settle), NC);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&misc->empty[buf]);
+        have_prev = true;
+        prev = d;
+        prev_ov = ovm;
     }
+    if (have_prev && !aborted) drain_prev();
     if (bad_symbol) atomicOr(&A.sa.status[1], ERR_SYMBOL);
-    if (tid == 0 && misc->abort) {
-        atomicOr(&A.sa.status[1], ERR_TIMEOUT);
-        // a copy may still be in flight: wait for it (bounded) before exit
-        mbar_wait_bounded(&misc->bar[0], 0);
-        mbar_wait_bounded(&misc->bar[1], 0);
-    }
 }
 
 // ------------------------------------------------------------ DFA carry queue
@@ -238,7 +352,7 @@ static cudaError_t launch_u(const BatchArgs *dev_args, int threads, int grid, ui
     auto k = scan_units<KIND, SB, TAB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, threads, smem, s>>>(dev_args);
+    k<<<grid, threads + 32, smem, s>>>(dev_args);   // + the producer warp
     return cudaGetLastError();
 }
 
@@ -247,7 +361,7 @@ static int occ_u(int threads, uint32_t smem) {
     int nb = 0;
     auto k = scan_units<KIND, SB, TAB>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads + 32, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
