@@ -542,6 +542,9 @@ def measure_serving(P, pf_unused, torch, dev, n_req=100_000, loads=(0.25, 0.5, 0
         return {"offered_req_per_s": load * cap_rps, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                 "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9, "matches_per_s": m / el,
                 "batches": st["batches"], "nomem_splits": st["nomem_splits"],
+                "max_loop_gap_ms": st["max_loop_gap_ms"], "max_loop_gap_at_s": st["max_loop_gap_at_s"],
+                "max_batch_ms": st["max_batch_ms"], "max_admit_ms": st["max_admit_ms"],
+                "max_complete_ms": st["max_complete_ms"],
                 "evictions": st["residency_evictions"] - before["evictions"],
                 "reloads": st["residency_reloads"] - before["reloads"]}
 

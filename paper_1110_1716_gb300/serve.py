@@ -92,6 +92,7 @@ class _Slot:
         self.done = torch.cuda.Event()
         self.reqs: List[Request] = []
         self.busy = False
+        self.t_launch = 0.0
         self.text_bytes = text_bytes
         self.out_rows = out_rows
         self.max_jobs = max_jobs
@@ -112,6 +113,8 @@ class Server:
     def __init__(self, pf: Pfsm, automata, slots: int = 3, slot_bytes: int = 64 << 20,
                  out_rows: int = 4 << 20, max_jobs: int = 1024):
         import torch
+        if not 1 <= max_jobs <= 65535:   # batch job indices are grouped as 16-bit keys
+            raise ValueError("max_jobs must be in [1, 65535]")
         self.torch = torch
         self.pf = pf
         self.ids = [pf.load(a) for a in automata]
@@ -128,6 +131,11 @@ class Server:
         # latency (s) of every completed request; finished Request objects are
         # not kept, so the interpreter's cycle collector has less to scan
         self.latencies: List[float] = []
+        self.max_loop_gap_s = 0.0
+        self.max_loop_gap_at = 0.0
+        self.max_batch_s = 0.0
+        self.max_admit_s = 0.0
+        self.max_complete_s = 0.0
         self.batches = 0
         self.overflow_reruns = 0
         self.nomem_splits = 0
@@ -208,6 +216,7 @@ class Server:
         slot.reqs = reqs
         slot.jobs = jobs
         slot.busy = True
+        slot.t_launch = time.perf_counter()
         self.batches += 1
         self.bytes_scanned += used
         return True
@@ -235,10 +244,14 @@ class Server:
                     slot.out_host[:total].copy_(slot.out_dev[:total], non_blocking=True)
                 slot.stream.synchronize()
                 m = slot.out_host[:total].numpy().view(np.uint32)
-            order = np.argsort(m[:, 0], kind="stable")
+            # group the rows by request: job indices fit 16 bits (a batch holds
+            # at most max_jobs <= 65535 requests), for which numpy's stable
+            # sort is a radix sort, linear in the number of matches
+            order = np.argsort(m[:, 0].astype(np.uint16), kind="stable")
             m = m[order]
             bounds = np.searchsorted(m[:, 0], np.arange(k + 1))
             now = time.perf_counter()
+            self.max_batch_s = max(self.max_batch_s, now - slot.t_launch)
             for i, r in enumerate(slot.reqs):
                 r.t_done = now
                 r.future.set_result(m[bounds[i]:bounds[i + 1], 1:])
@@ -296,9 +309,16 @@ class Server:
         futs: List[Future] = []
         i, k = 0, len(due)
         self.running = True
+        prev = time.perf_counter()
         try:
             while True:
                 now = time.perf_counter()
+                # the longest time the loop did not run (a stall of the host
+                # thread, as opposed to a batch that took long on the device)
+                if now - prev > self.max_loop_gap_s:
+                    self.max_loop_gap_s = now - prev
+                    self.max_loop_gap_at = now - t0
+                prev = now
                 with self.lock:
                     while i < k and due[i] <= now:
                         r = Request(self.next_rid, int(auts[i]),
@@ -310,11 +330,16 @@ class Server:
                 progressed = False
                 for slot in self.slots:
                     if slot.busy and slot.done.query():
+                        tc = time.perf_counter()
                         self._complete(slot)
+                        self.max_complete_s = max(self.max_complete_s, time.perf_counter() - tc)
                         progressed = True
                 for slot in self.slots:
-                    if not slot.busy and self._admit(slot):
-                        progressed = True
+                    if not slot.busy:
+                        ta = time.perf_counter()
+                        if self._admit(slot):
+                            progressed = True
+                        self.max_admit_s = max(self.max_admit_s, time.perf_counter() - ta)
                 if i >= k and not self.pending and not any(s.busy for s in self.slots):
                     break
                 if not progressed:
@@ -330,6 +355,11 @@ class Server:
     def reset_stats(self):
         """Forget completed requests and counters (between measured runs)."""
         self.latencies = []
+        self.max_loop_gap_s = 0.0   # longest pass of the trace loop
+        self.max_loop_gap_at = 0.0  # its end, in seconds from the trace start
+        self.max_batch_s = 0.0      # longest batch, launch to completion seen
+        self.max_admit_s = 0.0      # longest packing + launch of a batch
+        self.max_complete_s = 0.0   # longest hand-back of a batch's results
         self.batches = 0
         self.overflow_reruns = 0
         self.nomem_splits = 0
@@ -342,6 +372,11 @@ class Server:
         return {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "batches": self.batches,
+                "max_loop_gap_ms": self.max_loop_gap_s * 1e3,
+                "max_loop_gap_at_s": self.max_loop_gap_at,
+                "max_batch_ms": self.max_batch_s * 1e3,
+                "max_admit_ms": self.max_admit_s * 1e3,
+                "max_complete_ms": self.max_complete_s * 1e3,
                 "overflow_reruns": self.overflow_reruns, "nomem_splits": self.nomem_splits, **{
                     "residency_" + k: v for k, v in pfsm_get_stats(self.pf.ctx).items()}}
 
