@@ -79,20 +79,29 @@ typedef struct {
                            NFA (12 for a DFA over fewer than 256 symbols,
                            16 for bytes), lowered when an NFA's records
                            outgrow 16-bit offsets; an explicit k that does
-                           not fit fails with E_INVAL, keeping the old table */
+                           not fit fails with E_INVAL, keeping the old table.
+                           An NFA over at most 4 symbols with k + 5 <= 16
+                           also gets second-level records: for each state
+                           set that k symbols leave without a match (up to
+                           4096 sets, at most 8 MB of device memory), the
+                           outcome of the next 5 symbols */
     int32_t tile;       /* starts owned by one CTA tile (multiple of 4096, at
                            most 49152; 0 = automatic: 16384, smaller for short
                            texts) */
     int32_t halo;       /* text staged past the tile end (multiple of 16) */
-    int32_t threads;    /* threads per CTA: 128, 256 or 512 */
+    int32_t threads;    /* filtering threads per CTA: 128, 256 or 512 (a
+                           scan with 32 starts per thread adds one producer
+                           warp that stages the tiles) */
     int32_t spt;        /* consecutive starts each thread filters per round:
                            8 or 32; 0 = automatic (8 for texts too short to
                            give every SM 16 warps at 32, else 32) */
     int32_t table_smem; /* delta table in shared memory: 1 yes, 0 no, -1 auto */
     int32_t ctas_per_sm;/* persistent CTAs per SM (0 = occupancy maximum) */
     int32_t settle;     /* NFA: steps a surviving instance is advanced in the
-                           filter before it is queued for the exact path
-                           (0 = library default, -1 = queue at once) */
+                           filter before it is queued for the exact path,
+                           counted from k symbols past its start (an instance
+                           carried by a second-level record starts at step
+                           5); 0 = library default (16), -1 = queue at once */
     int32_t partition;  /* instances alive past their tile's staged text
                            (Sec. III.D.2): 1 = lazy (continue in place on the
                            global text), 2 = chained (DFA only: hand the
@@ -230,11 +239,14 @@ int pfsm_scan_union_async(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k,
                           const uint8_t *text_dev, uint64_t n, pfsm_bmatch *out_dev,
                           uint64_t cap, uint64_t *status_dev, void *stream);
 
-/* Launch shape of batches on this context: `threads` (128, 256 or 512 per
- * CTA), `ctas_per_sm` (1 to 4) and `tile` (multiple of 4096, at most 32768)
- * of *p are used, other fields are ignored. 0 in a field, or a NULL p,
- * selects the default: 256 threads x 2 CTAs per SM for DFA classes, 512 x 1
- * for NFA classes, tiles of 16384. Per-machine parameters (prefix depth,
+/* Launch shape of batches on this context: `threads` (128, 256 or 512
+ * filtering threads per CTA; the kernels add one producer warp, and NFA
+ * classes keep 512 threads in all, so 512 means 480 filtering threads there),
+ * `ctas_per_sm` (1 to 4) and `tile` (multiple of 4096, at most 32768; rounded
+ * down to whole filter rounds of 32 starts per filtering thread) of *p are
+ * used, other fields are ignored. 0 in a field, or a NULL p, selects the
+ * default: 256 threads x 2 CTAs per SM for DFA classes, 480 x 1 for NFA
+ * classes, tiles of 16384 (15360 for NFA classes). Per-machine parameters (prefix depth,
  * settling) still come from pfsm_set_params. The autotuner sets this.
  * Errors: E_INVAL (a value outside those ranges). */
 int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p);
