@@ -295,6 +295,14 @@ int pfsm_get_stats(pfsm_ctx *ctx, pfsm_stats *out);
  * batches under a residency budget. Errors: E_INVAL, E_NOENT. */
 int pfsm_aut_bytes(pfsm_ctx *ctx, pfsm_aut aut, uint64_t *bytes, int32_t *resident);
 
+/* Test of the timeout path (no counterpart in the paper). While enabled,
+ * single-text scans whose tiles are staged by a producer warp (32 starts per
+ * thread) hand no tile to their filtering warps: every wait for a tile runs
+ * into its bound (2 s), the kernel ends and the scan reports E_TIMEOUT, and
+ * the context stays usable. Nothing faults or hangs; scans of other forms
+ * are unaffected. For tests only. Errors: E_INVAL (NULL ctx). */
+int pfsm_test_hold_tiles(pfsm_ctx *ctx, int32_t enable);
+
 /* Kernel timing: when enabled, every scan records CUDA events around its
  * tile kernel (a batch: around its graph) on the scan's stream;
  * pfsm_kernel_time returns the summed milliseconds and launch count since

@@ -33,7 +33,8 @@ EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nf
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
            "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes",
-           "pfsm_scan_union", "pfsm_scan_union_async", "pfsm_load_nfa_eps")
+           "pfsm_scan_union", "pfsm_scan_union_async", "pfsm_load_nfa_eps",
+           "pfsm_test_hold_tiles")
 
 
 class pfsm_params(ctypes.Structure):
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_set_batch_params": [P, ctypes.POINTER(pfsm_params)],
         "pfsm_get_stats": [P, ctypes.POINTER(pfsm_stats)],
         "pfsm_set_timing": [P, ctypes.c_int],
+        "pfsm_test_hold_tiles": [P, I32],
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
         "pfsm_strerror": [ctypes.c_int],
         "pfsm_scan_dfa_noalloc": [P, I32, I32, I32, I32, P, P, U64, P, U64, P, P],
@@ -345,6 +347,11 @@ def pfsm_aut_bytes(ctx: int, aut: int):
     r = ctypes.c_int32()
     _check(load_library().pfsm_aut_bytes(ctx, aut, ctypes.byref(b), ctypes.byref(r)), "pfsm_aut_bytes")
     return b.value, bool(r.value)
+
+
+def pfsm_test_hold_tiles(ctx: int, enable: bool) -> None:
+    """Test hook for the timeout path (see include/pfsm.h)."""
+    _check(load_library().pfsm_test_hold_tiles(ctx, 1 if enable else 0), "pfsm_test_hold_tiles")
 
 
 def pfsm_set_timing(ctx: int, enable: bool) -> None:

@@ -913,6 +913,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     pl.a.out = out;
     pl.a.cap = cap;
     pl.a.status = status;
+    pl.a.hold_tiles = ctx->hold_tiles ? 1u : 0u;
     pl.a.carry = slot->carry;
     pl.a.carry_n = slot->carry_n;
     // lazy partitioning: no carry queue, instances continue in place
@@ -1311,6 +1312,12 @@ int pfsm_set_timing(pfsm_ctx *ctx, int enable) {
     ctx->timing = enable != 0;
     ctx->time_ms = 0.0;
     ctx->time_launches = 0;
+    return PFSM_OK;
+}
+
+int pfsm_test_hold_tiles(pfsm_ctx *ctx, int32_t enable) {
+    if (!ctx) return PFSM_E_INVAL;
+    ctx->hold_tiles = enable != 0;
     return PFSM_OK;
 }
 

@@ -124,6 +124,7 @@ struct pfsm_ctx {
     std::map<cudaStream_t, pfsm::UseRing> use_rings;
     std::mutex mu;
     bool timing = false;
+    bool hold_tiles = false;   // test hook: scans time out (see pfsm_test_hold_tiles)
     double time_ms = 0.0;
     uint64_t time_launches = 0;
     // batch executors, one per stream (batch.cu), and their launch shape

@@ -143,6 +143,8 @@ struct ScanArgs {
     uint32_t sm_pack;       // the staged tiles as 2-bit symbols (alphabets of <= 4 symbols)
     uint32_t pk_words;      // words of one packed tile
     uint32_t nbuf;          // staged tile buffers, 2 or 3 (layout_smem turns 0 into 2)
+    uint32_t hold_tiles;    // test of the timeout path: the producer warp hands no
+                            // tile over, so the filtering warps' waits run out
     uint32_t sm_band, sm_pool, sm_surv, sm_list;
     uint32_t stage_n;       // staged matches per warp before a flush
     int32_t memo_smem;      // prefix table staged to smem (else read from global)

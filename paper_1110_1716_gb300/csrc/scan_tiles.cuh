@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
                     // the realigned bytes are rewritten by a later bulk copy
                     if (a.shift) fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&misc->ready[buf]);
+                    if (lane == 0 && !a.hold_tiles) mbar_arrive(&misc->ready[buf]);
                     ++prepped;
                     progress = true;
                 }

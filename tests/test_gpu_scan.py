@@ -482,3 +482,26 @@ def test_second_level_records_beyond_the_table_cap(pf):
         P.pfsm_set_params(pf.ctx, a, {"prefix_k": k})
         t = W.text_uniform(50_000, 4, 950 + k)
         assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(m, t)), k
+
+
+# ---------------------------------------------------------------- bounded waits
+def test_bounded_waits_end_a_held_scan_with_timeout(pf):
+    """Every wait of the scan kernel is bounded: with the producer warp
+    handing no tile over (a test hook; nothing faults and nothing spins
+    without a limit), the filtering warps' waits run out, the scan reports
+    E_TIMEOUT within seconds, and the next scan on the same context is
+    exact."""
+    import time
+    nfa, t, _, _ = W.workload_motif_nfa(2, n=8 << 20, n_motifs=32)
+    a = pf.load(nfa)
+    P.pfsm_set_params(pf.ctx, a, {"spt": 32})   # tiles staged by a producer warp
+    P.pfsm_test_hold_tiles(pf.ctx, True)
+    try:
+        t0 = time.time()
+        with pytest.raises(P.PfsmError) as err:
+            gpu_matches(pf, a, t)
+        assert err.value.status == P.PFSM_E_TIMEOUT
+        assert time.time() - t0 < 30
+    finally:
+        P.pfsm_test_hold_tiles(pf.ctx, False)
+    assert np.array_equal(gpu_matches(pf, a, t), oracle.scan(nfa, t))
