@@ -127,12 +127,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // Shared-memory control words of a CTA.
-constexpr int kTileBufs = 3;   // staged tiles in flight in the single-text kernel
+constexpr int kTileBufs = 3;   // most staged tiles a CTA holds
 struct Misc {
-    uint64_t bar[2];              // batch kernel: copy of buffer 0 / 1 landed
-    uint64_t full[kTileBufs];     // single-text kernel: copy landed
+    uint64_t bar[2];              // batch kernel: bar[0] = the filtering warps' meetings
+    uint64_t full[kTileBufs];     // the buffer's copy landed
     uint64_t ready[kTileBufs];    //   realigned and packed by the producer warp
-    uint64_t empty[kTileBufs];    //   every consumer warp is done with it
+    uint64_t empty[kTileBufs];    //   every filtering warp is done with it
     uint32_t q_count;
     uint32_t q_head;
     uint32_t abort;
