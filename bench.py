@@ -87,6 +87,25 @@ def run_probe(args):
                           "params": P.pfsm_get_params(pf.ctx, aid)}))
 
 
+def run_probe_batch(args):
+    """Two batch scans of the mixed many-texts workload with
+    --probe-batch texts (the command batch profiles are taken on)."""
+    import torch
+    import paper_1110_1716_gb300 as P
+    w = W.batch_workload(seed=args.seed, n_texts=args.probe_batch)
+    with P.Pfsm(0) as pf:
+        ids = np.array([pf.load(a) for a in w.automata], dtype=np.int32)
+        data = pf.to_device(w.data)
+        table = P.job_table(ids[w.job_aut], data.data_ptr() + w.offsets[:-1], np.diff(w.offsets))
+        st, counts, total = P.pfsm_scan_batch(pf.ctx, table, None, 0)
+        out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=data.device)
+        for _ in range(2):
+            st, counts, total = P.pfsm_scan_batch(pf.ctx, table, out, out.shape[0])
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": "batch", "texts": args.probe_batch, "bytes": int(w.offsets[-1]),
+                          "matches": int(total)}))
+
+
 def kernel_traffic(name, text_bytes, params=None):
     """DRAM bytes per launch of the scan kernel on `name`, scaled from the
     recorded ncu capture by text length (the kernel reads its text once), or
@@ -648,6 +667,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--bytes", type=int, default=0, help="text length for --probe")
+    ap.add_argument("--probe-batch", type=int, default=0,
+                    help="two batch scans of this many texts (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -665,6 +686,9 @@ def main():
     __graft_entry__.build()
     if args.probe:
         run_probe(args)
+        return
+    if args.probe_batch:
+        run_probe_batch(args)
         return
     if world > 1:
         import torch
