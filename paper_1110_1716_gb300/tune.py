@@ -51,13 +51,20 @@ def candidates(kind: str, S: int, default_k: int) -> List[dict]:
     sbits = max(1, int(np.ceil(np.log2(max(2, S)))))
     kmax = min(8, 16 // sbits)
     ks = sorted({k for k in (default_k - 1, default_k, default_k + 1, kmax) if 1 <= k <= kmax})
+    # NFA settling cap: 16 by default; 8 measured faster on a motif NFA once
+    # its starts reach settling 5 symbols past the prefix table
+    settles = (8, 16) if kind == "nfa" else (0,)
     out = []
     for k in ks:
         for threads in (256, 512):
             for tile in (8192, 16384, 32768):
                 for cps in (0, 1):
-                    out.append({"prefix_k": k, "threads": threads, "tile": tile,
-                                "halo": 2048, "ctas_per_sm": cps})
+                    for settle in settles:
+                        p = {"prefix_k": k, "threads": threads, "tile": tile, "halo": 2048,
+                             "ctas_per_sm": cps}
+                        if settle:
+                            p["settle"] = settle
+                        out.append(p)
     return out
 
 

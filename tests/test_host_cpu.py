@@ -52,6 +52,8 @@ def test_tuner_candidates_and_cache(tmp_path, monkeypatch):
     c = tune.candidates("nfa", 4, 6)
     assert c and all(1 <= x["prefix_k"] <= 8 for x in c)
     assert all(x["threads"] in (256, 512) for x in c)
+    assert {x.get("settle") for x in c} == {8, 16}            # NFA: settling cap tried
+    assert all("settle" not in x for x in tune.candidates("dfa", 4, 6))
     tune._store("nfa/Q10/S4/gpu", {"prefix_k": 6}, 1.5)
     assert json.load(open(tmp_path / "cache.json"))["nfa/Q10/S4/gpu"]["params"] == {"prefix_k": 6}
 
