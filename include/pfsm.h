@@ -45,7 +45,10 @@ extern "C" {
 #define PFSM_E_NOMEM 2    /* device memory or the residency budget exhausted */
 #define PFSM_E_OVERFLOW 3 /* more matches than the output capacity */
 #define PFSM_E_NOENT 4    /* unknown or unloaded automaton id */
-#define PFSM_E_TIMEOUT 5  /* a bounded device wait expired */
+#define PFSM_E_TIMEOUT 5  /* a bounded device wait expired: a warp waited 2 s
+                             for a tile, a buffer or the other warps of its
+                             CTA while none of them was running continuation
+                             work (which always ends) */
 #define PFSM_E_CUDA 6     /* a CUDA runtime call failed */
 
 typedef struct pfsm_ctx pfsm_ctx;
@@ -172,10 +175,16 @@ int pfsm_load_nfa_eps(pfsm_ctx *ctx, const uint32_t *delta_bits, const uint32_t 
                       pfsm_aut *out_id);
 
 /* Drop the device copy of an automaton (its host copy stays); the next scan
- * that names it reloads it. Errors: E_NOENT. */
+ * that names it reloads it. This is the device form of the paper's remedy for
+ * insomnia (Sec. I-II: a machine too large for fast memory keeps only its hot
+ * part there): cold automata leave device memory and come back on use.
+ * Waits for the scans already enqueued that read the copy. Errors: E_NOENT. */
 int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut);
 
-/* Forget an automaton entirely; its id becomes invalid. Errors: E_NOENT. */
+/* Forget an automaton entirely; its id becomes invalid (removing one regular
+ * expression from a resident set, Sec. III.A and IV: the other automata keep
+ * running). Scans already enqueued that read it keep their copy, which is
+ * freed when the last of them completes. Errors: E_NOENT. */
 int pfsm_unload(pfsm_ctx *ctx, pfsm_aut aut);
 
 /* Launch parameters of an automaton (the autotuner sets them). `p` may be
@@ -199,7 +208,8 @@ int pfsm_get_params(pfsm_ctx *ctx, pfsm_aut aut, pfsm_params *out);
 int pfsm_scan(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text_dev, uint64_t n,
               pfsm_match *out_dev, uint64_t cap, uint64_t *n_matches, void *stream);
 
-/* Asynchronous form of pfsm_scan: enqueues the scan on `stream` and returns.
+/* Asynchronous form of pfsm_scan (Sec. III.B, the same match set M): enqueues
+ * the scan on `stream` and returns.
  * On completion, status_dev (device, 2 x uint64) holds { |M|, error bits }
  * where error bit 0 = a symbol >= S, bit 1 = a device wait timed out.
  * Capturable in a CUDA graph once the automaton is resident (a scan
@@ -251,8 +261,8 @@ int pfsm_scan_union_async(pfsm_ctx *ctx, const pfsm_aut *auts, int32_t k,
  * Errors: E_INVAL (a value outside those ranges). */
 int pfsm_set_batch_params(pfsm_ctx *ctx, const pfsm_params *p);
 
-/* Asynchronous form of pfsm_scan_batch: enqueues the batch on `stream` and
- * returns. status_dev (device, k + 2 uint64) receives, when the stream
+/* Asynchronous form of pfsm_scan_batch (Sec. III.B per text, Sec. III.D for
+ * the batch): enqueues the batch on `stream` and returns. status_dev (device, k + 2 uint64) receives, when the stream
  * reaches it: [0] total matches, [1] error bits (as pfsm_scan_async),
  * [2 + i] matches of job i. The job array may be reused once the call
  * returns. Errors detected on the host are returned directly. */
@@ -264,7 +274,11 @@ int pfsm_scan_batch_async(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_b
  * handed buffers, a process whose device memory belongs to another
  * allocator, a loop that must never stall on cudaMalloc/cudaFree). It needs
  * no context and allocates nothing; its working memory is one 4 MiB array
- * of device memory that every GPU loading the library holds until exit.
+ * of device memory that every GPU loading the library holds until exit. The
+ * driver reserves the array when it loads the library's module: with lazy
+ * module loading (the CUDA default) that happens during the first call on a
+ * device, so make that call before another allocator takes the device's
+ * memory (CUDA_MODULE_LOADING=EAGER reserves it when the library loads).
  *   delta_dev     device, int16 [Q][S] row-major (entries in [0, Q))
  *   is_final_dev  device, uint8 [Q]
  *   q0, dead      as for pfsm_load_dfa (dead = -1: none)
@@ -275,9 +289,10 @@ int pfsm_scan_batch_async(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_b
  *                 malformed table; |M| > cap means the output was truncated)
  * Limits: Q * S <= 524288 (the encoded table must fit 1 MiB of the array);
  * larger tables fail with E_INVAL. The result is the same match set as
- * pfsm_scan. Asynchronous on `stream`. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture. Calls share the array: two calls whose
+ * pfsm_scan. Asynchronous on `stream`. Every call looks up the array's
+ * device address (cudaGetSymbolAddress, which allocates nothing once the
+ * module is loaded), so make the first call on a device before any stream
+ * capture. Calls share the array: two calls whose
  * work overlaps on the GPU race, so issue them on one stream or wait in
  * between. Errors detected on the host are returned directly. */
 int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_t S, int32_t q0,

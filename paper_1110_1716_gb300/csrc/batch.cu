@@ -219,7 +219,8 @@ static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine 
     if (!m.surv.empty()) d.a_surv = take(static_cast<uint32_t>(m.surv.size() * 4));
     if (!deep && d.memo_n > 0) d.a_memo = take(((d.memo_n + 1) / 2) * 4);
     if (m.kind == 0) {
-        d.a_tab = take(((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4);
+        // table_smem 0: the DFA table stays in global memory (L2)
+        if (m.params.table_smem != 0) d.a_tab = take(((static_cast<uint32_t>(m.Q) * m.S + 1) / 2) * 4);
     } else {
         if (!m.band.empty()) d.a_band = take(static_cast<uint32_t>(m.band.size() * 4));
         if (!m.pool.empty()) d.a_pool = take(static_cast<uint32_t>(m.pool.size() * 4));

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         misc->q_count = 0;
         misc->q_head = 0;
         misc->abort = 0;
+        misc->busy = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
                 ++issued;
                 progress = true;
             }
-            if (progress) {
+            if (progress || *reinterpret_cast<volatile uint32_t *>(&misc->busy) != 0) {
                 idle_since = global_ns();
             } else {
                 // give up after 2 s without progress (one decision per warp)
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     auto meet_all = [&]() -> bool {
         __syncwarp();
         if (lane == 0) mbar_arrive(&misc->bar[0]);
-        const bool okm = __all_sync(0xffffffffu, mbar_wait_bounded(&misc->bar[0], meet & 1));
+        const bool okm = __all_sync(0xffffffffu, mbar_wait_live(&misc->bar[0], meet & 1, &misc->busy));
         ++meet;
         return okm;
     };
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     };
     for (uint32_t k = 0;; ++k) {
         const int buf = static_cast<int>(k % nb);
-        const bool go = mbar_wait_bounded(&misc->ready[buf], (k / nb) & 1) &&
+        const bool go = mbar_wait_live(&misc->ready[buf], (k / nb) & 1, &misc->busy) &&
                         !*reinterpret_cast<volatile uint32_t *>(&misc->abort);
         if (!__all_sync(0xffffffffu, go)) {
             if (lane == 0) atomicOr(&A.sa.status[1], ERR_TIMEOUT);

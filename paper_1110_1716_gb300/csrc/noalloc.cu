@@ -11,7 +11,11 @@
 // calls no allocating routine.
 //
 // The array is a fixed kNoAllocBytes per device, held by every device that
-// loads this library until the process exits. All calls on a device share
+// loads this library until the process exits. The driver reserves it when it
+// loads this file's module: with lazy module loading (the CUDA default) that
+// is the first call on a device, so such callers make that first call before
+// another allocator takes the device's memory (CUDA_MODULE_LOADING=EAGER
+// reserves it when the library is loaded). All calls on a device share
 // it: calls whose work overlaps on the GPU (for example on two streams)
 // race on it, so a caller issues them on one stream or waits between them.
 #include <cuda_runtime.h>
@@ -35,35 +39,36 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
 struct NoAllocDevice {
-    bool ready = false;
     uint8_t *scratch = nullptr;   // device address of g_noalloc_scratch
     int nsm = 0;
 };
 std::mutex g_noalloc_mu;
-NoAllocDevice g_noalloc_dev[128];
+int g_noalloc_nsm[128];   // SM count per device index (0: not read yet)
 
-// Resolve the array's device address once per device (the name is only a
-// host-side stand-in in host code).
-int noalloc_setup(int dev, NoAllocDevice **out) {
+// The array's device address for the current device. The name is only a
+// host-side stand-in in host code, so the address is looked up on every
+// call: after cudaDeviceReset, or when the primary context is released and
+// created again, the module is loaded anew and the array may sit elsewhere.
+// Once the module is loaded the lookup allocates nothing.
+int noalloc_setup(int dev, NoAllocDevice *out) {
     if (dev < 0 || dev >= 128) return PFSM_E_INVAL;
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    NoAllocDevice &d = g_noalloc_dev[dev];
-    if (!d.ready) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return PFSM_E_CUDA;
-        }
-        int nsm = 0;
-        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return PFSM_E_CUDA;
-        }
-        d.scratch = static_cast<uint8_t *>(p);
-        d.nsm = nsm;
-        d.ready = true;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PFSM_E_CUDA;
     }
-    *out = &d;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (g_noalloc_nsm[dev] == 0) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm <= 0) {
+            cudaGetLastError();
+            return PFSM_E_CUDA;
+        }
+        g_noalloc_nsm[dev] = nsm;
+    }
+    out->scratch = static_cast<uint8_t *>(p);
+    out->nsm = g_noalloc_nsm[dev];
     return PFSM_OK;
 }
 }  // namespace
@@ -116,9 +121,10 @@ extern "C" int pfsm_scan_dfa_noalloc(const int16_t *delta_dev, int32_t Q, int32_
     if (n >= (1ull << 32) || (n > 0 && !text_dev) || (cap > 0 && !out_dev)) return PFSM_E_INVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PFSM_E_CUDA;
-    NoAllocDevice *d = nullptr;
-    int st = noalloc_setup(dev, &d);
+    NoAllocDevice dd;
+    int st = noalloc_setup(dev, &dd);
     if (st) return st;
+    const NoAllocDevice *d = &dd;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(d->scratch);
     uint32_t *carry_n = reinterpret_cast<uint32_t *>(d->scratch + 16);

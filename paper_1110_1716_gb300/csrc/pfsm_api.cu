@@ -402,6 +402,7 @@ static bool survival_bits(const Machine &m, int mm, std::vector<uint32_t> &bits)
 // Two filters: a shallow one kept in shared memory (<= 32 KB) and a deep
 // one read from global memory / L2 (<= 8 MB) for the starts that pass the
 // first.
+
 void build_survival(Machine &m) {
     m.surv.clear();
     m.surv2.clear();
@@ -788,6 +789,10 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         while (threads > 128 && n < 2ull * ctx->nsm * static_cast<uint64_t>(spt) * threads)
             threads /= 2;
     }
+    // the NFA kernel with a producer warp runs 15 filtering warps: 16 warps
+    // in all put four on each of an SM's sub-partitions, whose registers then
+    // allow 128 per thread (a seventeenth warp would cut that to 96 and spill)
+    if (m.kind == 1 && spt == FILTER_SPT && threads == 512) threads = 480;
     uint32_t tile = static_cast<uint32_t>(p.tile);
     if (tile == 0 && spt == 8) {
         tile = static_cast<uint32_t>(spt) * threads;   // one filter round: the most CTAs
@@ -795,7 +800,9 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         // at least two tiles per SM when the text allows it
         const uint64_t want = n / (2ull * ctx->nsm);
         tile = static_cast<uint32_t>(std::min<uint64_t>(16384, std::max<uint64_t>(4096, (want + 4095) & ~4095ull)));
-        tile = std::max<uint32_t>(tile, static_cast<uint32_t>(spt) * threads);
+        // whole filter rounds
+        const uint32_t round = static_cast<uint32_t>(spt) * threads;
+        tile = std::max<uint32_t>(round, tile / round * round);
     }
     a.tile = tile;
     a.halo = p.halo;
@@ -853,6 +860,10 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
     a.settle_steps = m.params.settle > 0 ? m.params.settle : 0;
     need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
+    // 2-grams of bytes: the shallow bitmap as one byte per 2-gram (64 KB),
+    // so that the gram index is the load offset
+    const bool byte_table = m.sbits == 8 && m.sm_m == 2 && !m.surv.empty();
+    if (byte_table) need.surv_bytes = 1u << 16;
     // warp-wide bitsets of sets too large for a lane: shared memory keeps
     // their atomics on chip
     need.coop_bytes = m.kind == 1 ? static_cast<uint32_t>((threads / 32) * 2 * m.dm.Wq * 4) : 0u;
@@ -864,6 +875,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         // shrink, cheapest loss first: match staging, then table copies
         // (largest first)
         if (a.stage_n > 32) a.stage_n = 32;
+        else if (need.surv_bytes > (1u << 15) && byte_table) need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);
         else if (need.coop_bytes) need.coop_bytes = 0;   // rare: sets of more than 8 states
         else if (need.pool_bytes) need.pool_bytes = 0;
         else if (need.memo_bytes) need.memo_bytes = 0;
@@ -872,6 +884,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         else break;
     }
     if (!fit) return PFSM_E_INVAL;
+    a.surv_bytes = byte_table && need.surv_bytes == (1u << 16);
     int occ = max_ctas_per_sm(m.kind, m.sbits, threads, smem, a.tab_smem != 0, spt);
     if (occ <= 0) return PFSM_E_INVAL;
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);

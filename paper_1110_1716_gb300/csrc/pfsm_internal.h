@@ -93,6 +93,7 @@ constexpr int WARP_LIST = 1024;   // surviving starts a warp lists per round (32
 constexpr int WARP_LIST_BYTES = 2 * WARP_LIST + 4 * SETTLE_PAIRS + WARP_LIST / 8 + 16;
 constexpr int FILTER_SPT = 32;    // starts per thread per filter round
 constexpr int WARP_QUEUE = 256;   // per-warp queue of instances for the exact path
+constexpr int DEEP_GROUP = 1;     // chunks of 32 list entries whose deep-bitmap loads are in flight together
 
 struct ScanArgs {
     // text
@@ -127,6 +128,8 @@ struct ScanArgs {
     const uint32_t *surv2;  // deep survival bitmap (global memory), or null
     int32_t surv2_m;
     int32_t Wq;             // NFA: 32-bit words of a state bitset
+    int32_t surv_bytes;     // the shallow bitmap is staged as one byte per m-gram
+                            // (2-grams of bytes: the gram index is the byte offset)
     int32_t tab_smem;       // DFA table staged to smem
     uint32_t *coop_g;       // NFA: global scratch for warp-wide state bitsets
     // output

@@ -126,6 +126,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Wait on a barrier that other warps of the CTA complete: gives up after
+// ~2 s during which no warp of the CTA was inside a drain (*busy == 0
+// throughout). A drain ends by itself (every instance reaches the end of
+// its text or dies), so the wait stays bounded.
+__device__ __forceinline__ bool mbar_wait_live(uint64_t *bar, uint32_t parity,
+                                               const uint32_t *busy) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        const uint64_t now = global_ns();
+        if (*reinterpret_cast<const volatile uint32_t *>(busy) != 0) t0 = now;
+        else if (now - t0 > 2000000000ull) return false;
+    }
+    return true;
+}
+
 // Shared-memory control words of a CTA.
 constexpr int kTileBufs = 3;   // most staged tiles a CTA holds
 struct Misc {
@@ -136,7 +152,9 @@ struct Misc {
     uint32_t q_count;
     uint32_t q_head;
     uint32_t abort;
-    uint32_t pad;
+    uint32_t busy;                // warps inside a drain (continuation work that
+                                  // can run long but always ends): waits do not
+                                  // time out while it is nonzero
 };
 
 // ------------------------------------------------------------ symbol checks
@@ -211,30 +229,61 @@ __device__ __forceinline__ uint32_t pk_gram(const uint32_t *pk, uint32_t p) {
     return __funnelshift_r(pk[p >> 4], pk[(p >> 4) + 1], (p & 15u) * 2u);
 }
 
+// Byte-wise "x >= S" over a 32-bit word (S <= 128), high bit of each byte set
+// on a hit: (x & 0x7F) + 0x80 - S carries into bit 7 exactly when the low
+// seven bits reach S, and the OR with x catches bytes of 128 and above.
+__device__ __forceinline__ uint32_t bytes_ge32(uint32_t x, uint32_t S) {
+    return (((x & 0x7F7F7F7Fu) + (0x80u - S) * 0x01010101u) | x) & 0x80808080u;
+}
+
+// 2-bit packing of 16 bytes (each 0..3, in w0..w3) into 32 bits, byte m at
+// bits 2m. Multiplying a word of four 2-bit values b0..b3 (one per byte) by
+// 2^24 + 2^18 + 2^12 + 2^6 puts b0 + 4 b1 + 16 b2 + 64 b3 in its top byte:
+// the product of byte i with the term 2^(24 - 6i) lands at bit 24 + 2i, every
+// other partial product lands at bit 32 or above (dropped) or below bit 24,
+// and those lower ones sum to less than 2^24, so nothing carries into the
+// top byte. Three byte permutations gather the four top bytes.
+__device__ __forceinline__ uint32_t pack16(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+    constexpr uint32_t M = 0x01041040u;
+    constexpr uint32_t K = 0x03030303u;
+    const uint32_t lo = __byte_perm((w0 & K) * M, (w1 & K) * M, 0x0073);
+    const uint32_t hi = __byte_perm((w2 & K) * M, (w3 & K) * M, 0x0073);
+    return __byte_perm(lo, hi, 0x5410);
+}
+
 // Packs the staged tile (len bytes at tsm) to 2-bit symbols, 16 per word,
 // and checks the bytes of the tile's own starts [0, own) against the
-// alphabet. Every thread of the CTA calls it after the tile's barrier; the
-// caller synchronises before the packed words are read.
+// alphabet (S <= 4 here). The threads tid = 0, nt, 2 nt, ... of the caller
+// share the work; the caller synchronises before the packed words are read.
 __device__ __forceinline__ void pack_tile(const uint8_t *tsm, uint32_t *pk, uint32_t len,
                                           uint32_t own, uint32_t S, bool &bad_symbol, int tid,
                                           int nt) {
     const uint32_t nwords = (len + 15) / 16 + 1;
+    const uint32_t full = own / 16;   // blocks whose 16 bytes are all own starts
     const uint4 *t4 = reinterpret_cast<const uint4 *>(tsm);
+    uint32_t bad = 0;
+#pragma unroll 4
     for (uint32_t w = tid; w < nwords; w += nt) {
         const uint4 v = t4[w];
-        const uint64_t lo = v.x | (static_cast<uint64_t>(v.y) << 32);
-        const uint64_t hi = v.z | (static_cast<uint64_t>(v.w) << 32);
-        pk[w] = pack2(lo) | (pack2(hi) << 16);
-        const uint32_t b0 = 16 * w;
-        if (b0 < own) {
-            const uint32_t nb = min(16u, own - b0);
-            uint64_t bl = bytes_ge(lo, S), bh = bytes_ge(hi, S);
-            if (nb < 8) bl &= (1ull << (8 * nb)) - 1;
-            if (nb <= 8) bh = 0;
-            else if (nb < 16) bh &= (1ull << (8 * (nb - 8))) - 1;
-            if (bl | bh) bad_symbol = true;
+        pk[w] = pack16(v.x, v.y, v.z, v.w);
+        if (w < full) {
+            bad |= bytes_ge32(v.x, S) | bytes_ge32(v.y, S) | bytes_ge32(v.z, S) |
+                   bytes_ge32(v.w, S);
+        } else if (16 * w < own) {
+            // the block holding the last own start: bytes [16 w, own) only
+            const uint32_t nb = own - 16 * w;   // 1 .. 15
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int valid = static_cast<int>(nb) - 4 * k;
+                if (valid > 0) {
+                    const uint32_t m = valid >= 4 ? 0xFFFFFFFFu : ((1u << (8 * valid)) - 1);
+                    bad |= bytes_ge32(x[k], S) & m;
+                }
+            }
         }
     }
+    if (bad) bad_symbol = true;
 }
 
 // Prefix-table index of the start at offset `off` of the staged tile (k
@@ -296,6 +345,7 @@ struct Smem {
     const uint32_t *band;             // NFA band image (shared copy, global, or null)
     const uint32_t *pool;             // NFA prefix records (shared copy or global)
     const uint32_t *surv;             // survival bitmap (shared copy) or null
+    const uint8_t *survb;             // the same as one byte per m-gram, or null
     uint16_t *list;                   // this warp's list of surviving starts
     uint32_t *pairs;                  // this warp's settling pool (SETTLE_PAIRS)
     uint32_t *pcount;                 // its fill count
@@ -866,11 +916,14 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
                                       const Smem &sm, uint32_t &wq_n, uint32_t &sn, int lane,
                                       uint64_t pol_keep) {
     if (wq_n == 0) return;
+    // the CTA's waits do not time out while this drain runs
+    if (lane == 0) atomicAdd(&sm.misc->busy, 1u);
     if (KIND == 0)
         drain_dfa<TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     else
         drain_nfa<OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     __syncwarp();
+    if (lane == 0) atomicSub(&sm.misc->busy, 1u);
     wq_n = 0;
 }
 
@@ -897,105 +950,166 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
     const uint32_t m2bits = m2 * static_cast<uint32_t>(mv.sbits);
     const uint32_t m2mask = m2bits >= 32 ? 0xFFFFFFFFu : ((1u << m2bits) - 1);
     for (uint32_t r0 = b; r0 < own_end; r0 += round) {
-        // 1. this thread's SPT consecutive starts: symbol check and the
-        //    shared-memory survival bitmap, one 16-byte window per 8 starts
-        const uint32_t i0 = r0 + SPT * tid;
+        // 1. this thread's SPT starts, in SPT / 8 windows of 8 consecutive
+        //    starts: window g of lane l of warp w begins at
+        //    r0 + 32 SPT w + 256 g + 8 l, so the lanes of a warp read
+        //    consecutive bytes of the tile (no shared-memory bank
+        //    conflicts). Symbol check and the shared-memory survival bitmap,
+        //    one 16-byte window per 8 starts; bit 8 g + r of `live` is start
+        //    r of window g.
+        const uint32_t wbase = r0 + static_cast<uint32_t>(tid >> 5) * (32u * SPT) + 8u * lane;
         uint32_t live = 0;
-        if (i0 < own_end) {
-            const uint32_t nown = min(static_cast<uint32_t>(SPT), own_end - i0);
-            live = nown >= 32 ? 0xFFFFFFFFu : ((1u << nown) - 1);
 #pragma unroll
-            for (int g = 0; g < SPT / 8; ++g) {
-                if (static_cast<uint32_t>(8 * g) < nown) {
-                    // 2-bit kernels read the packed tile (symbols checked
-                    // when it was packed); others the bytes of the window
-                    uint64_t lo = 0, hi = 0;
-                    if (SB != 2) {
-                        const uint8_t *tp = tv.sm + (i0 - b) + 8 * g;
-                        const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
-                        const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
-                        lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
-                        hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
-                    }
-                    const uint32_t gown = min(8u, nown - 8 * g);
-                    if (SB != 2 && mv.S < 256) {
-                        uint64_t badm = bytes_ge(lo, mv.S);
-                        if (gown < 8) badm &= (1ull << (8 * gown)) - 1;
-                        if (badm) bad_symbol = true;
-                    }
-                    if (sm.surv) {
-                        const uint32_t p2 = SB == 2 ? pk_gram(sm.pk, i0 - b + 8 * g) : 0u;
-                        if ((SB == 2 || SB == 8) && gown == 8 && i0 + 8 * g + 7 + mm <= n) {
-                            // all eight starts have their m-gram: branch-free
-                            // indices and keep bits
-                            const uint32_t x0 = static_cast<uint32_t>(lo);
-                            const uint32_t x1 = static_cast<uint32_t>(lo >> 32);
-                            const uint32_t x2 = static_cast<uint32_t>(hi);
-                            uint32_t keep = 0;
+        for (int g = 0; g < SPT / 8; ++g) {
+            const uint32_t iw = wbase + 256u * g;   // the window's first start
+            if (iw < own_end) {
+                const uint32_t gown = min(8u, own_end - iw);
+                uint32_t keep = gown >= 8 ? 0xFFu : ((1u << gown) - 1);
+                // 2-bit kernels read the packed tile (symbols checked when it
+                // was packed); others the bytes of the window
+                uint64_t lo = 0, hi = 0;
+                if (SB != 2) {
+                    const uint8_t *tp = tv.sm + (iw - b);
+                    const uint2 l2 = *reinterpret_cast<const uint2 *>(tp);
+                    const uint2 h2 = *reinterpret_cast<const uint2 *>(tp + 8);
+                    lo = l2.x | (static_cast<uint64_t>(l2.y) << 32);
+                    hi = h2.x | (static_cast<uint64_t>(h2.y) << 32);
+                }
+                if (SB != 2 && mv.S < 256) {
+                    uint64_t badm = bytes_ge(lo, mv.S);
+                    if (gown < 8) badm &= (1ull << (8 * gown)) - 1;
+                    if (badm) bad_symbol = true;
+                }
+                if (sm.surv) {
+                    const uint32_t p2 = SB == 2 ? pk_gram(sm.pk, iw - b) : 0u;
+                    if ((SB == 2 || SB == 8) && gown == 8 && iw + 7 + mm <= n) {
+                        // all eight starts have their m-gram: branch-free
+                        // lookups, one bit per start, combined in a tree
+                        const uint32_t x0 = static_cast<uint32_t>(lo);
+                        const uint32_t x1 = static_cast<uint32_t>(lo >> 32);
+                        const uint32_t x2 = static_cast<uint32_t>(hi);
+                        uint32_t bit[8];
+                        if (SB == 8 && sm.survb) {
+                            // bytes r, r + 1 of the window are the 2-gram
+                            // index, and the offset into the byte table
 #pragma unroll
                             for (int r = 0; r < 8; ++r) {
-                                const uint32_t idx =
-                                    SB == 2 ? (p2 >> (2 * r)) & mmask
-                                            : __funnelshift_r(r < 4 ? x0 : x1, r < 4 ? x1 : x2, 8 * (r & 3)) & mmask;
-                                keep |= ((sm.surv[idx >> 5] >> (idx & 31)) & 1u) << r;
+                                const uint32_t idx = r < 3 ? __byte_perm(x0, 0u, 0x4400 | ((r + 1) << 4) | r)
+                                                   : r == 3 ? __byte_perm(x0, x1, 0x0043) & 0xFFFFu
+                                                   : r < 7 ? __byte_perm(x1, 0u, 0x4400 | ((r - 3) << 4) | (r - 4))
+                                                           : __byte_perm(x1, x2, 0x0043) & 0xFFFFu;
+                                bit[r] = sm.survb[idx];
                             }
-                            live &= ~(0xFFu << (8 * g)) | (keep << (8 * g));
                         } else {
 #pragma unroll
                             for (int r = 0; r < 8; ++r) {
-                                const uint32_t i = i0 + 8 * g + r;
-                                if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
-                                    const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
-                                    if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) live &= ~(1u << (8 * g + r));
-                                }
+                                const uint32_t t = SB == 2 ? p2 >> (2 * r)
+                                                           : __funnelshift_r(r < 4 ? x0 : x1, r < 4 ? x1 : x2, 8 * (r & 3));
+                                const uint32_t w = sm.surv[(t & mmask) >> 5];
+                                // rotating w right by t (mod 32) brings the bit to bit 0
+                                bit[r] = __funnelshift_r(w, w, t) & 1u;
+                            }
+                        }
+                        const uint32_t k01 = bit[0] | (bit[1] << 1), k23 = bit[2] | (bit[3] << 1);
+                        const uint32_t k45 = bit[4] | (bit[5] << 1), k67 = bit[6] | (bit[7] << 1);
+                        keep = (k01 | (k23 << 2)) | ((k45 | (k67 << 2)) << 4);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const uint32_t i = iw + r;
+                            if (static_cast<uint32_t>(r) < gown && i + mm <= n) {
+                                const uint32_t idx = memo_index<SB>(lo, hi, p2, r, mm, mv.sbits, mmask);
+                                if (!((sm.surv[idx >> 5] >> (idx & 31)) & 1u)) keep &= ~(1u << r);
                             }
                         }
                     }
                 }
+                live |= keep << (8 * g);
             }
         }
-        // 2. compact the surviving starts into this warp's list
+        // 2. compact the surviving starts into this warp's list: a ballot
+        //    per survivor rank when no lane holds more than two, else a
+        //    prefix sum over the lanes' counts
         uint32_t total = 0;
         if (__any_sync(FULLMASK, live != 0)) {
-            const uint32_t c = __popc(live);
-            uint32_t incl = c;
+            if (!__any_sync(FULLMASK, __popc(live) > 2)) {
+                uint32_t x = live;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
-                if (lane >= d) incl += v;
-            }
-            total = __shfl_sync(FULLMASK, incl, 31);
-            uint32_t p = incl - c;
-            uint32_t x = live;
-            while (x) {
-                const uint32_t r = __ffs(x) - 1;
-                x &= x - 1;
-                sm.list[p++] = static_cast<uint16_t>(i0 + r - b);
+                for (int it = 0; it < 2; ++it) {
+                    const uint32_t m = __ballot_sync(FULLMASK, x != 0);
+                    if (x) {
+                        const uint32_t r = __ffs(x) - 1;
+                        x &= x - 1;
+                        sm.list[total + __popc(m & lanemask_lt())] =
+                            static_cast<uint16_t>(wbase + 256u * (r >> 3) + (r & 7u) - b);
+                    }
+                    total += __popc(m);
+                }
+            } else {
+                const uint32_t c = __popc(live);
+                uint32_t incl = c;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t v = __shfl_up_sync(FULLMASK, incl, d);
+                    if (lane >= d) incl += v;
+                }
+                total = __shfl_sync(FULLMASK, incl, 31);
+                uint32_t p = incl - c;
+                uint32_t x = live;
+                while (x) {
+                    const uint32_t r = __ffs(x) - 1;
+                    x &= x - 1;
+                    sm.list[p++] = static_cast<uint16_t>(wbase + 256u * (r >> 3) + (r & 7u) - b);
+                }
             }
             __syncwarp();
         }
-        // 3a. deep survival bitmap (global memory, L2 resident): independent
-        //     loads per lane, then compact the list in place
+        // 3a. deep survival bitmap (global memory, L2 resident). The list is
+        //     taken DEEP_GROUP chunks of 32 at a time: every lane first issues
+        //     the loads of all its chunks, then the chunks are consumed in
+        //     order and the list compacted in place (an entry is written at
+        //     or below its own position, so chunks not yet consumed are
+        //     intact), so a warp waits for one L2 round trip per group
+        //     instead of one per chunk.
         if (mv.surv2 && total) {
             uint32_t w = 0;
-            for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-                const uint32_t j = j0 + lane;
-                bool keep = false;
-                uint32_t off = 0;
-                if (j < total) {
-                    off = sm.list[j];
-                    keep = true;
-                    if (b + off + m2 <= n) {
-                        const uint32_t i2 = SB == 2 ? pk_gram(sm.pk, off) & m2mask
-                                                    : gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
-                        keep = (ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep) >> (i2 & 31)) & 1u;
+            for (uint32_t g0 = 0; g0 < total; g0 += 32 * DEEP_GROUP) {
+                uint32_t word[DEEP_GROUP], bit[DEEP_GROUP];
+#pragma unroll
+                for (int c = 0; c < DEEP_GROUP; ++c) {
+                    const uint32_t j = g0 + 32 * c + lane;
+                    word[c] = 1u;
+                    bit[c] = 0u;
+                    if (j < total) {
+                        const uint32_t off = sm.list[j];
+                        if (b + off + m2 <= n) {
+                            uint32_t i2;
+                            if (SB == 2) {
+                                i2 = pk_gram(sm.pk, off) & m2mask;
+                            } else if (SB == 8 && m2 <= 4) {
+                                // bytes off .. off + 3 (the staged tile has slack past its end)
+                                const uint8_t *q = tv.sm + off;
+                                i2 = (q[0] | (q[1] << 8) | (q[2] << 16) | (static_cast<uint32_t>(q[3]) << 24)) & m2mask;
+                            } else {
+                                i2 = gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
+                            }
+                            word[c] = ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep);
+                            bit[c] = i2 & 31u;
+                        }
                     }
                 }
-                const uint32_t km = __ballot_sync(FULLMASK, keep);
-                __syncwarp();
-                if (keep) sm.list[w + __popc(km & lanemask_lt())] = static_cast<uint16_t>(off);
-                w += __popc(km);
-                __syncwarp();
+#pragma unroll
+                for (int c = 0; c < DEEP_GROUP; ++c) {
+                    const uint32_t j = g0 + 32 * c + lane;
+                    if (g0 + 32 * c >= total) break;   // warp-uniform
+                    const bool keep = j < total && ((word[c] >> bit[c]) & 1u);
+                    const uint32_t off = j < total ? sm.list[j] : 0u;
+                    const uint32_t km = __ballot_sync(FULLMASK, keep);
+                    __syncwarp();
+                    if (keep) sm.list[w + __popc(km & lanemask_lt())] = static_cast<uint16_t>(off);
+                    w += __popc(km);
+                    __syncwarp();
+                }
             }
             total = w;
         }
@@ -1107,6 +1221,7 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
     s.band = a.band_smem ? reinterpret_cast<const uint32_t *>(base + a.sm_band) : a.band;
     s.pk = reinterpret_cast<uint32_t *>(base + a.sm_pack);
     s.surv = a.surv ? reinterpret_cast<const uint32_t *>(base + a.sm_surv) : nullptr;
+    s.survb = a.surv && a.surv_bytes ? base + a.sm_surv : nullptr;
     uint8_t *wl = base + a.sm_list + wid * WARP_LIST_BYTES;
     s.list = reinterpret_cast<uint16_t *>(wl);
     s.pairs = reinterpret_cast<uint32_t *>(wl + 2 * WARP_LIST);

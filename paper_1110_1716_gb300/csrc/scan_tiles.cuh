@@ -24,7 +24,7 @@ namespace pfsm {
 // SM: every warp filters, two buffers alternate and the CTA synchronises once
 // per tile. Every wait is bounded (2 s) in both forms.
 template <int KIND, int SB, bool TAB_SMEM, int SPT>
-__global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const ScanArgs a) {
+__global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_tiles(const ScanArgs a) {
     constexpr bool PIPE = SPT != 8;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -50,10 +50,19 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
     if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
     if (KIND == 1) stage_nfa(smem, a.sm_band, a.sm_pool, a.band_smem ? a.band : nullptr, a.Q,
                              a.pool_smem ? a.pool : nullptr, a.pool_n, tid, NT);
-    if (a.surv) {
+    if (a.surv && a.surv_bytes) {
+        // one byte (0 or 1) per m-gram: word i of the bitmap gives bytes
+        // 32 i .. 32 i + 31, written as eight words of four bytes
+        uint32_t *d = reinterpret_cast<uint32_t *>(smem + a.sm_surv);
+        for (uint32_t i = tid; i < 8 * a.surv_words; i += NT) {
+            const uint32_t nib = (__ldg(a.surv + (i >> 3)) >> (4 * (i & 7))) & 0xFu;
+            d[i] = (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
+        }
+    } else if (a.surv) {
         uint32_t *d = reinterpret_cast<uint32_t *>(smem + a.sm_surv);
         for (uint32_t i = tid; i < a.surv_words; i += NT) d[i] = __ldg(a.surv + i);
     }
+
     if (tid == 0) {
         for (int i = 0; i < kTileBufs; ++i) {
             mbar_init(&misc->full[i], 1);
@@ -63,6 +72,7 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
         misc->q_count = 0;
         misc->q_head = 0;
         misc->abort = 0;
+        misc->busy = 0;
         fence_mbar_init();
     }
     __syncthreads();   // tables staged, barriers initialised
@@ -132,7 +142,7 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
                     ++issued;
                     progress = true;
                 }
-                if (progress) {
+                if (progress || *reinterpret_cast<volatile uint32_t *>(&misc->busy) != 0) {
                     idle_since = global_ns();
                 } else {
                     // give up after 2 s without progress (one decision per warp)
@@ -159,7 +169,7 @@ __global__ void __launch_bounds__(SPT == 8 ? 512 : 544, 1) scan_tiles(const Scan
             const uint32_t tile = blockIdx.x + k * gridDim.x;
             const uint32_t b = tile * a.tile;
             const uint32_t len = min(a.tile + a.halo, n - b);
-            const bool go = mbar_wait_bounded(&misc->ready[buf], (k / nb) & 1) &&
+            const bool go = mbar_wait_live(&misc->ready[buf], (k / nb) & 1, &misc->busy) &&
                             !*reinterpret_cast<volatile uint32_t *>(&misc->abort);
             if (!__all_sync(0xffffffffu, go)) {
                 if (lane == 0) atomicOr(&a.status[1], ERR_TIMEOUT);
