@@ -2,9 +2,8 @@
 
 Match sets are compared as sorted (start, end, state) arrays, element by
 element (bit-exact: the scan is integer work). Sizes span several tiles and
-a ragged tail; full-size workloads are compared on sampled start windows
-(lazy data partitioning makes "matches starting in [a, b)" a well-defined
-slice the oracle computes on its own) plus properties over every match.
+a ragged tail; the full-size workloads are in test_gpu_fullsize.py (every
+start, with the oracle split into start windows on every host core).
 """
 import numpy as np
 import pytest
@@ -182,48 +181,10 @@ def test_motif_nfa_4mib_full(pf):
     assert len(got) >= len(plants)
 
 
-@pytest.mark.slow
-def test_motif_nfa_64mib_sampled(pf):
-    nfa, t, motifs, plants = W.workload_motif_nfa(0)
-    got = gpu_matches(pf, pf.load(nfa), t)
-    n = len(t)
-    rng = np.random.default_rng(9)
-    wins = [0, n - (256 << 10)] + [int(x) for x in rng.integers(0, n - (256 << 10), size=6)]
-    for lo in wins:
-        hi = lo + (256 << 10)
-        assert np.array_equal(in_window(got, lo, hi), oracle.scan(nfa, t, lo, hi)), lo
-    # every match ends in a final state, inside the text, after its start
-    assert nfa.final[got[:, 2]].all()
-    assert (got[:, 0] <= got[:, 1]).all() and (got[:, 1] < n).all()
-    assert len(got) >= len(plants)
-
-
 def test_byte_trie_16mib_full(pf):
     d, t, sigs, final_of, plants = W.workload_byte_trie(0, n=16 << 20)
     got = gpu_matches(pf, pf.load(d), t)
     assert np.array_equal(got, oracle.scan(d, t))
-
-
-@pytest.mark.slow
-def test_byte_trie_1gib_sampled(pf):
-    d, t, sigs, final_of, plants = W.workload_byte_trie(0)
-    got = gpu_matches(pf, pf.load(d), t)
-    n = len(t)
-    rng = np.random.default_rng(10)
-    for lo in [0, n - (4 << 20)] + [int(x) for x in rng.integers(0, n - (4 << 20), size=6)]:
-        hi = lo + (4 << 20)
-        assert np.array_equal(in_window(got, lo, hi), oracle.scan(d, t, lo, hi)), lo
-    # each reported match spells a signature ending in that final state
-    sig_of = {f: s for s, f in final_of.items()}
-    tb = memoryview(t)
-    for i, j, f in got:
-        assert bytes(tb[i:j + 1]) == sig_of[int(f)]
-    # each intact planted occurrence is reported
-    have = set(map(tuple, got.tolist()))
-    for pos, i in plants:
-        s = sigs[i]
-        if bytes(tb[pos:pos + len(s)]) == s:
-            assert (pos, pos + len(s) - 1, final_of[s]) in have
 
 
 # ---------------------------------------------------------------- protocol and errors

@@ -46,16 +46,37 @@ def test_batch_and_serve_workloads_have_the_stated_shape():
     assert counts[0] > counts[-1]          # Zipf: the first machine is the most popular
 
 
-def test_tuner_candidates_and_cache(tmp_path, monkeypatch):
+def test_tuner_axes_and_cache(tmp_path, monkeypatch):
     from paper_1110_1716_gb300 import tune
-    monkeypatch.setattr(tune, "CACHE_PATH", str(tmp_path / "cache.json"))
-    c = tune.candidates("nfa", 4, 6)
-    assert c and all(1 <= x["prefix_k"] <= 8 for x in c)
-    assert all(x["threads"] in (256, 512) for x in c)
-    assert {x.get("settle") for x in c} == {8, 16}            # NFA: settling cap tried
-    assert all("settle" not in x for x in tune.candidates("dfa", 4, 6))
+    monkeypatch.setattr(tune, "CACHE_PATH", str(tmp_path / "sub" / "cache.json"))
+    ax = tune.axes("nfa", 4, 8)
+    assert ax["prefix_k"] and all(1 <= k <= 8 for k in ax["prefix_k"])
+    assert set(ax["spt"]) == {8, 32} and set(ax["threads"]) == {256, 512}
+    assert set(ax["settle"]) == {8, 16} and "table_smem" not in ax
+    dfa = tune.axes("dfa", 256, 2)
+    assert set(dfa["table_smem"]) == {-1, 0, 1} and "settle" not in dfa
+    assert max(dfa["prefix_k"]) == 2            # 8-bit symbols: 16 bits of index
+    c = tune.candidates("dfa", 4, 6)
+    assert len(c) == np.prod([len(v) for v in tune.axes("dfa", 4, 6).values()])
     tune._store("nfa/Q10/S4/gpu", {"prefix_k": 6}, 1.5)
-    assert json.load(open(tmp_path / "cache.json"))["nfa/Q10/S4/gpu"]["params"] == {"prefix_k": 6}
+    assert json.load(open(tmp_path / "sub" / "cache.json"))["nfa/Q10/S4/gpu"]["params"] == {"prefix_k": 6}
+    # the default cache sits outside the package directory
+    import paper_1110_1716_gb300 as pkg
+    assert not tune._default_cache_path().startswith(os.path.dirname(pkg.__file__))
+
+
+def test_tuner_descent_finds_the_minimum_axis_by_axis():
+    from paper_1110_1716_gb300 import tune
+    cost = {"a": {0: 5.0, 1: 3.0, 2: 4.0}, "b": {0: 2.0, 1: 1.0}}
+    calls = []
+
+    def timer(p):
+        calls.append(dict(p))
+        return cost["a"][p["a"]] + cost["b"][p["b"]]
+
+    best, ms, evals = tune._descend({"a": 0, "b": 0}, {"a": [0, 1, 2], "b": [0, 1]}, timer)
+    assert best == {"a": 1, "b": 1} and ms == 4.0
+    assert evals == len(calls) and len({json.dumps(c, sort_keys=True) for c in calls}) == evals
 
 
 # ---------------------------------------------------------------- serving: batch packing

@@ -31,6 +31,7 @@ Workload shapes (one generator per shape):
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 from typing import List, Optional, Sequence, Tuple
 
@@ -437,6 +438,17 @@ def trie_dfa(sigs: Sequence[bytes], S: int = 256) -> Tuple[Dfa, dict]:
     return Dfa(delta=delta, q0=0, dead=dead, final=fin, labels=labels), final_of
 
 
+@functools.lru_cache(maxsize=64)
+def _prefix_index(sigs: Tuple[bytes, ...]) -> dict:
+    """Which signatures begin with a given proper prefix (used to plant
+    overlapping pairs)."""
+    by_prefix = {}
+    for j, s in enumerate(sigs):
+        for ln in range(1, len(s)):
+            by_prefix.setdefault(s[:ln], []).append(j)
+    return by_prefix
+
+
 def plant_signatures(text: np.ndarray, sigs: Sequence[bytes], every: int, seed: int):
     """Plant one signature per ``every`` bytes at a random offset inside each
     block. One block in eight plants an overlapping pair: a second signature
@@ -445,11 +457,7 @@ def plant_signatures(text: np.ndarray, sigs: Sequence[bytes], every: int, seed: 
     Returns [(pos, signature index)] of everything written."""
     rng = np.random.default_rng(seed)
     n = len(text)
-    # index: which signatures begin with a suffix of signature i
-    by_prefix = {}
-    for j, s in enumerate(sigs):
-        for ln in range(1, len(s)):
-            by_prefix.setdefault(s[:ln], []).append(j)
+    by_prefix = _prefix_index(tuple(sigs))
     plants = []
     for blk in range(0, n, every):
         i = int(rng.integers(0, len(sigs)))
