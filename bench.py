@@ -229,22 +229,16 @@ def oracle_work(aut, text, threads):
     return sum(p[0] for p in parts), sum(p[1] for p in parts), time.perf_counter() - t0
 
 
-# INT32 lanes per SM (Blackwell: 128 cores, each able to take a 32-bit integer op per clock)
-INT_LANES_PER_SM = 128
-
-
-def work_rate(res, nsm, sm_mhz):
-    """Pair-steps per second of the scan kernel against the integer-issue
-    peak (one 32-bit integer op per pair-step on every lane of every SM)."""
+def work_rate(res):
+    """The method's throughput in the paper's unit (Sec. III.B): (start,
+    state) pairs the per-symbol procedure advances, counted by the oracle
+    over the whole text, per second of the scan kernel. The kernel skips
+    most of these steps through load-time tables, so this is a rate, not a
+    fraction of a machine peak."""
     cores = max(1, os.cpu_count() or 1)
     steps, cnt, secs = oracle_work(res["aut"], res["text"], cores)
-    rate = steps / (res["kernel_ms"] * 1e-3)
-    peak = nsm * INT_LANES_PER_SM * sm_mhz * 1e6
-    return {"unit": "pair-steps/s", "bound": "alu", "achieved": rate, "peak": peak,
-            "frac": rate / peak, "pair_steps": steps,
-            "pair_steps_per_byte": steps / max(1, len(res["text"])),
-            "peak_basis": "%d SMs x %d INT32 lanes x %.0f MHz, one op per pair-step"
-                          % (nsm, INT_LANES_PER_SM, sm_mhz),
+    return {"unit": "pair-steps/s", "achieved": steps / (res["kernel_ms"] * 1e-3),
+            "pair_steps": steps, "pair_steps_per_byte": steps / max(1, len(res["text"])),
             "source": "oracle count over the whole text, %d start windows on %d threads, %.1f s"
                       % (cores, cores, secs),
             "oracle_matches": cnt, "matches_agree": cnt == res["matches"]}
@@ -293,6 +287,13 @@ def device_time_steps(P, pf, aut_id, text_dev, out, status, steps, flush, stream
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def r4(x):
+    """Four significant digits (keeps the one JSON line short)."""
+    if isinstance(x, float):
+        return float("%.4g" % x)
+    return x
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1110_1716_gb300 as P
@@ -306,7 +307,10 @@ def run_ours(args, rank, world, local_rank):
 
     def measure(name, steps, warmup, seed):
         aut, text = make_workload(name, seed + rank)
+        t0 = time.perf_counter()
         aid = pf.load(aut)
+        load_ms = (time.perf_counter() - t0) * 1e3
+        dev_bytes, _ = P.pfsm_aut_bytes(pf.ctx, aid)
         if args.params:
             P.pfsm_set_params(pf.ctx, aid, json.loads(args.params))
         tdev = pf.to_device(text)
@@ -341,15 +345,17 @@ def run_ours(args, rank, world, local_rank):
         algo_bytes = n + 12 * int(cnt)
         kind = 0 if hasattr(aut, "delta") else 1
         launches_per_step = 2 if kind == 0 else 1
+        params = P.pfsm_get_params(pf.ctx, aid)
         res = {
             "workload": name, "desc": WORKLOADS[name], "bytes": n, "matches": int(cnt),
             "ms_per_step": step_ms, "gbps": n / (step_ms * 1e-3) / 1e9 * world,
             "matches_per_s": cnt / (step_ms * 1e-3) * world,
-            "kernel_ms": kernel_ms, "params": P.pfsm_get_params(pf.ctx, aid),
+            "kernel_ms": kernel_ms, "params": params,
+            "load_ms": load_ms, "device_bytes": int(dev_bytes),
             "roofline": {"bound": "hbm", "achieved": algo_bytes / (kernel_ms * 1e-3) / 1e9,
                          "peak": hbm, "unit": "GB/s",
                          "frac": algo_bytes / (kernel_ms * 1e-3) / 1e9 / hbm,
-                         "traffic": kernel_traffic(name, n, P.pfsm_get_params(pf.ctx, aid)),
+                         "traffic": kernel_traffic(name, n, params),
                          "peak_source": peak_kind,
                          "algorithmic_bytes": algo_bytes},
             "clocks": clk.summary(), "gpu_launches": launches_per_step * steps,
@@ -380,15 +386,8 @@ def run_ours(args, rank, world, local_rank):
         return res
 
     main = measure(args.workload, args.steps, args.warmup, args.seed)
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_mhz = float(main["clocks"].get("sm_max_mhz") or 2070.0)
     others = {}
-    if not args.only and not args.no_batch:
-        others["batch_10k_texts"] = measure_batch(P, pf, torch, dev)
-    if not args.only and not args.no_serve:
-        others["serving"] = measure_serving(P, pf, torch, dev)
-    if not args.only:
-        others["long_lived_dfa_16kib"] = measure_partitioning(P, pf, torch, dev)
+    cpu_ok = world == 1 and rank == 0 and not args.no_cpu_baseline
     if not args.only:
         for name in WORKLOADS:
             if name == args.workload:
@@ -397,41 +396,134 @@ def run_ours(args, rank, world, local_rank):
             r = measure(name, steps, 5, 0)
             others[name] = {k: r[k] for k in ("desc", "bytes", "matches", "ms_per_step", "gbps",
                                               "matches_per_s", "kernel_ms", "roofline", "e2e",
-                                              "params")}
-            if name == "dna_dfa_1mib" and rank == 0 and not args.no_cpu_baseline:
-                others[name]["work"] = work_rate(r, nsm, sm_mhz)
+                                              "params", "load_ms", "device_bytes")}
+            if cpu_ok:
+                others[name]["cpu_baseline"] = cpu_baseline(
+                    r["aut"], r["text"], seconds_target=4.0 if name == "dna_dfa_1mib" else 8.0)
+                if name == "dna_dfa_1mib":
+                    others[name]["work"] = work_rate(r)
+    if not args.only and not args.no_batch:
+        others["batch_10k_texts"] = measure_batch(P, pf, torch, dev, hbm, peak_kind,
+                                                  cpu=cpu_ok)
+    if not args.only:
+        others["long_lived_dfa_16kib"] = measure_partitioning(P, pf, torch, dev)
+    if not args.only and not args.no_serve:
+        others["serving"] = measure_serving(P, pf, torch, dev)
     if rank != 0:
-        return None
+        return None, None
+    detail = {"main": {k: v for k, v in main.items() if k not in ("aut", "text")},
+              "workloads": others}
     line = {
         "metric": "GB/s scanned (exact match set) of the PFSM scan",
         "value": main["gbps"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded generators; no public dataset exists for this method)",
-        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload],
-                   "bytes_per_gpu": main["bytes"], "matches": main["matches"],
-                   "l2": "flushed between steps (256 MiB write, untimed)",
-                   "parallelism": "replicas" if world == 1 else "weak, one text per rank",
-                   "params": main["params"]},
-        "matches_per_s": main["matches_per_s"],
-        "kernel_ms": main["kernel_ms"],
-        "roofline": main["roofline"],
-        "e2e": main["e2e"],
-        "clocks": main["clocks"],
         "gpu_launches": main["gpu_launches"],
-        "workloads": others,
+        "config": {"workload": args.workload, "bytes_per_gpu": main["bytes"],
+                   "matches": main["matches"], "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world == 1 else "weak, one text per rank"},
+        "roofline": {k: r4(v) for k, v in main["roofline"].items() if k != "algorithmic_bytes"},
+        "e2e": {k: r4(v) for k, v in main["e2e"].items()},
+        "clocks": main["clocks"],
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(main["aut"], main["text"])
-        line["work"] = work_rate(main, nsm, sm_mhz)
-    return line
+    if cpu_ok:
+        cb = cpu_baseline(main["aut"], main["text"])
+        detail["main"]["cpu_baseline"] = cb
+        line["cpu_baseline"] = {"value": r4(cb["value"]), "unit": cb["unit"], "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"]}
+        detail["main"]["work"] = work_rate(main)
+    line["configs"] = compact_configs(args.workload, main, others, detail)
+    return line, detail
 
 
-def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
+def compact_configs(main_name, main, others, detail):
+    """One short entry per configuration (the five of the survey's table),
+    placed at the end of the JSON line."""
+    def scan_entry(r, cpu=None):
+        e = {"gbps": r4(r["gbps"]), "kernel_ms": r4(r["kernel_ms"]),
+             "frac": r4(r["roofline"]["frac"]), "e2e_gbps": r4(r["e2e"]["value"]),
+             "matches": r["matches"], "load_ms": r4(r["load_ms"]),
+             "dev_mb": r4(r["device_bytes"] / 1e6)}
+        if cpu:
+            e["cpu_gbps"] = r4(cpu["value"])
+            e["cpu_1core_gbps"] = r4(cpu["single_thread"]["value"])
+        return e
+    allr = dict(others)
+    allr[main_name] = main
+    out = {}
+    for key, name in (("c0_dna_dfa_1mib", "dna_dfa_1mib"), ("c1_motif_nfa_64mib", "motif_nfa_64mib"),
+                      ("c2_byte_trie_1gib", "byte_trie_1gib")):
+        if name in allr:
+            r = allr[name]
+            cpu = r.get("cpu_baseline") or (detail["main"].get("cpu_baseline") if name == main_name else None)
+            out[key] = scan_entry(r, cpu)
+            work = r.get("work") or (detail["main"].get("work") if name == main_name else None)
+            if work:
+                out[key]["pair_steps_per_s"] = r4(work["achieved"])
+    b = others.get("batch_10k_texts")
+    if b:
+        out["c3_batch_10k_texts"] = {
+            "gbps": r4(b["gbps"]), "device_gbps": r4(b["device_gbps"]),
+            "frac": r4(b["roofline"]["frac"]), "e2e_gbps": r4(b["e2e"]["value"]),
+            "plain_gbps": r4(b["plain_gbps"]), "x_plain": r4(b["speedup_vs_plain"]),
+            "cpu_gbps": r4(b["cpu_baseline"]["value"]) if b.get("cpu_baseline") else None,
+            "params_source": b["params_source"], "tuned": b["tuned_batch"]}
+    sv = others.get("serving")
+    if sv:
+        out["c4_serving"] = {
+            "p50_ms": r4(sv["p50_ms"]), "p99_ms": r4(sv["p99_ms"]), "load": sv["offered_load"],
+            "served_gbps": r4(sv["served_gbps"]), "burst_rps": r4(sv["burst_req_per_s"]),
+            "plain_rps": r4(sv["plain_req_per_s"]),
+            "p99_by_load": {k: r4(v["p99_ms"]) for k, v in sv["loads"].items()},
+            "small_budget": {"p50_ms": r4(sv["small_budget"]["p50_ms"]),
+                             "p99_ms": r4(sv["small_budget"]["p99_ms"]),
+                             "evictions": sv["small_budget"]["evictions"]}}
+    return out
+
+
+def batch_cpu_baseline(w, seconds_target=8.0):
+    """The oracle on the batch's texts in job order (one text per task, on
+    every host core), over a bounded prefix of the batch sized to take about
+    `seconds_target`."""
+    import concurrent.futures
+    import oracle
+    cores = max(1, os.cpu_count() or 1)
+    lengths = np.diff(w.offsets)
+
+    def one(i):
+        a = w.automata[int(w.job_aut[i])]
+        return len(oracle.scan(a, w.data[int(w.offsets[i]):int(w.offsets[i + 1])]))
+
+    # probe: the first texts up to 4 MB on one thread
+    t0 = time.perf_counter()
+    k, probe = 0, 0
+    while k < len(lengths) and probe < (4 << 20):
+        one(k)
+        probe += int(lengths[k])
+        k += 1
+    rate = probe / max(1e-6, time.perf_counter() - t0)       # bytes/s on one core
+    want = rate * cores * seconds_target
+    k2 = int(np.searchsorted(np.cumsum(lengths), want)) + 1
+    k2 = max(k, min(len(lengths), k2))
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+        cnt = sum(ex.map(one, range(k2)))
+    wall = time.perf_counter() - t0
+    nbytes = int(w.offsets[k2])
+    return {"value": nbytes / wall / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "the first %d texts of the batch (%d bytes), one text per task on %d "
+                      "threads, %.1f s, %d matches" % (k2, nbytes, cores, wall, cnt)}
+
+
+def measure_batch(P, pf, torch, dev, hbm, peak_kind, n_texts=10_000, steps=5, cpu=True):
     """Batched form (one call over every text) against the plain form (one
-    pfsm_scan per text) on the mixed many-texts workload. batch_ms spans the
-    whole call on an idle stream (host planning, table copy, graph); the
-    graph alone is device_ms (the library's own timer)."""
+    pfsm_scan per text) on the mixed many-texts workload. The launch shape
+    and per-machine placement are chosen by the autotuner on the batch
+    first. batch_ms spans the whole call on an idle stream (host planning,
+    table copy, graph); the graph alone is device_ms (the library's own
+    timer)."""
+    from paper_1110_1716_gb300 import tune
     t0 = time.perf_counter()
     w = W.batch_workload(seed=0, n_texts=n_texts)
     gen_s = time.perf_counter() - t0
@@ -440,10 +532,15 @@ def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
     lengths = np.diff(w.offsets)
     table = P.job_table(ids[w.job_aut], data.data_ptr() + w.offsets[:-1], lengths)
     total_bytes = int(w.offsets[-1])
+    s = torch.cuda.Stream(device=dev)
+    # autotuner: launch shape, then table placement / settling per machine
+    kinds = {int(ids[i]): ("dfa" if hasattr(a, "delta") else "nfa") for i, a in enumerate(w.automata)}
+    t0 = time.perf_counter()
+    tuned = tune.tune_batch(pf.ctx, table, reps=1, stream=s, machines=kinds)
+    tune_s = time.perf_counter() - t0
     st, counts, total = P.pfsm_scan_batch(pf.ctx, table, None, 0)
     out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
     status = torch.zeros(len(table) + 2, dtype=torch.int64, device=dev)
-    s = torch.cuda.Stream(device=dev)
     P.pfsm_scan_batch_async(pf.ctx, table, out, status, stream=s)   # warm (graph capture)
     s.synchronize()
     ms, host_ms = [], []
@@ -463,6 +560,26 @@ def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
     P.pfsm_set_timing(pf.ctx, False)
     assert int(status[0].item()) == total and int(status[1].item()) == 0
     batch_ms = float(np.median(ms))
+    device_ms = dev_ms / max(1, nlaunch)
+    algo = total_bytes + 16 * int(total)
+    # end to end: the concatenated texts from pinned host memory, the batch,
+    # the matches back to the host
+    host = torch.from_numpy(w.data).pin_memory()
+    host_out = torch.empty((int(total) + 1024, 4), dtype=torch.int32).pin_memory()
+    dbuf = torch.empty(total_bytes, dtype=torch.uint8, device=dev)
+    table2 = P.job_table(ids[w.job_aut], dbuf.data_ptr() + w.offsets[:-1], lengths)
+    e2e = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            dbuf.copy_(host, non_blocking=True)
+            st, cnts, tot = P.pfsm_scan_batch(pf.ctx, table2, out, out.shape[0], stream=s)
+            host_out[:tot].copy_(out[:tot], non_blocking=True)
+        s.synchronize()
+        e2e.append(time.perf_counter() - t0)
+        assert tot == total
+    e2e_s = float(np.median(e2e))
     # plain form: one scan per text, back to back on one stream
     jobs = [(int(ids[w.job_aut[i]]), data[int(w.offsets[i]):int(w.offsets[i + 1])],
              int(lengths[i])) for i in range(len(lengths))]
@@ -478,14 +595,29 @@ def measure_batch(P, pf, torch, dev, n_texts=10_000, steps=3):
     plain_ms = e0.elapsed_time(e1)
     for a in ids:
         P.pfsm_unload(pf.ctx, int(a))
-    return {"desc": "10,000 texts, log-uniform 100 B-1 MiB, 8 motif NFAs + 8 byte tries",
-            "bytes": total_bytes, "matches": int(total), "texts": len(jobs),
-            "batch_ms": batch_ms, "gbps": total_bytes / (batch_ms * 1e-3) / 1e9,
-            "host_call_ms": float(np.median(host_ms)),
-            "device_ms": dev_ms / max(1, nlaunch),
-            "device_gbps": total_bytes / (dev_ms / max(1, nlaunch) * 1e-3) / 1e9,
-            "plain_loop_ms": plain_ms, "plain_gbps": total_bytes / (plain_ms * 1e-3) / 1e9,
-            "speedup_vs_plain": plain_ms / batch_ms, "generate_s": gen_s}
+    P.pfsm_set_batch_params(pf.ctx, None)
+    b = tuned["batch"]
+    res = {"desc": "10,000 texts, log-uniform 100 B-1 MiB, 8 motif NFAs + 8 byte tries",
+           "bytes": total_bytes, "matches": int(total), "texts": len(jobs),
+           "batch_ms": batch_ms, "gbps": total_bytes / (batch_ms * 1e-3) / 1e9,
+           "host_call_ms": float(np.median(host_ms)),
+           "device_ms": device_ms, "device_gbps": total_bytes / (device_ms * 1e-3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": algo / (device_ms * 1e-3) / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": algo / (device_ms * 1e-3) / 1e9 / hbm,
+                        "peak_source": peak_kind, "algorithmic_bytes": algo,
+                        "basis": "every text read once + 16 B per match, over the batch graph's "
+                                 "device time"},
+           "e2e": {"value": total_bytes / e2e_s / 1e9, "unit": "GB/s",
+                   "h2d_bytes_per_step": total_bytes, "d2h_bytes_per_step": 16 * int(total)},
+           "plain_loop_ms": plain_ms, "plain_gbps": total_bytes / (plain_ms * 1e-3) / 1e9,
+           "speedup_vs_plain": plain_ms / batch_ms, "generate_s": gen_s,
+           "params_source": "autotuner", "tune_s": tune_s,
+           "tuned_batch": {"threads": b["threads"], "ctas_per_sm": b["ctas_per_sm"],
+                           "tile": b["tile"]},
+           "tuned_machines": {str(k): v for k, v in tuned["machines"].items()}}
+    if cpu:
+        res["cpu_baseline"] = batch_cpu_baseline(w)
+    return res
 
 
 def measure_partitioning(P, pf, torch, dev, n=16 << 10, steps=10):
@@ -696,12 +828,16 @@ def main():
         # the scaling runs measure the main workload only: every GPU is held
         # for the whole run
         args.only = True
-    line = run_ours(args, rank, world, local_rank)
+    line, detail = run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank == 0 and line is not None:
+        # the full record on stderr; the one JSON line (with a short entry
+        # per configuration at its end) on stdout
+        print(json.dumps(detail, default=str), file=sys.stderr)
+        sys.stderr.flush()
         print(json.dumps(line))
 
 

@@ -41,7 +41,7 @@ __device__ __forceinline__ uint32_t find_unit_job(const BatchJob *jobs, uint32_t
 
 __device__ __forceinline__ MView mview_of(const DevMachine &m) {
     return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.surv2_m, m.surv2, m.dtab, m.off, m.tgt,
-                 m.tail, m.ecl_off, m.ecl_tgt, m.l2tab, m.pool2};
+                 m.tail, m.ecl_off, m.ecl_tgt, m.l2tab, m.pool2, m.memox};
 }
 
 // Copies `words` 32-bit words (16-byte aligned source and destination).
@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
         smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
+        Pend no_pend{0u, 0u, 0u, false};
         process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
-                                       static_cast<uint32_t>(M.settle), NC);
+                                       static_cast<uint32_t>(M.settle), NC, no_pend);
         __syncwarp();
         if (lane == 0) mbar_arrive(&misc->empty[buf]);
         have_prev = true;

@@ -297,6 +297,7 @@ bool build_memo_nfa(Machine &m) {
     m.tail.clear();
     m.l2tab.clear();
     m.pool2.clear();
+    m.memox.clear();
     if (m.k <= 0) {
         m.memo.clear();
         return true;
@@ -312,6 +313,18 @@ bool build_memo_nfa(Machine &m) {
     if (!b.ok) return false;
     if (b.l2) b.build_l2();
     if (m.pool.empty()) m.pool.push_back(0);
+    // the second-level set index of every k-gram's record, beside the table
+    m.memox.clear();
+    if (!m.l2tab.empty()) {
+        m.memox.assign(m.memo.size(), L2_NONE);
+        for (size_t g = 0; g < m.memo.size(); ++g) {
+            const uint32_t e = m.memo[g];
+            if (e >= PT_WALK) continue;
+            const uint32_t hdr = m.pool[e];
+            if ((hdr & 0xFFFFu) == 0 && (hdr >> 16) != 0)
+                m.memox[g] = static_cast<uint16_t>(m.pool[e + 1 + (hdr >> 16)]);
+        }
+    }
     return true;
 }
 
@@ -426,7 +439,8 @@ size_t device_bytes(const Machine &m) {
         b += align256(m.off.size() * 4) + align256(m.tgt.size() * 2 + 4) +
              align256(m.pool.size() * 4) + align256(m.band.size() * 4) +
              align256(m.ecl_off.size() * 4) + align256(m.ecl_tgt.size() * 2 + 4) +
-             align256(m.l2tab.size() * 2) + align256(m.pool2.size() * 4);
+             align256(m.l2tab.size() * 2) + align256(m.pool2.size() * 4 + 16) +
+             align256(m.memox.size() * 2 + 4);
     }
     return b;
 }
@@ -554,7 +568,9 @@ static int build_host_image(Machine &m) {
         m.o_eoff = put(m.ecl_off.data(), m.ecl_off.size() * 4, 0);
         m.o_etgt = put(m.ecl_tgt.data(), m.ecl_tgt.size() * 2, 4);
         m.o_l2tab = put(m.l2tab.data(), m.l2tab.size() * 2, 0);
-        m.o_pool2 = put(m.pool2.data(), m.pool2.size() * 4, 0);
+        // 16 bytes of slack: a record's first words are read together
+        m.o_pool2 = put(m.pool2.data(), m.pool2.size() * 4, 16);
+        m.o_memox = put(m.memox.data(), m.memox.size() * 2, 4);
     }
     if (o > bytes) {   // layout and size disagree: a bug, fail loudly
         cudaFreeHost(h);
@@ -597,6 +613,7 @@ static DevMachine dev_view(const Machine &m, uint8_t *base) {
         dm.ecl_tgt = m.ecl_off.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_etgt);
         dm.l2tab = m.l2tab.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_l2tab);
         dm.pool2 = m.l2tab.empty() ? nullptr : reinterpret_cast<const uint32_t *>(base + m.o_pool2);
+        dm.memox = m.memox.empty() ? nullptr : reinterpret_cast<const uint16_t *>(base + m.o_memox);
     }
     return dm;
 }
@@ -828,6 +845,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     a.tgt = m.dm.tgt;
     a.pool = m.dm.pool;
     a.l2tab = m.dm.l2tab;
+    a.memox = m.dm.memox;
     a.pool2 = m.dm.pool2;
     a.pool_n = m.dm.pool_n;
     a.band = m.dm.band;

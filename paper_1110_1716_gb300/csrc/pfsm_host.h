@@ -37,6 +37,7 @@ struct Machine {
     std::vector<uint32_t> pool;
     std::vector<uint16_t> l2tab;      // NFA: second-level tables (see L2_SYMS) or empty
     std::vector<uint32_t> pool2;      // NFA: second-level records
+    std::vector<uint16_t> memox;      // NFA: second-level set index per k-gram, or empty
     std::vector<uint32_t> band;   // NFA band image (S <= 4) or empty
     // survival bitmap over m-grams (m = 0: none)
     int sm_m = 0, sm_m2 = 0;
@@ -50,7 +51,7 @@ struct Machine {
     size_t img_bytes = 0;
     size_t o_memo = 0, o_tail = 0, o_surv = 0, o_surv2 = 0, o_tab = 0, o_off = 0,
            o_tgt = 0, o_pool = 0, o_band = 0, o_eoff = 0, o_etgt = 0, o_l2tab = 0,
-           o_pool2 = 0;   // section offsets
+           o_pool2 = 0, o_memox = 0;   // section offsets
     cudaEvent_t ready = nullptr;      // recorded after the last upload
     // last use per stream (an event recorded after a launch that read the
     // image); an eviction orders its free after every one of them

@@ -52,6 +52,11 @@ constexpr uint16_t L2_NONE = 0xFFFF;
 constexpr uint16_t L2_EMPTY = 0xFFFF;
 constexpr uint32_t L2_MAX_SETS = 4096;   // at most 8 MB of second-level tables
 constexpr uint32_t L2_NO_REC = 0xFFFFFFFFu;   // (device) a start without a second-level record
+// memox[w] (beside the prefix table, same index): the survivor-set index x
+// of k-gram w's first-level record when that record has survivors, no
+// matches and a second-level table, else L2_NONE. Read together with
+// memo[w], it lets a start go to the second level without reading the
+// record itself.
 
 // NFA short-gram table: a start with only j < k symbols left before the end
 // of its text has its whole future fixed by those j symbols: the matches it
@@ -118,6 +123,7 @@ struct ScanArgs {
     const uint32_t *pool;   // NFA: prefix records
     const uint16_t *l2tab;  // NFA: second-level tables (see L2_SYMS), or null
     const uint32_t *pool2;  // NFA: second-level records
+    const uint16_t *memox;  // NFA: second-level set index per k-gram (with l2tab)
     const uint32_t *band;   // NFA: band image (rows, then final bitmap) or null
     uint32_t pool_n;        // NFA: words of pool
     int32_t pool_smem;      // NFA: pool staged to smem
@@ -191,6 +197,7 @@ struct DevMachine {
     const uint32_t *pool;
     const uint16_t *l2tab;  // NFA: second-level tables, or null
     const uint32_t *pool2;
+    const uint16_t *memox;  // NFA: second-level set index per k-gram (with l2tab)
     const uint32_t *band;
     uint32_t pool_n;
     int32_t surv_m;

@@ -314,6 +314,7 @@ struct MView {
     const uint16_t *ecl_tgt;
     const uint16_t *l2tab;  // NFA second-level tables (see L2_SYMS), or null
     const uint32_t *pool2;  // NFA second-level records
+    const uint16_t *memox;  // NFA second-level set index per k-gram (with l2tab)
 };
 
 // Where matches and carried instances go.
@@ -592,12 +593,24 @@ static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const T
     {
         const uint32_t j = j0 + lane;
         uint32_t ns = 0, rec = 0;
+        uint32_t pre0 = 0, pre1 = 0, pre2 = 0;   // a second-level record's first survivors
         const bool lvl2 = r2 != L2_NO_REC;
         if (j < total) {
             if (e == PT_WALK) {
                 mark_entry(marks, j);
             } else if (e != PT_SKIP) {
-                const uint32_t hdr = lvl2 ? __ldg(mv.pool2 + r2) : sm.pool[e];
+                uint32_t hdr;
+                if (lvl2) {
+                    // the header and the first three words after it in one
+                    // round trip (the records are followed by 16 bytes of slack)
+                    const uint32_t *p = mv.pool2 + r2;
+                    hdr = __ldg(p);
+                    pre0 = __ldg(p + 1);
+                    pre1 = __ldg(p + 2);
+                    pre2 = __ldg(p + 3);
+                } else {
+                    hdr = sm.pool[e];
+                }
                 if (hdr & 0xFFFFu) mark_entry(marks, j);   // matches inside the prefix
                 else ns = hdr >> 16, rec = lvl2 ? r2 : e;
             }
@@ -613,9 +626,11 @@ static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const T
         if (ns && !fits) mark_entry(marks, j);
         if (ns && fits) {
             if (lvl2) {
-                for (uint32_t x = 0; x < ns; ++x)
-                    pairs[base + x] = (j << 21) | (static_cast<uint32_t>(L2_SYMS) << 15) |
-                                      __ldg(mv.pool2 + rec + 1 + x);
+                for (uint32_t x = 0; x < ns; ++x) {
+                    const uint32_t q = x == 0 ? pre0 : x == 1 ? pre1 : x == 2 ? pre2
+                                     : __ldg(mv.pool2 + rec + 1 + x);
+                    pairs[base + x] = (j << 21) | (static_cast<uint32_t>(L2_SYMS) << 15) | q;
+                }
             } else {
                 for (uint32_t x = 0; x < ns; ++x)
                     pairs[base + x] = (j << 21) | sm.pool[rec + 1 + x];   // step 0
@@ -927,15 +942,139 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
     wq_n = 0;
 }
 
+// ------------------------------------------------------------ lane-local settling
+// Single-text NFA scans with second-level records: a start that passes the
+// deep filter is held by one lane (its start and the 32 symbols from it,
+// packed), until every lane of the warp holds one. Then each lane, on its
+// own, looks its start up (prefix entry and second-level set index side by
+// side, the second-level entry, the first words of the second-level record)
+// and advances the record's state set (at most SETTLE_LANE_STATES states,
+// Sec. III.B step 3 on one instance) through the band rows from L2_SYMS
+// steps past the prefix up to the settling cap. An instance whose set
+// empties reports nothing and is done. Any other outcome (a final state,
+// a match inside the records, a row outside the band, a larger set, the
+// cap) sends the start to the exact path (the warp queue), which redoes it
+// from its first-level record. No warp synchronisation inside the pass.
+constexpr int SETTLE_LANE_STATES = 4;
+
+struct Pend {
+    uint32_t start;   // absolute start
+    uint32_t g0, g1;  // symbols start .. start + 15 and start + 16 .. start + 31
+    bool on;
+};
+
+template <int KIND, bool TAB_SMEM, int OUTW>
+__device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
+                             Pend &p, uint32_t &wq_n, uint32_t &sn, int lane, uint64_t pol_keep,
+                             uint32_t max_steps) {
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
+    const uint32_t kk = static_cast<uint32_t>(mv.k), n = tv.n;
+    const uint32_t mask = (1u << (2 * kk)) - 1;
+    const uint32_t *fin = sm.band + mv.Q;
+    bool exact = false;
+    uint32_t e = PT_SKIP;
+    if (p.on) {
+        const uint32_t gi = p.g0 & mask;
+        const uint32_t x = ldg_u16_keep(mv.memox + gi, pol_keep);
+        e = sm.memo[gi];
+        if (x == L2_NONE) {
+            exact = e != PT_SKIP;
+        } else {
+            const uint32_t o2 = ldg_u16_keep(
+                mv.l2tab + x * L2_GRAMS + ((p.g0 >> (2 * kk)) & (L2_GRAMS - 1)), pol_keep);
+            if (o2 != L2_EMPTY) {
+                const uint32_t *q = mv.pool2 + o2;   // 16 bytes of slack follow the records
+                const uint32_t hdr = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2),
+                               w3 = __ldg(q + 3);
+                const uint32_t ns = hdr >> 16;
+                if ((hdr & 0xFFFFu) || ns == 0 || ns > 3) {
+                    exact = true;
+                } else {
+                    uint32_t s0 = w1, s1 = ns > 1 ? w2 : NONE, s2 = ns > 2 ? w3 : NONE, s3 = NONE;
+                    uint32_t cnt = ns;
+                    for (uint32_t st = L2_SYMS; st < max_steps && cnt; ++st) {
+                        const uint32_t pos = p.start + kk + st;
+                        if (pos >= n) {   // the text ends: nothing more to report
+                            cnt = 0;
+                            break;
+                        }
+                        const uint32_t ix = kk + st;   // < 32
+                        const uint32_t c = (ix < 16 ? p.g0 >> (2 * ix) : p.g1 >> (2 * (ix - 16))) & 3u;
+                        uint32_t n0 = NONE, n1 = NONE, n2 = NONE, n3 = NONE, nc = 0;
+                        bool bad = false;
+#pragma unroll
+                        for (int i = 0; i < SETTLE_LANE_STATES; ++i) {
+                            const uint32_t qs = i == 0 ? s0 : i == 1 ? s1 : i == 2 ? s2 : s3;
+                            if (static_cast<uint32_t>(i) < cnt && !bad) {
+                                const uint32_t row = sm.band[qs];
+                                if (row == BAND_CSR) {
+                                    bad = true;
+                                } else {
+                                    uint32_t m = (row >> (8 * c)) & 0xFFu;
+                                    while (m && !bad) {
+                                        const uint32_t t = qs + __ffs(m);
+                                        m &= m - 1;
+                                        if ((fin[t >> 5] >> (t & 31)) & 1u) {
+                                            bad = true;   // a match: the exact path reports it
+                                        } else if (t != n0 && t != n1 && t != n2 && t != n3) {
+                                            if (nc == SETTLE_LANE_STATES) {
+                                                bad = true;
+                                            } else {
+                                                n0 = nc == 0 ? t : n0;
+                                                n1 = nc == 1 ? t : n1;
+                                                n2 = nc == 2 ? t : n2;
+                                                n3 = nc == 3 ? t : n3;
+                                                ++nc;
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        if (bad) {
+                            exact = true;
+                            cnt = 0;
+                            break;
+                        }
+                        s0 = n0;
+                        s1 = n1;
+                        s2 = n2;
+                        s3 = n3;
+                        cnt = nc;
+                    }
+                    if (cnt) exact = true;   // alive at the cap
+                }
+            }
+        }
+    }
+    p.on = false;
+    const uint32_t pm = __ballot_sync(FULLMASK, exact);
+    if (pm) {
+        if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
+            drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+        if (exact) {
+            const uint32_t at = wq_n + __popc(pm & lanemask_lt());
+            sm.wq_start[at] = p.start;
+            sm.wq_info[at] = static_cast<uint16_t>(e);
+        }
+        wq_n += __popc(pm);
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ one tile
 // Filter phase over the tile's own starts [b, own_end), then the
 // continuation of every queued instance. All threads of the CTA call this.
 // SPT: starts per thread per filter round (SPT / 8 windows of 8; 8 or 32).
 // NT consumer threads (ids 0 .. NT - 1) call it together.
-template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32>
+// DEFER (single-text NFA kernels): starts past the deep filter are settled
+// lane by lane (settle_lanes) once every lane holds one; `pend` persists
+// across tiles and the caller settles what is left after its last tile.
+template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32, bool DEFER = false>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
-                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps, int NT) {
+                             bool &bad_symbol, uint64_t pol_keep, uint32_t settle_steps, int NT,
+                             Pend &pend) {
     static_assert(SPT == 8 || SPT == 32, "SPT");
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = tv.n, b = tv.b;
@@ -1113,6 +1252,60 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             }
             total = w;
         }
+        // 3b'. lane-local settling: the entries are handed to lanes without
+        //      a start; a warp whose lanes all hold one settles them. Starts
+        //      too close to the end of the text for the second level go to
+        //      the exact path at once.
+        if (DEFER && KIND == 1 && SB == 2 && sm.band && settle_steps > 0 && mv.memox && total) {
+            for (uint32_t j0 = 0; j0 < total;) {
+                const uint32_t freem = __ballot_sync(FULLMASK, !pend.on);
+                if (freem == 0) {
+                    settle_lanes<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep,
+                                                       settle_steps);
+                    continue;
+                }
+                const uint32_t take = min(static_cast<uint32_t>(__popc(freem)), total - j0);
+                bool near_end = false;
+                uint32_t e = PT_SKIP, off = 0;
+                if (!pend.on) {
+                    const uint32_t r = __popc(freem & lanemask_lt());
+                    if (r < take) {
+                        off = sm.list[j0 + r];
+                        if (b + off + kk + L2_SYMS < n) {
+                            pend.start = b + off;
+                            pend.g0 = pk_gram(sm.pk, off);
+                            pend.g1 = pk_gram(sm.pk, off + 16);
+                            pend.on = true;
+                        } else {
+                            near_end = true;
+                            const uint32_t gram = pk_gram(sm.pk, off);
+                            if (b + off + kk <= n) {
+                                e = sm.memo[gram & mask];
+                            } else if (mv.tail) {
+                                const int jl = static_cast<int>(n - (b + off));
+                                e = __ldg(mv.tail + tail_base(jl, mv.sbits) + (gram & ((1u << (jl * 2)) - 1)));
+                            }
+                            near_end = e != PT_SKIP;
+                        }
+                    }
+                }
+                j0 += take;
+                const uint32_t nm = __ballot_sync(FULLMASK, near_end);
+                if (nm) {
+                    if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
+                        drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+                    if (near_end) {
+                        const uint32_t at = wq_n + __popc(nm & lanemask_lt());
+                        sm.wq_start[at] = b + off;
+                        sm.wq_info[at] = static_cast<uint16_t>(e);
+                    }
+                    wq_n += __popc(nm);
+                    __syncwarp();
+                }
+            }
+            __syncwarp();
+            continue;
+        }
         // 3b. every lane takes list entries: prefix table, settling, queue
         const bool settle = KIND == 1 && sm.band && settle_steps > 0 && total;
         if (settle) {
@@ -1129,23 +1322,18 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 e = PT_WALK;
                 if (kk != 0 && b + off + kk <= n) {
                     const uint32_t gram = SB == 2 ? pk_gram(sm.pk, off) : 0u;
-                    e = sm.memo[SB == 2 ? gram & mask
-                                        : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                    const uint32_t gi = SB == 2 ? gram & mask : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask);
                     // an NFA record with survivors and no matches carries the
-                    // start L2_SYMS symbols further through the second level
-                    if (KIND == 1 && SB == 2 && mv.l2tab && e < PT_WALK &&
-                        b + off + kk + L2_SYMS <= n) {
-                        const uint32_t hdr = sm.pool[e];
-                        if ((hdr & 0xFFFFu) == 0) {
-                            const uint32_t x = sm.pool[e + 1 + (hdr >> 16)];
-                            if (x != L2_NONE) {
-                                const uint32_t o2 = ldg_u16_keep(
-                                    mv.l2tab + x * L2_GRAMS + ((gram >> (2 * kk)) & (L2_GRAMS - 1)),
-                                    pol_keep);
-                                if (o2 == L2_EMPTY) e = PT_SKIP;   // nothing left: no match
-                                else r2 = o2;
-                            }
-                        }
+                    // start L2_SYMS symbols further through the second level:
+                    // its set index is read beside the prefix entry
+                    const bool l2 = KIND == 1 && SB == 2 && mv.memox && b + off + kk + L2_SYMS <= n;
+                    const uint32_t x = l2 ? ldg_u16_keep(mv.memox + gi, pol_keep) : L2_NONE;
+                    e = sm.memo[gi];
+                    if (l2 && x != L2_NONE) {
+                        const uint32_t o2 = ldg_u16_keep(
+                            mv.l2tab + x * L2_GRAMS + ((gram >> (2 * kk)) & (L2_GRAMS - 1)), pol_keep);
+                        if (o2 == L2_EMPTY) e = PT_SKIP;   // nothing left: no match
+                        else r2 = o2;
                     }
                 } else if (kk != 0 && mv.tail) {
                     // fewer than k symbols left: their matches are the whole result
@@ -1159,7 +1347,9 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             // reported here instead of going through the queue
             {
                 uint32_t pm_left = 0, pm_ptr = 0;
-                if (j < total && e != PT_SKIP && e != PT_WALK && (KIND == 1 || (e & PT_REC))) {
+                // (a start with a second-level record has survivors)
+                if (j < total && r2 == L2_NO_REC && e != PT_SKIP && e != PT_WALK &&
+                    (KIND == 1 || (e & PT_REC))) {
                     const uint32_t ro = KIND == 1 ? e : (e & 0x7FFFu);
                     const uint32_t hdr = sm.pool[ro];
                     if ((hdr >> 16) == 0) {

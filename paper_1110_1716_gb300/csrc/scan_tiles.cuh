@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
     const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
-                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2};
+                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox};
 
     if (a.memo_smem) stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
     if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     };
     uint32_t sn = 0;
     uint32_t wq_n = 0;   // entries in this warp's queue
+    Pend pend{0u, 0u, 0u, false};   // the start this lane holds for lane-local settling
     uint32_t abort_at = ~0u;   // CTA-synchronous form: the tile whose copy failed
 
     if constexpr (PIPE) {
@@ -177,9 +178,10 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
             }
             smk.pk = pk_sm + buf * a.pk_words;
             const TileView tv{text_sm + buf * a.text_buf, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT>(ov, mv, tv, smk, min(b + a.tile, n), wq_n, sn,
-                                                      bad_symbol, pol_keep,
-                                                      static_cast<uint32_t>(a.settle_steps), NC);
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, KIND == 1>(ov, mv, tv, smk, min(b + a.tile, n), wq_n,
+                                                                 sn, bad_symbol, pol_keep,
+                                                                 static_cast<uint32_t>(a.settle_steps), NC,
+                                                                 pend);
             __syncwarp();
             if (lane == 0) mbar_arrive(&misc->empty[buf]);
         }
@@ -204,16 +206,21 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
                 __syncthreads();
             }
             const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT>(ov, mv, tv, sm, min(b + a.tile, n), wq_n, sn,
-                                                      bad_symbol, pol_keep,
-                                                      static_cast<uint32_t>(a.settle_steps), NT);
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, KIND == 1>(ov, mv, tv, sm, min(b + a.tile, n), wq_n,
+                                                                 sn, bad_symbol, pol_keep,
+                                                                 static_cast<uint32_t>(a.settle_steps), NT,
+                                                                 pend);
             __syncthreads();   // the buffer is refilled next tile: every warp must be done
         }
     }
-    // instances queued across tiles run now, reading the text from global
-    // memory (the staged tiles are gone)
+    // starts still held for lane-local settling, then the instances queued
+    // across tiles, reading the text from global memory (the staged tiles
+    // are gone)
     {
         const TileView tv{text_sm, a.text, 0u, 0u, n, 0u, 0u};
+        if (KIND == 1 && __any_sync(0xffffffffu, pend.on))
+            settle_lanes<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep,
+                                            static_cast<uint32_t>(a.settle_steps));
         drain<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     }
     stage_flush<3>(sm.stage, sn, ov, 0u, lane);

@@ -194,7 +194,8 @@ def _time_batch(ctx, jobs, out, status, stream, reps) -> Optional[float]:
 def tune_batch(ctx: int, jobs, reps: int = 2, stream=None, machines: Optional[dict] = None,
                sweeps: int = 1) -> dict:
     """Pick the batch launch shape and per-machine placement for a
-    representative batch `jobs` ([(aut, text_tensor, n), ...]) by timing
+    representative batch `jobs` ([(aut, text_tensor, n), ...] or a job
+    table) on the current CUDA device by timing
     each candidate with CUDA events. `machines` maps each automaton id of
     the batch to "dfa" or "nfa" (its per-machine axes are searched; omit it
     to tune the launch shape only). Sets the fastest and returns
@@ -202,7 +203,7 @@ def tune_batch(ctx: int, jobs, reps: int = 2, stream=None, machines: Optional[di
     import torch
     stream = stream or torch.cuda.current_stream()
     st, counts, total = pfsm_scan_batch(ctx, jobs, None, 0)
-    dev = jobs[0][1].device if jobs else torch.device("cuda")
+    dev = torch.device("cuda", torch.cuda.current_device())
     out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
     status = torch.zeros(len(jobs) + 2, dtype=torch.int64, device=dev)
 

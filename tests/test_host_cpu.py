@@ -130,17 +130,16 @@ def test_pack_batch_one_machine():
 
 def test_bench_work_rate_counts_pair_steps():
     """The bench's work figure: the oracle's pair-step count over the whole
-    text (here a complete DFA: n(n+1)/2), per second of kernel time, against
-    SMs x INT32 lanes x clock."""
+    text (here a complete DFA: n(n+1)/2) per second of kernel time, reported
+    as a rate with no machine peak beside it."""
     import bench
     import oracle
     import workloads as W
     d = W.dfa_random(5, Q=7, S=3, dead=-1, finals=[1, 2], p_dead=0.0)
     text = W.text_uniform(3000, 3, 9)
     res = {"aut": d, "text": text, "kernel_ms": 2.0, "matches": len(oracle.scan(d, text))}
-    w = bench.work_rate(res, nsm=152, sm_mhz=2070.0)
+    w = bench.work_rate(res)
     assert w["pair_steps"] == 3000 * 3001 // 2
     assert w["matches_agree"] and w["oracle_matches"] == res["matches"]
     assert w["achieved"] == w["pair_steps"] / 2e-3
-    assert w["peak"] == 152 * 128 * 2070e6
-    assert abs(w["frac"] - w["achieved"] / w["peak"]) < 1e-12
+    assert "frac" not in w and "peak" not in w
