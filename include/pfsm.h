@@ -104,7 +104,7 @@ typedef struct {
                            filter before it is queued for the exact path,
                            counted from k symbols past its start (an instance
                            carried by a second-level record starts at step
-                           5); 0 = library default (16), -1 = queue at once */
+                           5); 0 = library default (8), -1 = queue at once */
     int32_t partition;  /* instances alive past their tile's staged text
                            (Sec. III.D.2): 1 = lazy (continue in place on the
                            global text), 2 = chained (DFA only: hand the

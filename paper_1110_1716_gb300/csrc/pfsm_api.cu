@@ -733,7 +733,9 @@ void fill_defaults(const Machine &m, pfsm_params &p) {
     // threads 0 = automatic: 512, fewer for texts too short to fill the GPU
 
     if (p.table_smem == 0) p.table_smem = -1;
-    if (p.settle == 0) p.settle = 16;
+    // settling cap: 8 steps past the prefix (3 past a second-level record)
+    // hands the few long-lived instances to the exact path early
+    if (p.settle == 0) p.settle = 8;
     if (p.partition == 0) p.partition = m.kind == 0 ? 2 : 1;
 }
 

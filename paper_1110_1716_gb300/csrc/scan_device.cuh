@@ -353,6 +353,8 @@ struct Smem {
     uint32_t *marks;                  // WARP_LIST bits: entries sent to the exact path
     uint32_t *wq_start;               // this warp's work queue: absolute starts
     uint16_t *wq_info;                //   and prefix-table entries (WARP_QUEUE)
+    uint32_t *wq_flag;                //   NFA: bit i set = entry i is a second-level
+                                      //   record (continue L2_SYMS symbols later)
     uint32_t *stage;   // this warp's staging buffer
     uint16_t *slots;   // this warp's NFA slots
     uint32_t *coop;    // this warp's two bitsets of Wq words
@@ -726,6 +728,13 @@ static __device__ void nfa_settle_chunk(const MView &mv, const Smem &sm, const T
     }
 }
 
+// Sets or clears the flag of queue entry p (NFA queues: the entry's record is
+// a second-level one). Called by the lane that writes the entry.
+__device__ __forceinline__ void queue_flag(uint32_t *flag, uint32_t p, bool on) {
+    if (on) atomicOr(&flag[p >> 5], 1u << (p & 31));
+    else atomicAnd(&flag[p >> 5], ~(1u << (p & 31)));
+}
+
 // ------------------------------------------------------------ continuation: NFA
 // Warp-cooperative advance of one instance as a bitset over Q (lazy data
 // partitioning: reads the global text once past the staged bytes).
@@ -783,6 +792,8 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
     bool act = false;
     uint32_t start = 0, pos = 0, cnt = 0, cb = 0, mode = MODE_LANE;
     uint32_t pm_left = 0, pm_ptr = 0, cptr = 0;
+    bool l2e = false;                  // this lane's record is a second-level one
+    const uint32_t *rec = sm.pool;     // and the pool holding it
     while (true) {
         const bool need = !act;
         const uint32_t m = __ballot_sync(FULLMASK, need);
@@ -797,24 +808,27 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
                     act = true;
                     mode = MODE_LANE;
                     pm_left = 0;
+                    // a second-level record continues L2_SYMS symbols later
+                    l2e = (sm.wq_flag[qi >> 5] >> (qi & 31)) & 1u;
+                    rec = l2e ? mv.pool2 : sm.pool;
                     if (info == PT_WALK) {
                         SLOT(cb, 0) = static_cast<uint16_t>(mv.q0);
                         cnt = 1;
                         pos = start;
                     } else {
                         const uint32_t ro = info;
-                        const uint32_t w0 = sm.pool[ro];
+                        const uint32_t w0 = rec[ro];
                         const uint32_t nm = w0 & 0xFFFFu, ns = w0 >> 16;
                         pm_left = nm;
                         pm_ptr = ro + 1;
-                        pos = start + mv.k;
+                        pos = start + mv.k + (l2e ? static_cast<uint32_t>(L2_SYMS) : 0u);
                         cnt = ns;
                         if (ns > static_cast<uint32_t>(C)) {
                             mode = MODE_COOP_POOL;
                             cptr = ro + 1 + nm;
                         } else {
                             for (uint32_t i = 0; i < ns; ++i)
-                                SLOT(cb, i) = static_cast<uint16_t>(sm.pool[ro + 1 + nm + i]);
+                                SLOT(cb, i) = static_cast<uint16_t>(rec[ro + 1 + nm + i]);
                         }
                     }
                 }
@@ -827,7 +841,7 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
             const bool has = pm_left > 0;
             uint32_t o = 0, f = 0;
             if (has) {
-                const uint32_t w = sm.pool[pm_ptr];
+                const uint32_t w = rec[pm_ptr];
                 o = w >> 16;
                 f = w & 0xFFFFu;
                 ++pm_ptr;
@@ -898,6 +912,8 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
             const uint32_t ccnt = __shfl_sync(FULLMASK, cnt, src);
             const uint32_t ccb = __shfl_sync(FULLMASK, cb, src);
             const uint32_t cpt = __shfl_sync(FULLMASK, cptr, src);
+            const bool cl2 = __shfl_sync(FULLMASK, l2e ? 1u : 0u, src) != 0;
+            const uint32_t *crec = cl2 ? mv.pool2 : sm.pool;
             uint32_t *b0 = sm.coop, *b1 = sm.coop + mv.Wq;
             for (uint32_t w = lane; w < static_cast<uint32_t>(mv.Wq); w += 32) {
                 b0[w] = 0;
@@ -911,7 +927,7 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
                 }
             } else {
                 for (uint32_t i = lane; i < ccnt; i += 32) {
-                    const uint32_t q = sm.pool[cpt + i];
+                    const uint32_t q = crec[cpt + i];
                     atomicOr(&b0[q >> 5], 1u << (q & 31));
                 }
             }
@@ -972,6 +988,7 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
     const uint32_t mask = (1u << (2 * kk)) - 1;
     const uint32_t *fin = sm.band + mv.Q;
     bool exact = false;
+    bool from_l2 = false;   // the exact path continues from the second-level record
     uint32_t e = PT_SKIP;
     if (p.on) {
         const uint32_t gi = p.g0 & mask;
@@ -983,6 +1000,10 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
             const uint32_t o2 = ldg_u16_keep(
                 mv.l2tab + x * L2_GRAMS + ((p.g0 >> (2 * kk)) & (L2_GRAMS - 1)), pol_keep);
             if (o2 != L2_EMPTY) {
+                // the first-level record has no matches: the exact path can
+                // resume from this one (its matches and its set L2_SYMS later)
+                e = o2;
+                from_l2 = true;
                 const uint32_t *q = mv.pool2 + o2;   // 16 bytes of slack follow the records
                 const uint32_t hdr = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2),
                                w3 = __ldg(q + 3);
@@ -1056,6 +1077,7 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
             const uint32_t at = wq_n + __popc(pm & lanemask_lt());
             sm.wq_start[at] = p.start;
             sm.wq_info[at] = static_cast<uint16_t>(e);
+            queue_flag(sm.wq_flag, at, from_l2);
         }
         wq_n += __popc(pm);
         __syncwarp();
@@ -1166,6 +1188,39 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 live |= keep << (8 * g);
             }
         }
+        // 1b. (lane-local settling kernels) the deep survival bitmap straight
+        //     from each window's keep bits: the eight loads of a window are
+        //     issued together (predicated on the start's bit), their 13-gram
+        //     indices cut from the 32 symbols after the window start, and
+        //     only the starts that pass both bitmaps are compacted below
+        const bool deep_here = DEFER && KIND == 1 && SB == 2 && mv.surv2 != nullptr;
+        if (deep_here && __any_sync(FULLMASK, live != 0)) {
+#pragma unroll
+            for (int g = 0; g < SPT / 8; ++g) {
+                const uint32_t k8 = (live >> (8 * g)) & 0xFFu;
+                if (!__any_sync(FULLMASK, k8 != 0)) continue;
+                const uint32_t iw = wbase + 256u * g;
+                const uint32_t q0 = k8 ? pk_gram(sm.pk, iw - b) : 0u;
+                const uint32_t q1 = k8 ? pk_gram(sm.pk, iw - b + 16) : 0u;
+                // starts whose m2-gram would pass the end of the text are
+                // kept without a lookup (only near the end of the text)
+                const uint32_t look = iw + 7 + m2 <= n ? k8
+                                    : k8 & (iw + m2 > n ? 0u : (2u << (n - iw - m2)) - 1u);
+                uint32_t word[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    word[r] = 0xFFFFFFFFu;   // no lookup: kept
+                    if ((look >> r) & 1u) {
+                        const uint32_t i2 = __funnelshift_r(q0, q1, 2 * r) & m2mask;
+                        word[r] = ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep) >> (i2 & 31);
+                    }
+                }
+                uint32_t d8 = 0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) d8 |= (word[r] & 1u) << r;
+                live &= ~((k8 & ~d8) << (8 * g));
+            }
+        }
         // 2. compact the surviving starts into this warp's list: a ballot
         //    per survivor rank when no lane holds more than two, else a
         //    prefix sum over the lanes' counts
@@ -1210,7 +1265,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
         //     or below its own position, so chunks not yet consumed are
         //     intact), so a warp waits for one L2 round trip per group
         //     instead of one per chunk.
-        if (mv.surv2 && total) {
+        if (mv.surv2 && total && !deep_here) {
             uint32_t w = 0;
             for (uint32_t g0 = 0; g0 < total; g0 += 32 * DEEP_GROUP) {
                 uint32_t word[DEEP_GROUP], bit[DEEP_GROUP];
@@ -1298,6 +1353,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                         const uint32_t at = wq_n + __popc(nm & lanemask_lt());
                         sm.wq_start[at] = b + off;
                         sm.wq_info[at] = static_cast<uint16_t>(e);
+                        queue_flag(sm.wq_flag, at, false);
                     }
                     wq_n += __popc(nm);
                     __syncwarp();
@@ -1385,6 +1441,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                     const uint32_t p = wq_n + __popc(pmask & lanemask_lt());
                     sm.wq_start[p] = b + off;
                     sm.wq_info[p] = static_cast<uint16_t>(e);
+                    if (KIND == 1) queue_flag(sm.wq_flag, p, false);
                 }
                 wq_n += __popc(pmask);
                 __syncwarp();
@@ -1403,6 +1460,8 @@ __device__ __forceinline__ Smem smem_regions(uint8_t *base, const ScanArgs &a, i
     s.wq_start = reinterpret_cast<uint32_t *>(base + a.sm_queue) + wid * WARP_QUEUE;
     s.wq_info = reinterpret_cast<uint16_t *>(base + a.sm_queue + nw * WARP_QUEUE * 4) +
                 wid * WARP_QUEUE;
+    s.wq_flag = reinterpret_cast<uint32_t *>(base + a.sm_queue + nw * WARP_QUEUE * 6) +
+                wid * (WARP_QUEUE / 32);
     s.stage = reinterpret_cast<uint32_t *>(base + a.sm_stage) + wid * (4 * a.stage_n);
     s.slots = reinterpret_cast<uint16_t *>(base + a.sm_slots) + wid * (2 * NFA_SLOT * 32);
     s.coop = a.coop_smem ? reinterpret_cast<uint32_t *>(base + a.sm_coop) + wid * 2 * a.Wq

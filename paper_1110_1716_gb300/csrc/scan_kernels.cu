@@ -59,7 +59,9 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     // each staged tile packed to 2-bit symbols, 16 per word (+1 word read past)
     a.pk_words = (a.text_buf + 15) / 16 + 2;
     a.sm_pack = take(nbuf * a.pk_words * 4, 16);
-    a.sm_queue = take(nw * WARP_QUEUE * 6, 16);
+    // queue: starts (uint32), prefix entries (uint16), and one flag bit per
+    // entry (NFA: the entry is a second-level record)
+    a.sm_queue = take(nw * WARP_QUEUE * 6 + nw * (WARP_QUEUE / 8), 16);
     a.sm_stage = take(nw * a.stage_n * 16, 16);
     a.sm_slots = take(has_nfa ? nw * 2 * NFA_SLOT * 32 * 2 : 0, 16);
     // warp-wide NFA bitsets: shared memory when planned, else global scratch
