@@ -876,7 +876,8 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     need.band_bytes = m.kind == 1 ? static_cast<uint32_t>(m.band.size() * 4) : 0;
     // the NFA records are read by every start that reaches settling: shared
     // memory when they fit
-    need.pool_bytes = (m.kind == 1 && m.pool.size() * 4 <= 64 * 1024)
+    need.pool_bytes = ((m.kind == 1 && m.pool.size() * 4 <= 64 * 1024) ||
+                       (m.kind == 0 && m.pool.size() > 1 && m.pool.size() * 4 <= 16 * 1024))
                           ? static_cast<uint32_t>(m.pool.size() * 4) : 0;
     a.settle_steps = m.params.settle > 0 ? m.params.settle : 0;
     need.surv_bytes = static_cast<uint32_t>(m.surv.size() * 4);

@@ -1223,9 +1223,15 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
         }
         // 2. compact the surviving starts into this warp's list: a ballot
         //    per survivor rank when no lane holds more than two, else a
-        //    prefix sum over the lanes' counts
+        //    prefix sum over the lanes' counts. A DFA without survival
+        //    bitmaps keeps every start: its list is implicit, entry j being
+        //    start j of the warp's range.
         uint32_t total = 0;
-        if (__any_sync(FULLMASK, live != 0)) {
+        const bool implicit = KIND == 0 && !sm.surv && !mv.surv2;
+        const uint32_t wfirst = r0 + static_cast<uint32_t>(tid >> 5) * (32u * SPT);   // the warp's range
+        if (implicit) {
+            total = wfirst < own_end ? min(32u * SPT, own_end - wfirst) : 0u;
+        } else if (__any_sync(FULLMASK, live != 0)) {
             if (!__any_sync(FULLMASK, __popc(live) > 2)) {
                 uint32_t x = live;
 #pragma unroll
@@ -1374,7 +1380,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
             uint32_t e = PT_SKIP, off = 0;
             uint32_t r2 = L2_NO_REC;   // second-level record of this lane's start
             if (j < total) {
-                off = sm.list[j];
+                off = implicit ? wfirst - b + j : sm.list[j];
                 e = PT_WALK;
                 if (kk != 0 && b + off + kk <= n) {
                     const uint32_t gram = SB == 2 ? pk_gram(sm.pk, off) : 0u;

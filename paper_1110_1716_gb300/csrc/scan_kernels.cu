@@ -11,6 +11,10 @@ namespace pfsm {
 // text from global memory (chained data partitioning, Sec. III.D.2). Entries
 // are {job, start, pos, state}.
 __global__ void __launch_bounds__(256) carry_dfa(const ScanArgs a) {
+    // launched as a programmatic dependent of the tile kernel: its launch
+    // overlaps the tile kernel's end, and this waits for that kernel to
+    // complete (and its writes to be visible) before the queue is read
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t nc = min(*a.carry_n, a.carry_cap);
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
@@ -42,14 +46,16 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
         o += bytes;
         return r;
     };
+    // table regions are whole 16-byte blocks: they are filled by bulk copies
+    auto r16 = [](uint32_t x) { return (x + 15u) & ~15u; };
     if (a.stage_n == 0) a.stage_n = STAGE;
     a.sm_misc = take(sizeof(Misc), 16);
-    a.sm_memo = take(need.memo_bytes, 16);
+    a.sm_memo = take(r16(need.memo_bytes), 16);
     a.memo_smem = need.memo_bytes > 0;
-    a.sm_tab = take(need.tab_bytes, 16);
-    a.sm_band = take(need.band_bytes, 16);
-    a.sm_pool = take(need.pool_bytes, 16);
-    a.sm_surv = take(need.surv_bytes, 16);
+    a.sm_tab = take(r16(need.tab_bytes), 16);
+    a.sm_band = take(r16(need.band_bytes), 16);
+    a.sm_pool = take(r16(need.pool_bytes), 16);
+    a.sm_surv = take(r16(need.surv_bytes), 16);
     a.band_smem = need.band_bytes > 0;
     a.pool_smem = need.pool_bytes > 0;
     a.sm_list = take(nw * WARP_LIST_BYTES, 16);
@@ -77,8 +83,17 @@ cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint
 }
 
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s) {
-    carry_dfa<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, carry_dfa, a);
 }
 
 int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem, int spt) {

@@ -46,10 +46,31 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
                    a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox};
 
-    if (a.memo_smem) stage_u16(const_cast<uint16_t *>(sm.memo), a.memo, a.memo_n, tid, NT);
-    if (TAB_SMEM) stage_u16(const_cast<uint16_t *>(sm.tab), a.dtab, a.Q * a.S, tid, NT);
-    if (KIND == 1) stage_nfa(smem, a.sm_band, a.sm_pool, a.band_smem ? a.band : nullptr, a.Q,
-                             a.pool_smem ? a.pool : nullptr, a.pool_n, tid, NT);
+    // Tables that go to shared memory as they are (prefix table, DFA table,
+    // NFA band rows, records, survival bitmap) arrive by 1-D bulk copies
+    // that one thread issues, completing on misc->bar[1]. Their device
+    // sections start on 256-byte boundaries and are padded to them, so each
+    // copy is rounded up to whole 16-byte blocks (the shared-memory regions
+    // are rounded up the same way).
+    auto r16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+    const uint32_t b_memo = a.memo_smem ? r16(((a.memo_n + 1) / 2) * 4) : 0u;
+    const uint32_t b_tab = TAB_SMEM ? r16(((static_cast<uint32_t>(a.Q) * a.S + 1) / 2) * 4) : 0u;
+    const uint32_t b_band = KIND == 1 && a.band_smem
+                                ? r16(static_cast<uint32_t>(a.Q + (a.Q + 31) / 32) * 4) : 0u;
+    const uint32_t b_pool = a.pool_smem ? r16(a.pool_n * 4) : 0u;
+    const uint32_t b_surv = a.surv && !a.surv_bytes ? r16(a.surv_words * 4) : 0u;
+    const uint32_t b_all = b_memo + b_tab + b_band + b_pool + b_surv;
+    if (tid == 0 && b_all) {
+        mbar_init(&misc->bar[1], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&misc->bar[1], b_all);
+        if (b_memo) tma_load_1d(smem + a.sm_memo, a.memo, b_memo, &misc->bar[1], pol_keep);
+        if (b_tab) tma_load_1d(smem + a.sm_tab, a.dtab, b_tab, &misc->bar[1], pol_keep);
+        if (b_band) tma_load_1d(smem + a.sm_band, a.band, b_band, &misc->bar[1], pol_keep);
+        if (b_pool) tma_load_1d(smem + a.sm_pool, a.pool, b_pool, &misc->bar[1], pol_keep);
+        if (b_surv) tma_load_1d(smem + a.sm_surv, a.surv, b_surv, &misc->bar[1], pol_keep);
+    }
     if (a.surv && a.surv_bytes) {
         // one byte (0 or 1) per m-gram: word i of the bitmap gives bytes
         // 32 i .. 32 i + 31, written as eight words of four bytes
@@ -58,9 +79,6 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
             const uint32_t nib = (__ldg(a.surv + (i >> 3)) >> (4 * (i & 7))) & 0xFu;
             d[i] = (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
         }
-    } else if (a.surv) {
-        uint32_t *d = reinterpret_cast<uint32_t *>(smem + a.sm_surv);
-        for (uint32_t i = tid; i < a.surv_words; i += NT) d[i] = __ldg(a.surv + i);
     }
 
     if (tid == 0) {
@@ -75,7 +93,20 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
         misc->busy = 0;
         fence_mbar_init();
     }
-    __syncthreads();   // tables staged, barriers initialised
+    __syncthreads();   // barriers initialised, the byte table expanded
+    if (b_all) {
+        // the bulk copies of the tables (bounded wait; on a timeout the
+        // CTA waits once more for them, bounded, and leaves)
+        if (tid == 0 && !mbar_wait_bounded(&misc->bar[1], 0)) misc->abort = 2;
+        __syncthreads();
+        if (misc->abort == 2) {
+            if (tid == 0) {
+                atomicOr(&a.status[1], ERR_TIMEOUT);
+                mbar_wait_bounded(&misc->bar[1], 0);
+            }
+            return;
+        }
+    }
 
     const uint32_t n = a.n;
     const uint32_t nb = a.nbuf;   // staged tile buffers, <= kTileBufs
