@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
         smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
-        Pend no_pend{0u, 0u, 0u, false};
+        Pend no_pend{0u, 0u, 0u, 0u, false};
         process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
                                        static_cast<uint32_t>(M.settle), NC, no_pend);
         __syncwarp();

@@ -973,11 +973,40 @@ __device__ __forceinline__ void drain(const OView &ov, const MView &mv, const Ti
 // from its first-level record. No warp synchronisation inside the pass.
 constexpr int SETTLE_LANE_STATES = 4;
 
+// The same register slot serves DFA scans with a deep bitmap (see
+// dfa_consume): there g0 is the start's prefix entry and g1 its deep-bitmap
+// word as loaded a round earlier, sh the bit of g1 to test.
 struct Pend {
     uint32_t start;   // absolute start
     uint32_t g0, g1;  // symbols start .. start + 15 and start + 16 .. start + 31
+    uint32_t sh;
     bool on;
 };
+
+// DFA scans with a deep survival bitmap: the loads of a round's candidates
+// (the starts that pass the shallow bitmap) are issued into the lanes'
+// registers and consumed one round later, when the next round's filter has
+// hidden their latency. A candidate whose deep bit is set and whose prefix
+// entry is not PT_SKIP goes to the warp queue with that entry.
+template <bool TAB_SMEM, int OUTW>
+__device__ __forceinline__ void dfa_consume(const OView &ov, const MView &mv, const TileView &tv,
+                                            const Smem &sm, Pend &p, uint32_t &wq_n, uint32_t &sn,
+                                            int lane, uint64_t pol_keep) {
+    const bool push = p.on && ((p.g1 >> p.sh) & 1u) && p.g0 != PT_SKIP;
+    p.on = false;
+    const uint32_t pm = __ballot_sync(FULLMASK, push);
+    if (pm) {
+        if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
+            drain<0, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
+        if (push) {
+            const uint32_t at = wq_n + __popc(pm & lanemask_lt());
+            sm.wq_start[at] = p.start;
+            sm.wq_info[at] = static_cast<uint16_t>(p.g0);
+        }
+        wq_n += __popc(pm);
+        __syncwarp();
+    }
+}
 
 template <int KIND, bool TAB_SMEM, int OUTW>
 __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
@@ -1263,6 +1292,40 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 }
             }
             __syncwarp();
+        }
+        // 2b. (DFA, deferred deep filter) the previous round's candidates,
+        //     then this round's loads, left in flight; a round with more
+        //     than 32 candidates takes the steps below instead
+        if (DEFER && KIND == 0 && mv.surv2) {
+            dfa_consume<TAB_SMEM, OUTW>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep);
+            if (total <= 32) {
+                if (static_cast<uint32_t>(lane) < total) {
+                    const uint32_t off = sm.list[lane];
+                    pend.start = b + off;
+                    pend.g0 = PT_WALK;
+                    if (kk != 0 && b + off + kk <= n)
+                        pend.g0 = sm.memo[SB == 2 ? pk_gram(sm.pk, off) & mask
+                                                  : kgram_at<SB>(tv.sm, off, mv.k, mv.sbits, mask)];
+                    pend.g1 = 1u;
+                    pend.sh = 0u;
+                    if (b + off + m2 <= n) {
+                        uint32_t i2;
+                        if (SB == 2) {
+                            i2 = pk_gram(sm.pk, off) & m2mask;
+                        } else if (SB == 8 && m2 <= 4) {
+                            const uint8_t *q = tv.sm + off;
+                            i2 = (q[0] | (q[1] << 8) | (q[2] << 16) | (static_cast<uint32_t>(q[3]) << 24)) & m2mask;
+                        } else {
+                            i2 = gram_at16<SB>(tv.sm, off, m2, mv.sbits, m2mask);
+                        }
+                        pend.g1 = ldg_u32_keep(mv.surv2 + (i2 >> 5), pol_keep);
+                        pend.sh = i2 & 31u;
+                    }
+                    pend.on = true;
+                }
+                __syncwarp();
+                continue;
+            }
         }
         // 3a. deep survival bitmap (global memory, L2 resident). The list is
         //     taken DEEP_GROUP chunks of 32 at a time: every lane first issues

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     };
     uint32_t sn = 0;
     uint32_t wq_n = 0;   // entries in this warp's queue
-    Pend pend{0u, 0u, 0u, false};   // the start this lane holds for lane-local settling
+    Pend pend{0u, 0u, 0u, 0u, false};   // the start this lane holds (lane-local settling,
+                                        // or a DFA candidate whose loads are in flight)
     uint32_t abort_at = ~0u;   // CTA-synchronous form: the tile whose copy failed
 
     if constexpr (PIPE) {
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
             }
             smk.pk = pk_sm + buf * a.pk_words;
             const TileView tv{text_sm + buf * a.text_buf, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT, KIND == 1>(ov, mv, tv, smk, min(b + a.tile, n), wq_n,
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, true>(ov, mv, tv, smk, min(b + a.tile, n), wq_n,
                                                                  sn, bad_symbol, pol_keep,
                                                                  static_cast<uint32_t>(a.settle_steps), NC,
                                                                  pend);
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
                 __syncthreads();
             }
             const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT, KIND == 1>(ov, mv, tv, sm, min(b + a.tile, n), wq_n,
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, true>(ov, mv, tv, sm, min(b + a.tile, n), wq_n,
                                                                  sn, bad_symbol, pol_keep,
                                                                  static_cast<uint32_t>(a.settle_steps), NT,
                                                                  pend);
@@ -252,6 +253,8 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
         if (KIND == 1 && __any_sync(0xffffffffu, pend.on))
             settle_lanes<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep,
                                             static_cast<uint32_t>(a.settle_steps));
+        if (KIND == 0 && __any_sync(0xffffffffu, pend.on))
+            dfa_consume<TAB_SMEM, 3>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep);
         drain<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     }
     stage_flush<3>(sm.stage, sn, ov, 0u, lane);
