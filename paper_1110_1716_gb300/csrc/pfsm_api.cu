@@ -891,6 +891,7 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
     uint32_t smem = 0;
     bool fit = false;
     for (int attempt = 0; attempt < 8 && !fit; ++attempt) {
+        a.surv_bytes = byte_table && need.surv_bytes == (1u << 16);
         smem = layout_smem(a, kmask, threads, need);
         if (smem <= kSmemMax - kSmemStatic) { fit = true; break; }
         // shrink, cheapest loss first: match staging, then table copies
@@ -905,7 +906,6 @@ int plan_scan(pfsm_ctx *ctx, const Machine &m, const uint8_t *text, uint64_t n, 
         else break;
     }
     if (!fit) return PFSM_E_INVAL;
-    a.surv_bytes = byte_table && need.surv_bytes == (1u << 16);
     int occ = max_ctas_per_sm(m.kind, m.sbits, threads, smem, a.tab_smem != 0, spt);
     if (occ <= 0) return PFSM_E_INVAL;
     if (p.ctas_per_sm > 0) occ = std::min(occ, p.ctas_per_sm);

@@ -35,6 +35,11 @@ namespace pfsm {
 
 #define FULLMASK 0xffffffffu
 
+// The dynamic shared memory of the scan kernels (the same array as the
+// kernels' own extern declaration). A 2-gram byte table sits at offset 0 of
+// it, so a gram indexes this array directly.
+extern __shared__ __align__(128) uint8_t pfsm_dyn_smem[];
+
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1149,6 +1154,32 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
         //    r of window g.
         const uint32_t wbase = r0 + static_cast<uint32_t>(tid >> 5) * (32u * SPT) + 8u * lane;
         uint32_t live = 0;
+        // byte alphabets of 256 symbols with a 2-gram byte table, every window
+        // of the round owned and clear of the end of the text: no checks
+        const uint32_t wlast = wbase + 256u * (SPT / 8 - 1);
+        const bool fast = SB == 8 && sm.survb != nullptr && mv.S == 256 && wlast + 8 <= own_end &&
+                          wlast + 8 + mm <= n;
+        if (__all_sync(FULLMASK, fast)) {
+            const uint8_t *tp = tv.sm + (wbase - b);
+#pragma unroll
+            for (int g = 0; g < SPT / 8; ++g) {
+                const uint2 l = *reinterpret_cast<const uint2 *>(tp + 256 * g);
+                const uint32_t x0 = l.x, x1 = l.y;
+                const uint32_t x2 = *reinterpret_cast<const uint32_t *>(tp + 256 * g + 8);
+                uint32_t v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const uint32_t idx = r < 3 ? __byte_perm(x0, 0u, 0x4400 | ((r + 1) << 4) | r)
+                                       : r == 3 ? __byte_perm(x0, x1, 0x0043) & 0xFFFFu
+                                       : r < 7 ? __byte_perm(x1, 0u, 0x4400 | ((r - 3) << 4) | (r - 4))
+                                               : __byte_perm(x1, x2, 0x0043) & 0xFFFFu;
+                    v[r] = pfsm_dyn_smem[idx];
+                }
+                const uint32_t k01 = v[0] | (v[1] << 1), k23 = v[2] | (v[3] << 1);
+                const uint32_t k45 = v[4] | (v[5] << 1), k67 = v[6] | (v[7] << 1);
+                live |= ((k01 | (k23 << 2)) | ((k45 | (k67 << 2)) << 4)) << (8 * g);
+            }
+        } else
 #pragma unroll
         for (int g = 0; g < SPT / 8; ++g) {
             const uint32_t iw = wbase + 256u * g;   // the window's first start
@@ -1188,7 +1219,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                                                    : r == 3 ? __byte_perm(x0, x1, 0x0043) & 0xFFFFu
                                                    : r < 7 ? __byte_perm(x1, 0u, 0x4400 | ((r - 3) << 4) | (r - 4))
                                                            : __byte_perm(x1, x2, 0x0043) & 0xFFFFu;
-                                bit[r] = sm.survb[idx];
+                                bit[r] = pfsm_dyn_smem[idx];   // the table is at offset 0
                             }
                         } else {
 #pragma unroll
