@@ -1123,9 +1123,12 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
 // continuation of every queued instance. All threads of the CTA call this.
 // SPT: starts per thread per filter round (SPT / 8 windows of 8; 8 or 32).
 // NT consumer threads (ids 0 .. NT - 1) call it together.
-// DEFER (single-text NFA kernels): starts past the deep filter are settled
-// lane by lane (settle_lanes) once every lane holds one; `pend` persists
-// across tiles and the caller settles what is left after its last tile.
+// DEFER (the single-text kernels, whose shared-memory layout puts the
+// shallow survival table at offset 0): NFA starts past the deep filter are
+// settled lane by lane (settle_lanes) once every lane holds one, and a DFA
+// round's deep-bitmap loads are consumed a round later (dfa_consume); `pend`
+// persists across tiles and the caller finishes what is left after its
+// last tile.
 template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32, bool DEFER = false>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
@@ -1159,7 +1162,27 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
         const uint32_t wlast = wbase + 256u * (SPT / 8 - 1);
         const bool fast = SB == 8 && sm.survb != nullptr && mv.S == 256 && wlast + 8 <= own_end &&
                           wlast + 8 + mm <= n;
-        if (__all_sync(FULLMASK, fast)) {
+        // 2-bit symbols with a shallow bitmap (single-text kernels: at
+        // offset 0), every window of the round owned and clear of the end
+        const bool fast2 = SB == 2 && DEFER && sm.surv != nullptr && wlast + 8 <= own_end &&
+                           wlast + 8 + mm <= n;
+        if (__all_sync(FULLMASK, fast2)) {
+            const uint32_t *bm = reinterpret_cast<const uint32_t *>(pfsm_dyn_smem);
+#pragma unroll
+            for (int g = 0; g < SPT / 8; ++g) {
+                const uint32_t p2 = pk_gram(sm.pk, wbase - b + 256u * g);
+                uint32_t v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const uint32_t t = p2 >> (2 * r);
+                    const uint32_t w = bm[(t & mmask) >> 5];
+                    v[r] = __funnelshift_r(w, w, t) & 1u;   // rotate bit t mod 32 to bit 0
+                }
+                const uint32_t k01 = v[0] | (v[1] << 1), k23 = v[2] | (v[3] << 1);
+                const uint32_t k45 = v[4] | (v[5] << 1), k67 = v[6] | (v[7] << 1);
+                live |= ((k01 | (k23 << 2)) | ((k45 | (k67 << 2)) << 4)) << (8 * g);
+            }
+        } else if (__all_sync(FULLMASK, fast)) {
             const uint8_t *tp = tv.sm + (wbase - b);
 #pragma unroll
             for (int g = 0; g < SPT / 8; ++g) {

@@ -49,17 +49,16 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
     // table regions are whole 16-byte blocks: they are filled by bulk copies
     auto r16 = [](uint32_t x) { return (x + 15u) & ~15u; };
     if (a.stage_n == 0) a.stage_n = STAGE;
-    // a byte table of 2-grams (64 KB) sits at offset 0: the kernel indexes
-    // the shared array with the gram itself
-    const bool byte_table = a.surv_bytes && need.surv_bytes == (1u << 16);
-    if (byte_table) a.sm_surv = take(need.surv_bytes, 16);
+    // the shallow survival bitmap (or 2-gram byte table) sits at offset 0:
+    // the single-text kernel indexes the shared array with the gram itself
+    if (need.surv_bytes) a.sm_surv = take(r16(need.surv_bytes), 16);
     a.sm_misc = take(sizeof(Misc), 16);
     a.sm_memo = take(r16(need.memo_bytes), 16);
     a.memo_smem = need.memo_bytes > 0;
     a.sm_tab = take(r16(need.tab_bytes), 16);
     a.sm_band = take(r16(need.band_bytes), 16);
     a.sm_pool = take(r16(need.pool_bytes), 16);
-    if (!byte_table) a.sm_surv = take(r16(need.surv_bytes), 16);
+    if (!need.surv_bytes) a.sm_surv = 0;
     a.band_smem = need.band_bytes > 0;
     a.pool_smem = need.pool_bytes > 0;
     a.sm_list = take(nw * WARP_LIST_BYTES, 16);
