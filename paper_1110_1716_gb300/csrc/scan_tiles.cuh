@@ -26,6 +26,10 @@ namespace pfsm {
 template <int KIND, int SB, bool TAB_SMEM, int SPT>
 __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_tiles(const ScanArgs a) {
     constexpr bool PIPE = SPT != 8;
+    // lane-held deferral (NFA settling, DFA deep-bitmap loads): every
+    // single-text kernel but the DFA one for short texts, which keeps its
+    // registers for a third CTA per SM
+    constexpr bool DEFER = KIND == 1 || SPT != 8;
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (PIPE ? (a.nbuf < 2 || a.nbuf > kTileBufs) : a.nbuf != 2) {   // the layout's buffers
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
             }
             smk.pk = pk_sm + buf * a.pk_words;
             const TileView tv{text_sm + buf * a.text_buf, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT, true>(ov, mv, tv, smk, min(b + a.tile, n), wq_n,
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, DEFER>(ov, mv, tv, smk, min(b + a.tile, n), wq_n,
                                                                  sn, bad_symbol, pol_keep,
                                                                  static_cast<uint32_t>(a.settle_steps), NC,
                                                                  pend);
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
                 __syncthreads();
             }
             const TileView tv{tsm, a.text, b, len, n, 0u, 0u};
-            process_tile<KIND, SB, TAB_SMEM, 3, SPT, true>(ov, mv, tv, sm, min(b + a.tile, n), wq_n,
+            process_tile<KIND, SB, TAB_SMEM, 3, SPT, DEFER>(ov, mv, tv, sm, min(b + a.tile, n), wq_n,
                                                                  sn, bad_symbol, pol_keep,
                                                                  static_cast<uint32_t>(a.settle_steps), NT,
                                                                  pend);
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
         if (KIND == 1 && __any_sync(0xffffffffu, pend.on))
             settle_lanes<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep,
                                             static_cast<uint32_t>(a.settle_steps));
-        if (KIND == 0 && __any_sync(0xffffffffu, pend.on))
+        if (KIND == 0 && DEFER && __any_sync(0xffffffffu, pend.on))
             dfa_consume<TAB_SMEM, 3>(ov, mv, tv, sm, pend, wq_n, sn, lane, pol_keep);
         drain<KIND, TAB_SMEM, 3>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
     }
