@@ -185,7 +185,14 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
         }
     }
     if (base + kMinArena > budget) return PFSM_E_INVAL;
-    const uint32_t arena = (budget - base) & ~15u;
+    // the table arena comes first (offset 0: a machine's survival bitmap,
+    // placed first in it, is where the kernels' check-free filter path
+    // expects it); every other region moves up by its size
+    const uint32_t arena = (budget - base) & ~127u;
+    for (uint32_t *o : {&a.sm_misc, &a.sm_memo, &a.sm_tab, &a.sm_band, &a.sm_pool, &a.sm_surv,
+                        &a.sm_list, &a.sm_text, &a.sm_pack, &a.sm_queue, &a.sm_stage, &a.sm_slots,
+                        &a.sm_coop})
+        *o += arena;
     const uint32_t smem = base + arena;
     const int occ = max_units_ctas_per_sm(cls, threads, smem);
     if (occ <= 0) return PFSM_E_INVAL;
@@ -431,7 +438,7 @@ static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bm
         A.job_lo = pl.job_lo[c];
         A.job_hi = pl.job_hi[c];
         A.unit_tiles = pl.unit_tiles[c];
-        A.sm_arena = sh.smem - sh.arena;
+        A.sm_arena = 0;   // the arena is the first region (see class_shape)
         A.unit_counter = b->ctr + c;
         A.jobs = reinterpret_cast<const BatchJob *>(b->dev + b->off_jobs);
         A.machs = reinterpret_cast<const DevMachine *>(b->dev + b->off_machs);

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
 
     uint32_t sn = 0;
     uint32_t wq_n = 0;
+    Pend pend{0u, 0u, 0u, 0u, false};   // held start of the current text (see process_tile)
     bool bad_symbol = false;
     bool aborted = false;
     uint32_t cur_mach = 0xFFFFFFFFu;   // machine whose tables the arena holds
@@ -247,6 +248,14 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     auto drain_prev = [&]() {
         const MView pmv = mview_of(A.machs[prev.mach]);
         const TileView ptv{text_sm, prev.text, 0u, 0u, prev.n, prev.job, prev.orig};
+        // the starts this warp still holds for the previous text (lane-local
+        // settling, deferred deep-bitmap loads) go first: the arena still
+        // holds that machine's tables
+        if (KIND == 1 && __any_sync(0xffffffffu, pend.on))
+            settle_lanes<KIND, TAB, 4>(prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep,
+                                       static_cast<uint32_t>(A.machs[prev.mach].settle));
+        if (KIND == 0 && __any_sync(0xffffffffu, pend.on))
+            dfa_consume<TAB, 4>(prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep);
         drain<KIND, TAB, 4>(prev_ov, pmv, ptv, smi, wq_n, sn, lane, pol_keep);
         stage_flush<4>(sm.stage, sn, ov, prev.orig, lane);
     };
@@ -300,9 +309,8 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
         smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
-        Pend no_pend{0u, 0u, 0u, 0u, false};
-        process_tile<KIND, SB, TAB, 4>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol, pol_keep,
-                                       static_cast<uint32_t>(M.settle), NC, no_pend);
+        process_tile<KIND, SB, TAB, 4, 32, true>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol,
+                                                 pol_keep, static_cast<uint32_t>(M.settle), NC, pend);
         __syncwarp();
         if (lane == 0) mbar_arrive(&misc->empty[buf]);
         have_prev = true;

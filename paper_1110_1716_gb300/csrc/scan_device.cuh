@@ -1123,12 +1123,11 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
 // continuation of every queued instance. All threads of the CTA call this.
 // SPT: starts per thread per filter round (SPT / 8 windows of 8; 8 or 32).
 // NT consumer threads (ids 0 .. NT - 1) call it together.
-// DEFER (the single-text kernels, whose shared-memory layout puts the
-// shallow survival table at offset 0): NFA starts past the deep filter are
-// settled lane by lane (settle_lanes) once every lane holds one, and a DFA
-// round's deep-bitmap loads are consumed a round later (dfa_consume); `pend`
-// persists across tiles and the caller finishes what is left after its
-// last tile.
+// DEFER: NFA starts past the deep filter are settled lane by lane
+// (settle_lanes) once every lane holds one, and a DFA round's deep-bitmap
+// loads are consumed a round later (dfa_consume); `pend` persists across
+// tiles of one text and the caller finishes what is left (settle_lanes /
+// dfa_consume) before it changes text or machine and after its last tile.
 template <int KIND, int SB, bool TAB_SMEM, int OUTW, int SPT = 32, bool DEFER = false>
 __device__ void process_tile(const OView &ov, const MView &mv, const TileView &tv,
                              const Smem &sm, uint32_t own_end, uint32_t &wq_n, uint32_t &sn,
@@ -1164,8 +1163,8 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                           wlast + 8 + mm <= n;
         // 2-bit symbols with a shallow bitmap (single-text kernels: at
         // offset 0), every window of the round owned and clear of the end
-        const bool fast2 = SB == 2 && DEFER && sm.surv != nullptr && wlast + 8 <= own_end &&
-                           wlast + 8 + mm <= n;
+        const bool fast2 = SB == 2 && sm.surv == reinterpret_cast<const uint32_t *>(pfsm_dyn_smem) &&
+                           wlast + 8 <= own_end && wlast + 8 + mm <= n;
         if (__all_sync(FULLMASK, fast2)) {
             const uint32_t *bm = reinterpret_cast<const uint32_t *>(pfsm_dyn_smem);
 #pragma unroll
