@@ -50,6 +50,10 @@ extern "C" {
                              CTA while none of them was running continuation
                              work (which always ends) */
 #define PFSM_E_CUDA 6     /* a CUDA runtime call failed */
+#define PFSM_E_CHECK 7    /* a device-side bounds check failed: only the checked
+                             build (libpfsm_checked.so, compiled with
+                             PFSM_CHECKED) tests indices; an async status then
+                             has error bit 3 set */
 
 typedef struct pfsm_ctx pfsm_ctx;
 typedef int32_t pfsm_aut;

@@ -19,7 +19,10 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpfsm.so")
+# PFSM_CHECKED=1 in the environment selects the build whose device code tests
+# its data-dependent indices (libpfsm_checked.so; build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "libpfsm_checked.so" if os.environ.get("PFSM_CHECKED") == "1"
+                        else "libpfsm.so")
 
 PFSM_OK = 0
 PFSM_E_INVAL = 1
@@ -28,6 +31,7 @@ PFSM_E_OVERFLOW = 3
 PFSM_E_NOENT = 4
 PFSM_E_TIMEOUT = 5
 PFSM_E_CUDA = 6
+PFSM_E_CHECK = 7
 
 EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nfa",
            "pfsm_evict", "pfsm_unload", "pfsm_set_params", "pfsm_get_params", "pfsm_scan",
@@ -79,8 +83,9 @@ def load_library(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError("libpfsm.so is not built at %s: run "
-                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        raise RuntimeError("%s is not built: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` (the checked "
+                           "build: paper_1110_1716_gb300.build.build(checked=True))" % path)
     lib = ctypes.CDLL(path)
     P, I32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
     sig = {

@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` file is compiled to an object under ``_build/`` in
 parallel, then linked into ``libpfsm.so`` next to this file. Objects and
 the library are rebuilt only when a source or header is newer.
+
+``build(checked=True)`` builds ``libpfsm_checked.so`` the same way (objects
+under ``_build_checked/``) with ``-DPFSM_CHECKED``: device code that tests its
+data-dependent indices and reports a failure as PFSM_E_CHECK. The binding
+loads it when PFSM_CHECKED=1 is set in the environment.
 """
 import concurrent.futures
 import glob
@@ -32,16 +37,20 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    build_dir = os.path.join(HERE, "_build_checked") if checked else BUILD
+    lib_path = os.path.join(HERE, "libpfsm_checked.so") if checked else LIB
+    if checked:
+        extra = tuple(extra) + ("-DPFSM_CHECKED",)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
                glob.glob(os.path.join(INCLUDE, "*.h")))
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     hdr_time = _newest(headers + [__file__])
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_time):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -58,12 +67,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < _newest(objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -250,6 +250,7 @@ struct BatchPlan {
 // every class's texts into work units.
 static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan &pl,
                       cudaStream_t s) {
+    NvtxRange nr("pfsm batch plan");
     ctx->epoch++;
     // machine slot of every job (slots numbered in order of first use)
     std::map<int, uint32_t> slot_of;
@@ -398,6 +399,7 @@ static int graph_for(pfsm_ctx *ctx, BatchState *b, uint32_t mask, cudaGraphExec_
 // b->status (device): [0] total, [1] error bits, [2 + i] count of job i.
 static int batch_enqueue(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, pfsm_bmatch *out,
                          uint64_t cap, cudaStream_t s, BatchState **bs) {
+    NvtxRange nr("pfsm batch (plan, graph launch)");
     BatchPlan pl;
     int st = plan_batch(ctx, jobs, k, pl, s);
     // the pins protect this batch's machines while it is planned; once its

@@ -39,9 +39,10 @@ __device__ __forceinline__ uint32_t find_unit_job(const BatchJob *jobs, uint32_t
     return lo;
 }
 
-__device__ __forceinline__ MView mview_of(const DevMachine &m) {
+__device__ __forceinline__ MView mview_of(const DevMachine &m, unsigned long long *status) {
     return MView{m.Q, m.S, m.q0, m.k, m.sbits, m.Wq, m.surv_m, m.surv2_m, m.surv2, m.dtab, m.off, m.tgt,
-                 m.tail, m.ecl_off, m.ecl_tgt, m.l2tab, m.pool2, m.memox};
+                 m.tail, m.ecl_off, m.ecl_tgt, m.l2tab, m.pool2, m.memox, status, m.pool_n,
+                 m.memo_n};
 }
 
 // Copies `words` 32-bit words (16-byte aligned source and destination).
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     // drains this warp's queue of the previous text (reading it from global
     // memory: its staged tile may be gone) and flushes its staged matches
     auto drain_prev = [&]() {
-        const MView pmv = mview_of(A.machs[prev.mach]);
+        const MView pmv = mview_of(A.machs[prev.mach], A.sa.status);
         const TileView ptv{text_sm, prev.text, 0u, 0u, prev.n, prev.job, prev.orig};
         // the starts this warp still holds for the previous text (lane-local
         // settling, deferred deep-bitmap loads) go first: the arena still
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
                 break;
             }
         }
-        const MView mv = mview_of(M);
+        const MView mv = mview_of(M, A.sa.status);
         const TileView tv{text_sm + buf * A.sa.text_buf, d.text, d.b, d.len, d.n, d.job, d.orig};
         OView ovm = ov;
         if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine

@@ -623,6 +623,7 @@ static DevMachine dev_view(const Machine &m, uint8_t *base) {
 // least recently used machines are evicted in stream order, an image is
 // taken from the pool and the pinned host image is copied in on `s`.
 int make_resident(pfsm_ctx *ctx, int id, Machine &m, cudaStream_t s) {
+    NvtxRange nr("pfsm make_resident");
     m.last_use = ++ctx->clock;
     if (!m.ready && cudaEventCreateWithFlags(&m.ready, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -933,6 +934,7 @@ void collect_timing(pfsm_ctx *ctx, Slot *slot, int keep) {
 
 int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, uint32_t *out,
                  uint64_t cap, unsigned long long *status, Slot *slot, cudaStream_t s) {
+    NvtxRange nr("pfsm scan (plan, tile kernel, carry)");
     auto it = ctx->machines.find(aut);
     if (it == ctx->machines.end()) return PFSM_E_NOENT;
     Machine &m = it->second;
@@ -973,6 +975,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     }
     if (e != cudaSuccess) return PFSM_E_CUDA;
     if (m.kind == 0 && pl.a.carry_cap > 0) {
+        NvtxRange nr("pfsm carry_dfa launch");
         e = launch_carry(pl.a, 2 * ctx->nsm, s);
         if (e != cudaSuccess) return PFSM_E_CUDA;
     }
@@ -986,6 +989,7 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
 
 int finish_status(const unsigned long long *hs, uint64_t cap, uint64_t *n_matches) {
     if (n_matches) *n_matches = hs[0];
+    if (hs[1] & ERR_CHECK) return PFSM_E_CHECK;
     if (hs[1] & ERR_TIMEOUT) return PFSM_E_TIMEOUT;
     if (hs[1] & ERR_SYMBOL) return PFSM_E_INVAL;
     if (hs[0] > cap) return PFSM_E_OVERFLOW;
@@ -1060,6 +1064,7 @@ int pfsm_ctx_destroy(pfsm_ctx *ctx) {
 }
 
 static int finish_load(pfsm_ctx *ctx, Machine &&m, pfsm_aut *out_id) {
+    NvtxRange nr("pfsm load (tables, survival bitmaps, upload)");
     m.sbits = ceil_log2(m.S);
     fill_defaults(m, m.params);
     m.k = m.params.prefix_k < 0 ? 0 : m.params.prefix_k;
@@ -1231,6 +1236,7 @@ int pfsm_load_nfa_eps(pfsm_ctx *ctx, const uint32_t *delta_bits, const uint32_t 
 }
 
 int pfsm_evict(pfsm_ctx *ctx, pfsm_aut aut) {
+    NvtxRange nr("pfsm evict");
     if (!ctx) return PFSM_E_INVAL;
     auto it = ctx->machines.find(aut);
     if (it == ctx->machines.end()) return PFSM_E_NOENT;
@@ -1373,6 +1379,7 @@ const char *pfsm_strerror(int status) {
         case PFSM_E_NOENT: return "unknown automaton id";
         case PFSM_E_TIMEOUT: return "a bounded device wait expired";
         case PFSM_E_CUDA: return "CUDA runtime error";
+        case PFSM_E_CHECK: return "a device bounds check failed (checked build)";
         default: return "unknown status";
     }
 }

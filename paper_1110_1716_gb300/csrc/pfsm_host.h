@@ -7,6 +7,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pfsm_internal.h"
 
 namespace pfsm {
@@ -90,6 +92,16 @@ struct BatchShape {
     int threads = 0, grid = 0;
     uint32_t smem = 0, arena = 0;
     ScanArgs layout{};
+};
+
+// An NVTX range over a scope (load, table build, scan, carry, batch planning
+// and launch, reload, eviction), for timeline profilers; without a profiler
+// attached each push and pop is a call that returns at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 struct DeviceGuard {

@@ -87,6 +87,7 @@ constexpr uint32_t BAND_CSR = 0xFFFFFFFFu;
 // status[0] = match count, status[1] = error bits (ERR_*).
 constexpr unsigned long long ERR_SYMBOL = 1ull;
 constexpr unsigned long long ERR_TIMEOUT = 2ull;
+constexpr unsigned long long ERR_CHECK = 8ull;   // a device bounds check failed (PFSM_CHECKED builds)
 
 constexpr int NFA_SLOT = 8;       // states one lane holds for a small NFA set
 constexpr int STAGE = 128;        // largest per-warp match staging (entries)

@@ -35,6 +35,17 @@ namespace pfsm {
 
 #define FULLMASK 0xffffffffu
 
+// PFSM_CHECKED builds (libpfsm_checked.so) test the data-dependent indices of
+// the device code before they are used: a failing test sets ERR_CHECK in the
+// scan's status (reported as PFSM_E_CHECK) and the access is skipped or made
+// with a safe index instead. Nothing traps. Other builds compile the tests
+// away (PFSM_OK_IDX is then always true).
+#ifdef PFSM_CHECKED
+#define PFSM_OK_IDX(cond, status) ((cond) ? true : (atomicOr(&(status)[1], ERR_CHECK), false))
+#else
+#define PFSM_OK_IDX(cond, status) true
+#endif
+
 // The dynamic shared memory of the scan kernels (the same array as the
 // kernels' own extern declaration). A 2-gram byte table sits at offset 0 of
 // it, so a gram indexes this array directly.
@@ -320,6 +331,8 @@ struct MView {
     const uint16_t *l2tab;  // NFA second-level tables (see L2_SYMS), or null
     const uint32_t *pool2;  // NFA second-level records
     const uint16_t *memox;  // NFA second-level set index per k-gram (with l2tab)
+    unsigned long long *chk;   // status words of the scan (bounds-check failures)
+    uint32_t pool_n, memo_n;   // words of the record pool, entries of the prefix table
 };
 
 // Where matches and carried instances go.
@@ -402,6 +415,7 @@ __device__ __forceinline__ void warp_emit(bool has, uint32_t s, uint32_t e, uint
     if (m == 0) return;
     const uint32_t c = __popc(m);
     if (sn + c > ov.stage_n) stage_flush<OUTW>(buf, sn, ov, tv.orig, lane);
+    if (!PFSM_OK_IDX(sn + c <= ov.stage_n, ov.status)) return;
     if (has) {
         uint32_t *p = buf + OUTW * (sn + __popc(m & lanemask_lt()));
         if (OUTW == 4) *p++ = tv.orig;
@@ -516,7 +530,8 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
                 uint16_t e = DEAD16;
                 if (c < S) {
                     const uint32_t ix = s * S + c;
-                    e = TAB_SMEM ? sm.tab[ix] : ldg_u16_keep(mv.dtab + ix, pol_keep);
+                    if (PFSM_OK_IDX(s < static_cast<uint32_t>(mv.Q), ov.status))
+                        e = TAB_SMEM ? sm.tab[ix] : ldg_u16_keep(mv.dtab + ix, pol_keep);
                 }
                 if (e == DEAD16) {
                     act = false;
@@ -538,6 +553,7 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
 template <class F>
 __device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *band, uint32_t q,
                                             uint32_t c, uint64_t pol_keep, F &&f) {
+    if (!PFSM_OK_IDX(q < static_cast<uint32_t>(mv.Q), mv.chk)) return;
     if (band) {
         const uint32_t row = band[q];
         if (row != BAND_CSR) {
@@ -546,6 +562,7 @@ __device__ __forceinline__ void nfa_targets(const MView &mv, const uint32_t *ban
             while (m) {
                 const uint32_t t = q + __ffs(m);
                 m &= m - 1;
+                if (!PFSM_OK_IDX(t < static_cast<uint32_t>(mv.Q), mv.chk)) break;
                 f(t | (((fin[t >> 5] >> (t & 31)) & 1u) << 15));
             }
             return;
@@ -822,7 +839,7 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
                         pos = start;
                     } else {
                         const uint32_t ro = info;
-                        const uint32_t w0 = rec[ro];
+                        const uint32_t w0 = PFSM_OK_IDX(l2e || ro < mv.pool_n, ov.status) ? rec[ro] : 0u;
                         const uint32_t nm = w0 & 0xFFFFu, ns = w0 >> 16;
                         pm_left = nm;
                         pm_ptr = ro + 1;
@@ -1005,8 +1022,10 @@ __device__ __forceinline__ void dfa_consume(const OView &ov, const MView &mv, co
             drain<0, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
         if (push) {
             const uint32_t at = wq_n + __popc(pm & lanemask_lt());
-            sm.wq_start[at] = p.start;
-            sm.wq_info[at] = static_cast<uint16_t>(p.g0);
+            if (PFSM_OK_IDX(at < static_cast<uint32_t>(WARP_QUEUE), ov.status)) {
+                sm.wq_start[at] = p.start;
+                sm.wq_info[at] = static_cast<uint16_t>(p.g0);
+            }
         }
         wq_n += __popc(pm);
         __syncwarp();
@@ -1027,7 +1046,7 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
     if (p.on) {
         const uint32_t gi = p.g0 & mask;
         const uint32_t x = ldg_u16_keep(mv.memox + gi, pol_keep);
-        e = sm.memo[gi];
+        e = PFSM_OK_IDX(gi < mv.memo_n, ov.status) ? sm.memo[gi] : PT_SKIP;
         if (x == L2_NONE) {
             exact = e != PT_SKIP;
         } else {
@@ -1061,7 +1080,8 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
                         for (int i = 0; i < SETTLE_LANE_STATES; ++i) {
                             const uint32_t qs = i == 0 ? s0 : i == 1 ? s1 : i == 2 ? s2 : s3;
                             if (static_cast<uint32_t>(i) < cnt && !bad) {
-                                const uint32_t row = sm.band[qs];
+                                const uint32_t row = PFSM_OK_IDX(qs < static_cast<uint32_t>(mv.Q), ov.status)
+                                                         ? sm.band[qs] : BAND_CSR;
                                 if (row == BAND_CSR) {
                                     bad = true;
                                 } else {
@@ -1109,9 +1129,11 @@ __device__ void settle_lanes(const OView &ov, const MView &mv, const TileView &t
             drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
         if (exact) {
             const uint32_t at = wq_n + __popc(pm & lanemask_lt());
-            sm.wq_start[at] = p.start;
-            sm.wq_info[at] = static_cast<uint16_t>(e);
-            queue_flag(sm.wq_flag, at, from_l2);
+            if (PFSM_OK_IDX(at < static_cast<uint32_t>(WARP_QUEUE), ov.status)) {
+                sm.wq_start[at] = p.start;
+                sm.wq_info[at] = static_cast<uint16_t>(e);
+                queue_flag(sm.wq_flag, at, from_l2);
+            }
         }
         wq_n += __popc(pm);
         __syncwarp();
@@ -1341,7 +1363,9 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 while (x) {
                     const uint32_t r = __ffs(x) - 1;
                     x &= x - 1;
-                    sm.list[p++] = static_cast<uint16_t>(wbase + 256u * (r >> 3) + (r & 7u) - b);
+                    if (PFSM_OK_IDX(p < static_cast<uint32_t>(WARP_LIST), ov.status))
+                        sm.list[p] = static_cast<uint16_t>(wbase + 256u * (r >> 3) + (r & 7u) - b);
+                    ++p;
                 }
             }
             __syncwarp();
@@ -1471,7 +1495,8 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 if (nm) {
                     if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
                         drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
-                    if (near_end) {
+                    if (near_end && PFSM_OK_IDX(wq_n + __popc(nm & lanemask_lt()) <
+                                                    static_cast<uint32_t>(WARP_QUEUE), ov.status)) {
                         const uint32_t at = wq_n + __popc(nm & lanemask_lt());
                         sm.wq_start[at] = b + off;
                         sm.wq_info[at] = static_cast<uint16_t>(e);
@@ -1506,7 +1531,7 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                     // its set index is read beside the prefix entry
                     const bool l2 = KIND == 1 && SB == 2 && mv.memox && b + off + kk + L2_SYMS <= n;
                     const uint32_t x = l2 ? ldg_u16_keep(mv.memox + gi, pol_keep) : L2_NONE;
-                    e = sm.memo[gi];
+                    e = PFSM_OK_IDX(gi < mv.memo_n, ov.status) ? sm.memo[gi] : PT_SKIP;
                     if (l2 && x != L2_NONE) {
                         const uint32_t o2 = ldg_u16_keep(
                             mv.l2tab + x * L2_GRAMS + ((gram >> (2 * kk)) & (L2_GRAMS - 1)), pol_keep);
@@ -1559,7 +1584,8 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                 // this warp's queue: drain it first when these would not fit
                 if (wq_n + 32 > static_cast<uint32_t>(WARP_QUEUE))
                     drain<KIND, TAB_SMEM, OUTW>(ov, mv, tv, sm, wq_n, sn, lane, pol_keep);
-                if (push) {
+                if (push && PFSM_OK_IDX(wq_n + __popc(pmask & lanemask_lt()) < static_cast<uint32_t>(WARP_QUEUE),
+                                        ov.status)) {
                     const uint32_t p = wq_n + __popc(pmask & lanemask_lt());
                     sm.wq_start[p] = b + off;
                     sm.wq_info[p] = static_cast<uint16_t>(e);

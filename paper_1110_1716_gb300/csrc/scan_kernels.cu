@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) carry_dfa(const ScanArgs a) {
         while (pos < a.n) {
             const uint32_t ch = __ldg(a.text + pos);
             if (ch >= static_cast<uint32_t>(a.S)) break;
+            if (!PFSM_OK_IDX(s < static_cast<uint32_t>(a.Q), a.status)) break;
             const uint16_t e = ldg_u16_keep(a.dtab + s * a.S + ch, pol_keep);
             if (e == DEAD16) break;
             s = e & 0x7FFFu;

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     const uint64_t pol_keep = policy_evict_last();
     const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
     const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
-                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox};
+                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox, a.status, a.pool_n,
+                   a.memo_n};
 
     // Tables that go to shared memory as they are (prefix table, DFA table,
     // NFA band rows, records, survival bitmap) arrive by 1-D bulk copies
