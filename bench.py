@@ -437,7 +437,8 @@ def run_ours(args, rank, world, local_rank):
         others["batch_10k_texts"] = measure_batch(P, pf, torch, dev, hbm, peak_kind,
                                                   cpu=cpu_ok)
     if not args.only:
-        others["long_lived_dfa_16kib"] = measure_partitioning(P, pf, torch, dev)
+        others["long_lived_dfa_16kib"] = measure_partitioning(P, pf, torch, dev, "dfa")
+        others["long_lived_nfa_16kib"] = measure_partitioning(P, pf, torch, dev, "nfa", steps=3)
     if not args.only and not args.no_serve:
         others["serving"] = measure_serving(P, pf, torch, dev)
     if rank != 0:
@@ -499,7 +500,13 @@ def compact_configs(main_name, main, others, detail):
             "frac": r4(b["roofline"]["frac"]), "e2e_gbps": r4(b["e2e"]["value"]),
             "plain_gbps": r4(b["plain_gbps"]), "x_plain": r4(b["speedup_vs_plain"]),
             "cpu_gbps": r4(b["cpu_baseline"]["value"]) if b.get("cpu_baseline") else None,
-            "params_source": b["params_source"], "tuned": b["tuned_batch"]}
+            "params_source": b["params_source"], "tuned": b["tuned_batch"],
+            "default_device_ms": r4(b["default_params_device_ms"]), "device_ms": r4(b["device_ms"])}
+    for key in ("long_lived_dfa_16kib", "long_lived_nfa_16kib"):
+        r = others.get(key)
+        if r:
+            out["f2_" + key] = {"lazy_ms": r4(r["lazy"]["ms"]), "chained_ms": r4(r["chained"]["ms"]),
+                                "matches": r["matches"]}
     sv = others.get("serving")
     if sv:
         out["c4_serving"] = {
@@ -564,34 +571,42 @@ def measure_batch(P, pf, torch, dev, hbm, peak_kind, n_texts=10_000, steps=5, cp
     table = P.job_table(ids[w.job_aut], data.data_ptr() + w.offsets[:-1], lengths)
     total_bytes = int(w.offsets[-1])
     s = torch.cuda.Stream(device=dev)
-    # autotuner: launch shape, then table placement / settling per machine
-    kinds = {int(ids[i]): ("dfa" if hasattr(a, "delta") else "nfa") for i, a in enumerate(w.automata)}
-    t0 = time.perf_counter()
-    tuned = tune.tune_batch(pf.ctx, table, reps=1, stream=s, machines=kinds)
-    tune_s = time.perf_counter() - t0
     st, counts, total = P.pfsm_scan_batch(pf.ctx, table, None, 0)
     out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
     status = torch.zeros(len(table) + 2, dtype=torch.int64, device=dev)
-    P.pfsm_scan_batch_async(pf.ctx, table, out, status, stream=s)   # warm (graph capture)
-    s.synchronize()
-    ms, host_ms = [], []
-    P.pfsm_set_timing(pf.ctx, True)
-    P.pfsm_kernel_time(pf.ctx)   # reset the library's timer
-    for _ in range(steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        h0 = time.perf_counter()
-        P.pfsm_scan_batch_async(pf.ctx, table, out, status, stream=s)
-        host_ms.append((time.perf_counter() - h0) * 1e3)
-        e1.record(s)
+
+    def timed(k):
+        """Whole-call times (ms), host call times (ms) and the graph's mean
+        device time (ms) over k batches, after one untimed batch."""
+        P.pfsm_scan_batch_async(pf.ctx, table, out, status, stream=s)   # warm (graph capture)
         s.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    dev_ms, nlaunch = P.pfsm_kernel_time(pf.ctx)
-    P.pfsm_set_timing(pf.ctx, False)
-    assert int(status[0].item()) == total and int(status[1].item()) == 0
+        ms, host_ms = [], []
+        P.pfsm_set_timing(pf.ctx, True)
+        P.pfsm_kernel_time(pf.ctx)   # reset the library's timer
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            h0 = time.perf_counter()
+            P.pfsm_scan_batch_async(pf.ctx, table, out, status, stream=s)
+            host_ms.append((time.perf_counter() - h0) * 1e3)
+            e1.record(s)
+            s.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        dev_ms, nlaunch = P.pfsm_kernel_time(pf.ctx)
+        P.pfsm_set_timing(pf.ctx, False)
+        assert int(status[0].item()) == total and int(status[1].item()) == 0
+        return ms, host_ms, dev_ms / max(1, nlaunch)
+
+    # the library's default launch shape and placement, for comparison
+    _, _, default_device_ms = timed(steps)
+    # autotuner: launch shape, then table placement / settling per machine
+    kinds = {int(ids[i]): ("dfa" if hasattr(a, "delta") else "nfa") for i, a in enumerate(w.automata)}
+    t0 = time.perf_counter()
+    tuned = tune.tune_batch(pf.ctx, table, reps=3, stream=s, machines=kinds)
+    tune_s = time.perf_counter() - t0
+    ms, host_ms, device_ms = timed(steps)
     batch_ms = float(np.median(ms))
-    device_ms = dev_ms / max(1, nlaunch)
     algo = total_bytes + 16 * int(total)
     # end to end: the concatenated texts from pinned host memory, the batch,
     # the matches back to the host
@@ -643,6 +658,7 @@ def measure_batch(P, pf, torch, dev, hbm, peak_kind, n_texts=10_000, steps=5, cp
            "plain_loop_ms": plain_ms, "plain_gbps": total_bytes / (plain_ms * 1e-3) / 1e9,
            "speedup_vs_plain": plain_ms / batch_ms, "generate_s": gen_s,
            "params_source": "autotuner", "tune_s": tune_s,
+           "default_params_device_ms": default_device_ms,
            "tuned_batch": {"threads": b["threads"], "ctas_per_sm": b["ctas_per_sm"],
                            "tile": b["tile"]},
            "tuned_machines": {str(k): v for k, v in tuned["machines"].items()}}
@@ -651,20 +667,28 @@ def measure_batch(P, pf, torch, dev, hbm, peak_kind, n_texts=10_000, steps=5, cp
     return res
 
 
-def measure_partitioning(P, pf, torch, dev, n=16 << 10, steps=10):
-    """Lazy against chained partitioning (Sec. III.D.2) where every instance
-    lives to the end of the text: a 6-state DFA without a dead state, so the
-    match count grows with n^2 (the paper's worst case)."""
-    d = W.dfa_random(18, Q=6, S=4, dead=-1, finals=[1, 4], p_dead=0.0)
+def measure_partitioning(P, pf, torch, dev, kind="dfa", n=16 << 10, steps=10):
+    """Lazy against chained partitioning (Sec. III.D.2) where instances live
+    to the end of the text, so the match count grows with n^2 (the paper's
+    worst case). DFA: 6 states without a dead state, every instance lives.
+    NFA: a live core of 5 states that every start with symbol 0 enters and
+    never leaves (workloads.live_core_nfa)."""
+    if kind == "dfa":
+        aut = W.dfa_random(18, Q=6, S=4, dead=-1, finals=[1, 4], p_dead=0.0)
+        desc = ("6-state DFA without a dead state, 16 KiB uniform DNA: every instance lives "
+                "to the end of the text")
+    else:
+        aut = W.live_core_nfa(5, 7)
+        desc = ("8-state NFA, live core of 5 states entered on symbol 0, 16 KiB uniform DNA: "
+                "a quarter of the instances live to the end of the text")
     t = W.text_uniform(n, 4, 19)
-    aid = pf.load(d)
+    aid = pf.load(aut)
     tt = pf.to_device(t)
     st, cnt = P.pfsm_scan(pf.ctx, aid, tt, None, None, 0)
     out = torch.empty((int(cnt) + 1024, 3), dtype=torch.int32, device=dev)
     status = torch.zeros(2, dtype=torch.int64, device=dev)
     s = torch.cuda.Stream(device=dev)
-    res = {"desc": "6-state DFA without a dead state, 16 KiB uniform DNA: every instance lives "
-                   "to the end of the text", "bytes": n, "matches": int(cnt)}
+    res = {"desc": desc, "bytes": n, "matches": int(cnt)}
     for name, part in (("lazy", 1), ("chained", 2)):
         P.pfsm_set_params(pf.ctx, aid, {"partition": part, "tile": 4096})
         ms = []

@@ -111,10 +111,13 @@ typedef struct {
                            5); 0 = library default (8), -1 = queue at once */
     int32_t partition;  /* instances alive past their tile's staged text
                            (Sec. III.D.2): 1 = lazy (continue in place on the
-                           global text), 2 = chained (DFA only: hand the
-                           (start, position, state) to a carry queue finished
-                           by a second kernel); 0 = default (DFA chained, NFA
-                           lazy). 2 for an NFA is E_INVAL. */
+                           global text), 2 = chained (hand the instance, a
+                           DFA's (start, position, state) or an NFA's (start,
+                           position, state set), to a carry queue that a
+                           second kernel finishes; when the queue is full the
+                           rest continue in place); 0 = default (DFA chained,
+                           NFA lazy). In pfsm_scan_batch NFA machines are
+                           always lazy. */
 } pfsm_params;
 
 /* Residency counters of a context. */
@@ -321,6 +324,15 @@ int pfsm_aut_bytes(pfsm_ctx *ctx, pfsm_aut aut, uint64_t *bytes, int32_t *reside
  * the context stays usable. Nothing faults or hangs; scans of other forms
  * are unaffected. For tests only. Errors: E_INVAL (NULL ctx). */
 int pfsm_test_hold_tiles(pfsm_ctx *ctx, int32_t enable);
+
+/* Test of a full carry queue (no counterpart in the paper). Caps the carry
+ * queue of later chained single-text scans at `entries` instances and, for
+ * NFAs, its pool at `pool_states` states of sets larger than 8; instances
+ * that find no room continue in place (lazy), as they do when the real
+ * queue fills. 0 restores the library's capacities (2^20 DFA entries;
+ * 2^18 NFA entries and 2^21 pool states); values above them are clamped.
+ * For tests only. Errors: E_INVAL (NULL ctx). */
+int pfsm_test_carry_cap(pfsm_ctx *ctx, uint32_t entries, uint32_t pool_states);
 
 /* Kernel timing: when enabled, every scan records CUDA events around its
  * tile kernel (a batch: around its graph) on the scan's stream;

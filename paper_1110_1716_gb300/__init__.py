@@ -38,7 +38,7 @@ EXPORTS = ("pfsm_ctx_create", "pfsm_ctx_destroy", "pfsm_load_dfa", "pfsm_load_nf
            "pfsm_scan_async", "pfsm_scan_batch", "pfsm_scan_batch_async", "pfsm_set_batch_params", "pfsm_get_stats", "pfsm_set_timing",
            "pfsm_kernel_time", "pfsm_strerror", "pfsm_scan_dfa_noalloc", "pfsm_aut_bytes",
            "pfsm_scan_union", "pfsm_scan_union_async", "pfsm_load_nfa_eps",
-           "pfsm_test_hold_tiles")
+           "pfsm_test_hold_tiles", "pfsm_test_carry_cap")
 
 
 class pfsm_params(ctypes.Structure):
@@ -87,7 +87,7 @@ def load_library(path: str = LIB_PATH):
                            "`python -c 'import __graft_entry__ as g; g.build()'` (the checked "
                            "build: paper_1110_1716_gb300.build.build(checked=True))" % path)
     lib = ctypes.CDLL(path)
-    P, I32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+    P, I32, U32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
     sig = {
         "pfsm_ctx_create": [ctypes.c_int, U64, ctypes.POINTER(P)],
         "pfsm_ctx_destroy": [P],
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "pfsm_get_stats": [P, ctypes.POINTER(pfsm_stats)],
         "pfsm_set_timing": [P, ctypes.c_int],
         "pfsm_test_hold_tiles": [P, I32],
+        "pfsm_test_carry_cap": [P, U32, U32],
         "pfsm_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64)],
         "pfsm_strerror": [ctypes.c_int],
         "pfsm_scan_dfa_noalloc": [P, I32, I32, I32, I32, P, P, U64, P, U64, P, P],
@@ -357,6 +358,11 @@ def pfsm_aut_bytes(ctx: int, aut: int):
 def pfsm_test_hold_tiles(ctx: int, enable: bool) -> None:
     """Test hook for the timeout path (see include/pfsm.h)."""
     _check(load_library().pfsm_test_hold_tiles(ctx, 1 if enable else 0), "pfsm_test_hold_tiles")
+
+
+def pfsm_test_carry_cap(ctx: int, entries: int = 0, pool_states: int = 0) -> None:
+    """Test hook for a full carry queue (see include/pfsm.h)."""
+    _check(load_library().pfsm_test_carry_cap(ctx, entries, pool_states), "pfsm_test_carry_cap")
 
 
 def pfsm_set_timing(ctx: int, enable: bool) -> None:

@@ -214,7 +214,7 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
 static int place_tables(const Machine &m, uint32_t arena, int warps, DevMachine &d) {
     d.a_memo = d.a_tab = d.a_band = d.a_pool = d.a_surv = d.a_coop = kNotStaged;
     d.settle = m.params.settle > 0 ? m.params.settle : 0;
-    d.lazy = m.params.partition == 1 ? 1 : 0;
+    d.lazy = m.params.partition == 1 || m.kind == 1 ? 1 : 0;
     uint32_t used = 0;
     auto take = [&](uint32_t bytes) {
         const uint32_t at = (used + 15) & ~15u;

@@ -307,7 +307,9 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         const MView mv = mview_of(M, A.sa.status);
         const TileView tv{text_sm + buf * A.sa.text_buf, d.text, d.b, d.len, d.n, d.job, d.orig};
         OView ovm = ov;
-        if (M.lazy) ovm.carry_cap = 0;   // lazy partitioning for this machine
+        // lazy partitioning for this machine; NFA machines of a batch are
+        // always lazy (the batch carry queue holds DFA entries only)
+        if (M.lazy || KIND == 1) ovm.carry_cap = 0;
         smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
         process_tile<KIND, SB, TAB, 4, 32, true>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol,

@@ -751,8 +751,7 @@ int validate_params(const Machine &m, const pfsm_params &p) {
     if (p.table_smem < -1 || p.table_smem > 1) return PFSM_E_INVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 8) return PFSM_E_INVAL;
     if (p.settle < -1 || p.settle > 63) return PFSM_E_INVAL;
-    if (p.partition < 0 || p.partition > 2 || (m.kind == 1 && p.partition == 2))
-        return PFSM_E_INVAL;
+    if (p.partition < 0 || p.partition > 2) return PFSM_E_INVAL;
     if (!m.ecl_off.empty() && p.prefix_k == -1) return PFSM_E_INVAL;   // see finish_load
     return PFSM_OK;
 }
@@ -952,14 +951,21 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     pl.a.hold_tiles = ctx->hold_tiles ? 1u : 0u;
     pl.a.carry = slot->carry;
     pl.a.carry_n = slot->carry_n;
-    // lazy partitioning: no carry queue, instances continue in place
-    pl.a.carry_cap = m.params.partition == 1 ? 0u : kCarryCap;
+    // lazy partitioning: no carry queue, instances continue in place.
+    // Chained: the slot's carry buffer holds kCarryCap DFA entries of 4
+    // words, or for an NFA kCarryCap / 4 entries of 8 words followed by a
+    // pool of 2 kCarryCap states for the larger sets
+    pl.a.carry_cap = m.params.partition == 1 ? 0u : m.kind == 0 ? kCarryCap : kCarryCap / 4;
+    pl.a.cpool = m.kind == 1 ? reinterpret_cast<uint16_t *>(slot->carry + 2 * kCarryCap) : nullptr;
+    pl.a.cpool_cap = m.kind == 1 ? 2 * kCarryCap : 0u;
+    if (pl.a.carry_cap && ctx->test_carry_cap) pl.a.carry_cap = std::min(pl.a.carry_cap, ctx->test_carry_cap);
+    if (pl.a.cpool_cap && ctx->test_cpool_cap) pl.a.cpool_cap = std::min(pl.a.cpool_cap, ctx->test_cpool_cap);
     if (m.kind == 1 && !pl.a.coop_smem) {
         const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * m.dm.Wq;
         if (ensure_words(&slot->coop, &slot->coop_words, need)) return PFSM_E_NOMEM;
         pl.a.coop_g = slot->coop;
     }
-    if (m.kind == 0 && cudaMemsetAsync(slot->carry_n, 0, sizeof(uint32_t), s) != cudaSuccess)
+    if (pl.a.carry_cap && cudaMemsetAsync(slot->carry_n, 0, 8 * sizeof(uint32_t), s) != cudaSuccess)
         return PFSM_E_CUDA;
     int ev = -1;
     if (ctx->timing) {
@@ -977,6 +983,10 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     if (m.kind == 0 && pl.a.carry_cap > 0) {
         NvtxRange nr("pfsm carry_dfa launch");
         e = launch_carry(pl.a, 2 * ctx->nsm, s);
+        if (e != cudaSuccess) return PFSM_E_CUDA;
+    } else if (m.kind == 1 && pl.a.carry_cap > 0) {
+        NvtxRange nr("pfsm carry_nfa launch");
+        e = launch_carry_nfa(pl.a, ctx->nsm, std::min(pl.threads, 256), s);
         if (e != cudaSuccess) return PFSM_E_CUDA;
     }
     {
@@ -1358,6 +1368,13 @@ int pfsm_set_timing(pfsm_ctx *ctx, int enable) {
 int pfsm_test_hold_tiles(pfsm_ctx *ctx, int32_t enable) {
     if (!ctx) return PFSM_E_INVAL;
     ctx->hold_tiles = enable != 0;
+    return PFSM_OK;
+}
+
+int pfsm_test_carry_cap(pfsm_ctx *ctx, uint32_t entries, uint32_t pool_states) {
+    if (!ctx) return PFSM_E_INVAL;
+    ctx->test_carry_cap = entries;
+    ctx->test_cpool_cap = pool_states;
     return PFSM_OK;
 }
 

@@ -138,6 +138,7 @@ struct pfsm_ctx {
     std::mutex mu;
     bool timing = false;
     bool hold_tiles = false;   // test hook: scans time out (see pfsm_test_hold_tiles)
+    uint32_t test_carry_cap = 0, test_cpool_cap = 0;   // see pfsm_test_carry_cap
     double time_ms = 0.0;
     uint64_t time_launches = 0;
     // batch executors, one per stream (batch.cu), and their launch shape

@@ -143,10 +143,13 @@ struct ScanArgs {
     uint32_t *out;          // pfsm_match[cap] as words, or pfsm_bmatch
     uint64_t cap;
     unsigned long long *status;
-    // chained-partitioning carry queue (DFA): entries {start, pos, state}
+    // chained-partitioning carry queue: DFA entries {job, start, pos, state},
+    // NFA entries of 8 words (see NFA_CARRY_WORDS) with larger sets in cpool
     uint32_t *carry;
-    uint32_t *carry_n;
-    uint32_t carry_cap;
+    uint32_t *carry_n;      // counters (DFA: [0] entries; NFA: see NFA_CARRY_WORDS)
+    uint32_t carry_cap;     // entries; 0 = lazy partitioning
+    uint16_t *cpool;
+    uint32_t cpool_cap;
     // shared-memory layout (byte offsets into dynamic smem)
     uint32_t sm_memo, sm_tab, sm_text, sm_queue, sm_stage, sm_slots, sm_coop, sm_misc;
     int32_t coop_smem;      // NFA: warp-wide bitsets at sm_coop (else in coop_g)
@@ -161,6 +164,24 @@ struct ScanArgs {
     int32_t settle_steps;   // NFA: settling step cap (0 = no settling)
     int32_t spt;            // starts per thread per filter round: 8 or 32 (0 = 32)
 };
+
+// Dynamic shared memory of the NFA carry kernel with `nw` warps: band rows
+// (when the scan stages them), then per warp the lane slots, the match
+// staging buffer and (when the scan keeps them in shared memory) the two
+// warp-wide bitsets. Fills the four region offsets, returns the bytes.
+inline __host__ __device__ uint32_t carry_nfa_layout(const ScanArgs &a, int nw, uint32_t off[4]) {
+    auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+    uint32_t o = 0;
+    off[0] = o;
+    if (a.band_smem && a.band) o += a16(static_cast<uint32_t>(a.Q + (a.Q + 31) / 32) * 4);
+    off[1] = o;
+    o += a16(static_cast<uint32_t>(nw) * 2 * NFA_SLOT * 32 * 2);
+    off[2] = o;
+    o += a16(static_cast<uint32_t>(nw) * a.stage_n * 16);
+    off[3] = o;
+    if (a.coop_smem) o += a16(static_cast<uint32_t>(nw) * 2 * a.Wq * 4);
+    return o;
+}
 
 // ---- batch executor ------------------------------------------------------
 // Machines of a batch fall into classes, one specialised persistent kernel
@@ -246,6 +267,7 @@ uint32_t layout_smem(ScanArgs &a, int kind_mask, int threads, const SmemNeed &ne
 cudaError_t launch_scan(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,
                         cudaStream_t s);
 cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_carry_nfa(const ScanArgs &a, int grid, int threads, cudaStream_t s);
 int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem, int spt = 32);
 // the kernel instantiated for 8 starts per thread (scan_kernels_spt8.cu)
 cudaError_t launch_scan_spt8(const ScanArgs &a, int kind, int threads, int grid, uint32_t smem,

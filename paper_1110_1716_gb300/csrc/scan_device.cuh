@@ -5,9 +5,10 @@
 // One persistent CTA loops over text tiles. A tile owns the instances that
 // start in [b, b + tile) and stages t[b, b + tile + halo) into shared memory
 // with a 1-D bulk TMA copy (double buffered, evict-first in L2). Instances
-// that are still alive past the staged halo continue on the global text:
-// DFA instances are pushed to a carry queue drained by a second kernel
-// (chained data partitioning, Sec. III.D.2), NFA instances continue in place
+// that are still alive past the staged halo either go to a carry queue that a
+// second kernel continues over the global text (chained data partitioning,
+// Sec. III.D.2: a DFA instance as its start, position and state, an NFA
+// instance as its start, position and state set) or continue in place
 // (lazy data partitioning, same section).
 //
 // Every start i is an instance {(i, q0)} (reinitialisation, Sec. III.B step 1).
@@ -341,11 +342,34 @@ struct OView {
     uint64_t cap;
     unsigned long long *status;       // [0] match count, [1] error bits
     unsigned long long *job_counts;   // per-text counts (batch) or null
-    uint32_t *carry;                  // {job, start, pos, state} entries
-    uint32_t *carry_n;
-    uint32_t carry_cap;
+    uint32_t *carry;                  // DFA: {job, start, pos, state} entries;
+                                      // NFA: NFA_CARRY_WORDS-word entries
+    uint32_t *carry_n;                // DFA: [0] entries. NFA: see NFA_CARRY_WORDS
+    uint32_t carry_cap;               // entries (0: lazy partitioning)
     uint32_t stage_n;                 // per-warp staging capacity (entries)
+    uint16_t *cpool = nullptr;        // NFA: states of carried sets of more than
+    uint32_t cpool_cap = 0;           //   NFA_CARRY_INLINE states
+    // NFA, single text: an instance started at i is carried from the end of
+    // its own tile's staged text, min(n, (i / seg_tile + 1) seg_tile +
+    // seg_halo), or from i + NFA_CARRY_AFTER if that comes first; seg_tile
+    // 0: from the end of the tile staged when it runs
+    uint32_t seg_tile = 0, seg_halo = 0;
 };
+
+// NFA carry queue: entries of 8 words {job, start, pos, n, ...}. The first
+// half of the queue holds the sets a lane held (n <= NFA_CARRY_INLINE states
+// packed two per word in words 4 .. 7; counter carry_n[0], claimed through
+// carry_n[2]); the second half the sets the whole warp held, their states in
+// cpool from the offset in word 4 (counter carry_n[3], claimed through
+// carry_n[4]; carry_n[1] counts cpool states).
+constexpr uint32_t NFA_CARRY_WORDS = 8;
+constexpr uint32_t NFA_CARRY_INLINE = 8;
+// An NFA instance is carried (chained partitioning) when it reaches the end
+// of its tile's staged text or, earlier, NFA_CARRY_AFTER symbols past its
+// start: a long-lived instance then runs in the carry kernel, which spreads
+// such instances over every SM, instead of in the drain of the warp that
+// queued it.
+constexpr uint32_t NFA_CARRY_AFTER = 256;
 
 // One staged tile: bytes [b, b + len) of a text are in shared memory.
 struct TileView {
@@ -758,29 +782,147 @@ __device__ __forceinline__ void queue_flag(uint32_t *flag, uint32_t p, bool on) 
 }
 
 // ------------------------------------------------------------ continuation: NFA
-// Warp-cooperative advance of one instance as a bitset over Q (lazy data
-// partitioning: reads the global text once past the staged bytes).
+// Chained partitioning: one lane hands its instance (n <= NFA_CARRY_INLINE
+// states, FINAL_BIT ignored) to the carry queue. False when the queue is full.
+__device__ __forceinline__ bool carry_nfa_lane(const OView &ov, uint32_t job, uint32_t start,
+                                               uint32_t pos, const uint16_t *st, uint32_t stride,
+                                               uint32_t cnt) {
+    const uint32_t ci = atomicAdd(&ov.carry_n[0], 1u);
+    if (ci >= ov.carry_cap / 2) return false;
+    uint32_t *c = ov.carry + NFA_CARRY_WORDS * ci;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < NFA_CARRY_INLINE; ++i) {
+        const uint32_t v = i < cnt ? (static_cast<uint32_t>(st[i * stride]) & 0x7FFFu) << (16 * (i & 1))
+                                   : 0u;
+        if (i < 2) w0 |= v;
+        else if (i < 4) w1 |= v;
+        else if (i < 6) w2 |= v;
+        else w3 |= v;
+    }
+    reinterpret_cast<uint4 *>(c)[0] = make_uint4(job, start, pos, cnt);
+    reinterpret_cast<uint4 *>(c)[1] = make_uint4(w0, w1, w2, w3);
+    return true;
+}
+
+// The whole warp hands the set in `bits` (a bitset over Q) to the carry
+// queue, its states in cpool. False, with nothing queued, when there is no
+// room (an entry claimed without pool room is written empty).
+static __device__ __noinline__ bool carry_nfa_warp(const OView &ov, const MView &mv, uint32_t job,
+                                                   uint32_t start, uint32_t pos, const uint32_t *bits,
+                                                   int lane) {
+    const uint32_t Wq = mv.Wq;
+    uint32_t mine = 0;
+    for (uint32_t w = lane; w < Wq; w += 32) mine += __popc(bits[w]);
+    uint32_t incl = mine;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULLMASK, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
+    uint32_t ci = 0, po = 0, ok = 0;
+    if (lane == 0) {
+        ci = atomicAdd(&ov.carry_n[3], 1u);
+        if (ci < ov.carry_cap - ov.carry_cap / 2) {
+            po = atomicAdd(&ov.carry_n[1], total);
+            ok = po + total <= ov.cpool_cap && po + total >= po ? 1u : 2u;
+        }
+    }
+    ok = __shfl_sync(FULLMASK, ok, 0);
+    ci = __shfl_sync(FULLMASK, ci, 0);
+    po = __shfl_sync(FULLMASK, po, 0);
+    if (ok == 0) return false;
+    uint32_t *c = ov.carry + NFA_CARRY_WORDS * (ov.carry_cap / 2 + ci);
+    if (ok == 2) {   // an entry without pool room: written empty
+        if (lane == 0) reinterpret_cast<uint4 *>(c)[0] = make_uint4(job, start, pos, 0u);
+        __syncwarp();
+        return false;
+    }
+    uint32_t j = po + incl - mine;
+    for (uint32_t w = lane; w < Wq; w += 32) {
+        uint32_t x = bits[w];
+        while (x) {
+            ov.cpool[j++] = static_cast<uint16_t>(w * 32 + __ffs(x) - 1);
+            x &= x - 1;
+        }
+    }
+    if (lane == 0) {
+        reinterpret_cast<uint4 *>(c)[0] = make_uint4(job, start, pos, total);
+        reinterpret_cast<uint4 *>(c)[1] = make_uint4(po, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    return true;
+}
+
+// Position of the k-th (from 0) set bit of x; k < popc(x).
+__device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t k) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t low = __popc(x & ((1u << w) - 1u));
+        if (k >= low) {
+            k -= low;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Warp-cooperative advance of one instance as a bitset over Q. The states of
+// each 32-word chunk of the set are ranked (a warp scan of the words' bit
+// counts) and lane j steps the states of rank j, j + 32, ..., so a set packed
+// into a few words spreads over the whole warp. At `seg_end` (the end of the
+// instance's own segment) it goes to the carry queue when the scan has one
+// (chained partitioning) and room is left, otherwise it reads the global
+// text on (lazy).
 template <int OUTW>
 __device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
                                       const uint32_t *band, const TileView &tv,
                                       uint32_t *bits0, uint32_t *bits1, uint32_t start,
-                                      uint32_t pos, int lane, uint64_t pol_keep) {
+                                      uint32_t pos, uint32_t seg_end, int lane, uint64_t pol_keep) {
     const uint32_t Wq = mv.Wq, S = mv.S, n = tv.n;
+    // single-text scans only: a batch's NFA machines are always lazy
+    bool chain = OUTW == 3 && ov.carry_cap > 0;
     uint32_t *cur = bits0, *nxt = bits1;
     while (pos < n) {
+        if (OUTW == 3 && chain && pos >= seg_end) {
+            if (carry_nfa_warp(ov, mv, tv.job, start, pos, cur, lane)) break;
+            chain = false;
+        }
         const uint32_t c = text_at(tv, pos);
         if (c >= S) break;
-        for (uint32_t w = lane; w < Wq; w += 32) {
-            uint32_t x = cur[w];
-            while (x) {
-                const uint32_t bit = __ffs(x) - 1;
-                x &= x - 1;
-                nfa_targets(mv, band, w * 32 + bit, c, pol_keep, [&](uint32_t t) {
-                    const uint32_t ts = t & 0x7FFFu;
-                    const uint32_t mb = 1u << (ts & 31);
-                    const uint32_t old = atomicOr(&nxt[ts >> 5], mb);
-                    if ((t & FINAL_BIT) && !(old & mb)) emit_direct<OUTW>(ov, tv.orig, start, pos, ts);
-                });
+        for (uint32_t w0 = 0; w0 < Wq; w0 += 32) {
+            const uint32_t x = w0 + lane < Wq ? cur[w0 + lane] : 0u;
+            const uint32_t cx = __popc(x);
+            uint32_t incl = cx;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULLMASK, incl, d);
+                if (lane >= d) incl += t;
+            }
+            const uint32_t excl = incl - cx;
+            const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
+            for (uint32_t r = 0; r < total; r += 32) {
+                const uint32_t j = r + lane;
+                // the lane holding rank j: the last with excl <= j
+                uint32_t own = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t e = __shfl_sync(FULLMASK, excl, own + step);
+                    if (e <= j) own += step;
+                }
+                const uint32_t xo = __shfl_sync(FULLMASK, x, own);
+                const uint32_t eo = __shfl_sync(FULLMASK, excl, own);
+                if (j < total) {
+                    const uint32_t q = (w0 + own) * 32 + select_bit(xo, j - eo);
+                    nfa_targets(mv, band, q, c, pol_keep, [&](uint32_t t) {
+                        const uint32_t ts = t & 0x7FFFu;
+                        const uint32_t mb = 1u << (ts & 31);
+                        const uint32_t old = atomicOr(&nxt[ts >> 5], mb);
+                        if ((t & FINAL_BIT) && !(old & mb)) emit_direct<OUTW>(ov, tv.orig, start, pos, ts);
+                    });
+                }
             }
         }
         __syncwarp();
@@ -802,36 +944,96 @@ __device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
 enum : uint32_t { MODE_LANE = 0, MODE_COOP_SLOT = 1, MODE_COOP_POOL = 2 };
 
 // Drains the work queue for an NFA: each lane holds one instance's state set
-// (up to NFA_SLOT states) and advances it one symbol per iteration.
-template <int OUTW>
+// (up to NFA_SLOT states) and advances it one symbol per iteration. With
+// CARRY the work is the first half of the carry queue instead (qn entries
+// of lane-held sets, claimed through ov.carry_n[2] by every warp of the carry
+// kernel, at most `claim` at a time, so that a short queue still spreads
+// over every warp).
+enum : uint32_t { REC_POOL = 0, REC_POOL2 = 1 };
+
+template <int OUTW, bool CARRY = false>
 __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, const Smem &sm,
-                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep) {
+                          uint32_t qn, uint32_t &sn, int lane, uint64_t pol_keep,
+                          uint32_t claim = 32) {
     uint32_t head = 0;
     const uint32_t S = mv.S, n = tv.n;
+    // no staged tile (the final drain, the carry kernel): nothing to carry
+    const uint32_t tile_end = tv.len ? tv.b + tv.len : 0xFFFFFFFFu;
     constexpr int C = NFA_SLOT;
+    static_assert(C <= static_cast<int>(NFA_CARRY_INLINE), "a lane's set fits a carry entry");
     uint16_t *slots = sm.slots;
 #define SLOT(sel, i) slots[((sel) * C + (i)) * 32 + lane]
     bool act = false;
+    bool gmode = false;                // past the staged text with the carry queue full
+    bool done = false;                 // CARRY: every entry is claimed
     uint32_t start = 0, pos = 0, cnt = 0, cb = 0, mode = MODE_LANE;
     uint32_t pm_left = 0, pm_ptr = 0, cptr = 0;
+    uint32_t send = 0xFFFFFFFFu;       // end of the instance's own segment
     bool l2e = false;                  // this lane's record is a second-level one
-    const uint32_t *rec = sm.pool;     // and the pool holding it
+    uint32_t rsel = REC_POOL;          // where its record (or carried set) is
+    const uint32_t *rec = sm.pool;
     while (true) {
         const bool need = !act;
         const uint32_t m = __ballot_sync(FULLMASK, need);
-        if (m && head < qn) {
-            const uint32_t base = head;
+        uint32_t base = 0;
+        bool got = false;
+        uint32_t take = __popc(m);
+        if (CARRY) {
+            take = min(take, claim);
+            if (m && !done) {
+                uint32_t b0 = 0;
+                if (lane == 0) b0 = atomicAdd(&ov.carry_n[2], take);
+                base = __shfl_sync(FULLMASK, b0, 0);
+                done = base >= qn;
+                got = !done;
+            }
+        } else if (m && head < qn) {
+            base = head;
             head += __popc(m);
-            if (need) {
-                const uint32_t qi = base + __popc(m & lanemask_lt());
-                if (qi < qn) {
+            got = true;
+        }
+        const uint32_t rank = __popc(m & lanemask_lt());
+        if (got && need && (!CARRY || rank < take)) {
+            const uint32_t qi = base + rank;
+            if (CARRY && qi < qn) {
+                const uint32_t *c = ov.carry + NFA_CARRY_WORDS * qi;
+                const uint4 h = reinterpret_cast<const uint4 *>(c)[0];
+                start = h.y;
+                pos = h.z;
+                cnt = h.w & 0xFFFFu;
+                send = 0xFFFFFFFFu;
+                act = true;
+                gmode = false;
+                mode = MODE_LANE;
+                pm_left = 0;
+                l2e = false;
+                rsel = REC_POOL;
+                const uint4 sw = reinterpret_cast<const uint4 *>(c)[1];
+                if (cnt > static_cast<uint32_t>(C)) cnt = C;
+#pragma unroll
+                for (uint32_t i = 0; i < static_cast<uint32_t>(C); ++i) {
+                    const uint32_t w = i < 2 ? sw.x : i < 4 ? sw.y : i < 6 ? sw.z : sw.w;
+                    if (i < cnt) SLOT(cb, i) = static_cast<uint16_t>(w >> (16 * (i & 1)));
+                }
+            } else if (!CARRY && qi < qn) {
+                {
                     start = sm.wq_start[qi];
                     const uint32_t info = sm.wq_info[qi];
                     act = true;
+                    gmode = false;
+                    // chained: the instance leaves at the end of its own
+                    // tile's staged text, also when a later tile (or the
+                    // final drain) runs it
+                    if (OUTW == 3)
+                        send = ov.seg_tile
+                                   ? min(min(n, (start / ov.seg_tile + 1) * ov.seg_tile + ov.seg_halo),
+                                         start + NFA_CARRY_AFTER)
+                                   : tile_end;
                     mode = MODE_LANE;
                     pm_left = 0;
                     // a second-level record continues L2_SYMS symbols later
                     l2e = (sm.wq_flag[qi >> 5] >> (qi & 31)) & 1u;
+                    rsel = l2e ? REC_POOL2 : REC_POOL;
                     rec = l2e ? mv.pool2 : sm.pool;
                     if (info == PT_WALK) {
                         SLOT(cb, 0) = static_cast<uint16_t>(mv.q0);
@@ -873,6 +1075,16 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
         }
         if (act && mode == MODE_LANE && cnt == 0) act = false;
 
+        // past the staged text: to the carry queue (chained partitioning)
+        // unless the scan is lazy or the queue is full (single-text scans
+        // only: a batch's NFA machines are always lazy)
+        if (OUTW == 3 && act && pos < n && pos >= send && ov.carry_cap && !gmode) {
+            if (mode == MODE_LANE) {
+                if (carry_nfa_lane(ov, tv.job, start, pos, &SLOT(cb, 0), 32, cnt)) act = false;
+                else gmode = true;
+            }
+        }
+
         // one symbol for every lane-held instance
         bool anyfin = false;
         if (act && mode == MODE_LANE) {
@@ -911,8 +1123,9 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
                 }
             }
         }
-        if (__any_sync(FULLMASK, anyfin)) {
-            for (uint32_t j = 0; j < static_cast<uint32_t>(C); ++j) {
+        const uint32_t fin_n = __reduce_max_sync(FULLMASK, anyfin ? cnt : 0u);
+        if (fin_n) {
+            for (uint32_t j = 0; j < fin_n; ++j) {
                 const bool has = anyfin && j < cnt && (SLOT(cb, j) & FINAL_BIT);
                 warp_emit<OUTW>(has, start, pos, has ? (SLOT(cb, j) & 0x7FFFu) : 0u, sm.stage,
                                 sn, ov, tv, lane);
@@ -934,8 +1147,10 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
             const uint32_t ccnt = __shfl_sync(FULLMASK, cnt, src);
             const uint32_t ccb = __shfl_sync(FULLMASK, cb, src);
             const uint32_t cpt = __shfl_sync(FULLMASK, cptr, src);
-            const bool cl2 = __shfl_sync(FULLMASK, l2e ? 1u : 0u, src) != 0;
-            const uint32_t *crec = cl2 ? mv.pool2 : sm.pool;
+            const uint32_t cse = OUTW == 3 ? __shfl_sync(FULLMASK, gmode ? 0xFFFFFFFFu : send, src)
+                                           : 0xFFFFFFFFu;
+            const uint32_t csel = __shfl_sync(FULLMASK, rsel, src);
+            const uint32_t *crec = csel == REC_POOL2 ? mv.pool2 : sm.pool;
             uint32_t *b0 = sm.coop, *b1 = sm.coop + mv.Wq;
             for (uint32_t w = lane; w < static_cast<uint32_t>(mv.Wq); w += 32) {
                 b0[w] = 0;
@@ -950,11 +1165,12 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
             } else {
                 for (uint32_t i = lane; i < ccnt; i += 32) {
                     const uint32_t q = crec[cpt + i];
+                    if (!PFSM_OK_IDX(q < static_cast<uint32_t>(mv.Q), ov.status)) continue;
                     atomicOr(&b0[q >> 5], 1u << (q & 31));
                 }
             }
             __syncwarp();
-            coop_run<OUTW>(ov, mv, sm.band, tv, b0, b1, cs, cp, lane, pol_keep);
+            coop_run<OUTW>(ov, mv, sm.band, tv, b0, b1, cs, cp, cse, lane, pol_keep);
             if (lane == src) {
                 act = false;
                 mode = MODE_LANE;

@@ -1,7 +1,7 @@
 // PFSM single-text scan kernels for sm_103a: one persistent CTA per SM loops
 // over the tiles of one text (the device building blocks are in
-// scan_device.cuh), plus the carry kernel that finishes DFA instances past
-// their tile, and the shared-memory layout and launch helpers.
+// scan_device.cuh), plus the carry kernels that finish DFA and NFA instances
+// past their tile, and the shared-memory layout and launch helpers.
 #include "scan_tiles.cuh"
 
 namespace pfsm {
@@ -34,6 +34,83 @@ __global__ void __launch_bounds__(256) carry_dfa(const ScanArgs a) {
             ++pos;
         }
     }
+}
+
+// ------------------------------------------------------------ NFA carry queue
+// Continues NFA instances that outlived their segment (chained data
+// partitioning, Sec. III.D.2: the live instance, its start as the tag and its
+// state set, passes to the next stage), on the global text to its end. Sets
+// that the whole warp held (the second half of the queue) are claimed one
+// per warp and run as bitsets over Q; then the lane-held sets (the first
+// half) by the exact path's lane refill, one instance per lane. Shared
+// memory: band rows (when the scan staged them), then per warp the lane
+// slots, the match staging buffer and, when the scan keeps them in shared
+// memory, the two warp-wide bitsets.
+__global__ void __launch_bounds__(256, 1) carry_nfa(const ScanArgs a) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    uint32_t off[4];
+    carry_nfa_layout(a, nw, off);
+    const uint32_t half = a.carry_cap / 2;
+    const uint32_t n_lane = min(a.carry_n[0], half);
+    const uint32_t n_warp = min(a.carry_n[3], a.carry_cap - half);
+    if (n_lane == 0 && n_warp == 0) return;
+    const uint64_t pol_keep = policy_evict_last();
+    // nothing is carried again: the carried instances run to the end
+    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, 0u, a.stage_n,
+                   a.cpool, a.cpool_cap};
+    const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
+                   a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox, a.status, a.pool_n,
+                   a.memo_n};
+    Smem sm = {};
+    if (a.band_smem && a.band) {
+        uint32_t *b = reinterpret_cast<uint32_t *>(smem + off[0]);
+        const uint32_t words = static_cast<uint32_t>(a.Q + (a.Q + 31) / 32);
+        for (uint32_t i = tid; i < words; i += blockDim.x) b[i] = __ldg(a.band + i);
+        sm.band = b;
+    } else {
+        sm.band = a.band;
+    }
+    __syncthreads();
+    sm.pool = a.pool;
+    sm.slots = reinterpret_cast<uint16_t *>(smem + off[1]) + wid * (2 * NFA_SLOT * 32);
+    sm.stage = reinterpret_cast<uint32_t *>(smem + off[2]) + wid * (4 * a.stage_n);
+    sm.coop = a.coop_smem ? reinterpret_cast<uint32_t *>(smem + off[3]) + wid * 2 * a.Wq
+            : a.coop_g ? a.coop_g + (static_cast<size_t>(blockIdx.x) * nw + wid) * 2 * a.Wq
+                       : nullptr;
+    const TileView tv{nullptr, a.text, 0u, 0u, a.n, 0u, 0u};
+    // 1. warp-held sets, one per warp
+    if (sm.coop) {
+        uint32_t *b0 = sm.coop, *b1 = sm.coop + a.Wq;
+        while (true) {
+            uint32_t idx = 0;
+            if (lane == 0) idx = atomicAdd(&a.carry_n[4], 1u);
+            idx = __shfl_sync(FULLMASK, idx, 0);
+            if (idx >= n_warp) break;
+            const uint4 h = *reinterpret_cast<const uint4 *>(a.carry + NFA_CARRY_WORDS * (half + idx));
+            const uint32_t po = a.carry[NFA_CARRY_WORDS * (half + idx) + 4];
+            for (uint32_t w = lane; w < static_cast<uint32_t>(a.Wq); w += 32) {
+                b0[w] = 0;
+                b1[w] = 0;
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < h.w; i += 32) {
+                const uint32_t q = a.cpool[po + i];
+                if (!PFSM_OK_IDX(q < static_cast<uint32_t>(a.Q), a.status)) continue;
+                atomicOr(&b0[q >> 5], 1u << (q & 31));
+            }
+            __syncwarp();
+            coop_run<3>(ov, mv, sm.band, tv, b0, b1, h.y, h.z, 0xFFFFFFFFu, lane, pol_keep);
+        }
+    }
+    // 2. lane-held sets
+    uint32_t sn = 0;
+    // entries per claim: the lane-held sets spread over every warp of the grid
+    const uint32_t warps = gridDim.x * nw;
+    const uint32_t claim = min(32u, max(1u, (n_lane + warps - 1) / warps));
+    if (n_lane) drain_nfa<3, true>(ov, mv, tv, sm, n_lane, sn, lane, pol_keep, claim);
+    stage_flush<3>(sm.stage, sn, ov, 0u, lane);
 }
 
 // ------------------------------------------------------------ host helpers
@@ -98,6 +175,26 @@ cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, carry_dfa, a);
+}
+
+cudaError_t launch_carry_nfa(const ScanArgs &a, int grid, int threads, cudaStream_t s) {
+    uint32_t off[4];
+    const uint32_t smem = carry_nfa_layout(a, threads / 32, off);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(carry_nfa, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, carry_nfa, a);
 }
 
 int max_ctas_per_sm(int kind, int sbits, int threads, uint32_t smem, bool tab_smem, int spt) {

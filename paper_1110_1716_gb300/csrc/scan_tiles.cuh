@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
     uint32_t *pk_sm = reinterpret_cast<uint32_t *>(smem + a.sm_pack);
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
-    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
+    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n,
+                   a.cpool, a.cpool_cap, KIND == 1 ? a.tile : 0u, a.halo};
     const MView mv{a.Q, a.S, a.q0, a.k, a.sbits, a.Wq, a.surv_m, a.surv2_m, a.surv2, a.dtab, a.off, a.tgt,
                    a.tail, a.ecl_off, a.ecl_tgt, a.l2tab, a.pool2, a.memox, a.status, a.pool_n,
                    a.memo_n};

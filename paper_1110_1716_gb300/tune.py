@@ -114,8 +114,10 @@ def time_params(ctx: int, aut: int, text, out, status, params: dict, reps: int =
     return float(np.median(times))
 
 
-def _descend(start: dict, ax: Dict[str, list], timer, sweeps: int = 2):
-    """Coordinate descent: returns (best params, best ms, evaluations)."""
+def _descend(start: dict, ax: Dict[str, list], timer, sweeps: int = 2, gain: float = 0.99):
+    """Coordinate descent: returns (best params, best ms, evaluations). A
+    candidate replaces the best when it takes less than `gain` times its
+    time."""
     best = dict(start)
     best_ms = timer(best)
     if best_ms is None:
@@ -133,7 +135,7 @@ def _descend(start: dict, ax: Dict[str, list], timer, sweeps: int = 2):
                 ms = timer(p)
                 evals += 1
                 seen[key] = ms if ms is not None else float("inf")
-                if ms is not None and ms < best_ms * 0.99:
+                if ms is not None and ms < best_ms * gain:
                     best, best_ms, moved = p, ms, True
         if not moved:
             break
@@ -191,21 +193,28 @@ def _time_batch(ctx, jobs, out, status, stream, reps) -> Optional[float]:
     return float(np.median(times))
 
 
-def tune_batch(ctx: int, jobs, reps: int = 2, stream=None, machines: Optional[dict] = None,
-               sweeps: int = 1) -> dict:
+def tune_batch(ctx: int, jobs, reps: int = 3, stream=None, machines: Optional[dict] = None,
+               sweeps: int = 1, warmup: int = 5, gain: float = 0.97) -> dict:
     """Pick the batch launch shape and per-machine placement for a
     representative batch `jobs` ([(aut, text_tensor, n), ...] or a job
     table) on the current CUDA device by timing
-    each candidate with CUDA events. `machines` maps each automaton id of
-    the batch to "dfa" or "nfa" (its per-machine axes are searched; omit it
-    to tune the launch shape only). Sets the fastest and returns
-    {"batch": shape, "machines": {aut: params}, "ms": time}."""
+    each candidate with CUDA events (the median of `reps` runs after one
+    untimed run; the batch runs `warmup` times first, so that the first
+    candidate does not pay for the GPU's clocks ramping up). A candidate
+    must beat the best so far by 1 - `gain` (3 %) to replace it. `machines`
+    maps each automaton id of the batch to "dfa" or "nfa" (its per-machine
+    axes are searched; omit it to tune the launch shape only). Sets the
+    fastest and returns {"batch": shape, "machines": {aut: params}, "ms":
+    time}."""
     import torch
     stream = stream or torch.cuda.current_stream()
     st, counts, total = pfsm_scan_batch(ctx, jobs, None, 0)
     dev = torch.device("cuda", torch.cuda.current_device())
     out = torch.empty((int(total) + 1024, 4), dtype=torch.int32, device=dev)
     status = torch.zeros(len(jobs) + 2, dtype=torch.int64, device=dev)
+    for _ in range(warmup):
+        pfsm_scan_batch_async(ctx, jobs, out, status, stream=stream)
+    stream.synchronize()
 
     # 1. launch shape: threads x CTAs per SM, then the tile
     def shape_timer(p):
@@ -223,7 +232,7 @@ def tune_batch(ctx: int, jobs, reps: int = 2, stream=None, machines: Optional[di
         return {"threads": threads, "ctas_per_sm": ctas, "tile": p["tile"]}
 
     best, best_ms, _ = _descend({"shape": (0, 0), "tile": 16384}, shape_axes,
-                                lambda p: shape_timer(shape_params(p)), sweeps)
+                                lambda p: shape_timer(shape_params(p)), sweeps, gain)
     shape = shape_params(best)
     pfsm_set_batch_params(ctx, shape)
 
@@ -242,7 +251,7 @@ def tune_batch(ctx: int, jobs, reps: int = 2, stream=None, machines: Optional[di
             except Exception:
                 continue
             ms = _time_batch(ctx, jobs, out, status, stream, reps)
-            if ms is not None and ms < best_v_ms * 0.99:
+            if ms is not None and ms < best_v_ms * gain:
                 best_v, best_v_ms = v, ms
         pfsm_set_params(ctx, aut, dict(cur, **{name: best_v}))
         best_ms = min(best_ms, best_v_ms)

@@ -282,11 +282,71 @@ def test_lazy_and_chained_partitioning(pf, partition):
     assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
 
 
-def test_nfa_partition_is_lazy_only(pf):
+def test_nfa_partition_default_is_lazy(pf):
     a = pf.load(W.eps_free(W.fig1_union()))
     assert P.pfsm_get_params(pf.ctx, a)["partition"] == 1
+    P.pfsm_set_params(pf.ctx, a, {"partition": 2})
+    assert P.pfsm_get_params(pf.ctx, a)["partition"] == 2
     with pytest.raises(P.PfsmError):
-        P.pfsm_set_params(pf.ctx, a, {"partition": 2})
+        P.pfsm_set_params(pf.ctx, a, {"partition": 3})
+
+
+@pytest.mark.parametrize("partition", [1, 2])
+@pytest.mark.parametrize("K", [5, 24])
+@pytest.mark.parametrize("spt", [8, 32])
+def test_nfa_lazy_and_chained_partitioning(pf, partition, K, spt):
+    """Sec. III.D.2 for NFAs on instances that never die. Chained: a live
+    instance leaves its tile as (start, position, state set), inline for a
+    core of 5 states (sets of at most 8 held by one lane), in the carry pool
+    for a core of 24 (sets run by the whole warp), and the carry kernel
+    continues it; lazy: it continues in place on the global text."""
+    m = W.live_core_nfa(K, 7)
+    a = pf.load(m)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "spt": spt, "partition": partition})
+    t = W.text_uniform(6000, 4, 11)
+    want = oracle.scan(m, t)
+    assert len(want) > 200_000
+    assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
+
+
+@pytest.mark.parametrize("K", [5, 24])
+def test_nfa_chained_partitioning_with_a_full_carry_queue(pf, K):
+    """A carry queue of 100 entries and a pool of 64 states: the instances
+    that find no room (entries or pool) continue in place, and the match set
+    is unchanged."""
+    m = W.live_core_nfa(K, 8)
+    a = pf.load(m)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "partition": 2})
+    t = W.text_uniform(9000, 4, 12)
+    want = oracle.scan(m, t)
+    P.pfsm_test_carry_cap(pf.ctx, 100, 64)
+    try:
+        got = gpu_matches(pf, a, t, cap=len(want) + 16)
+    finally:
+        P.pfsm_test_carry_cap(pf.ctx, 0, 0)
+    assert np.array_equal(got, want)
+
+
+def test_nfa_chained_partitioning_on_cyclic_sets(pf):
+    """Random cyclic NFAs (sets grow and shrink; seeds picked so that
+    thousands of matches come from instances that crossed the first tile's
+    end) chained against the oracle, one of them following epsilon edges at
+    run time."""
+    for seed in (102, 109, 110, 126):
+        rng = np.random.default_rng(seed)
+        Q, S = 12 + (seed % 4) * 4, 4
+        edges = [(q, x, u) for q in range(Q) for x in range(S) for u in range(Q)
+                 if rng.random() < 0.06]
+        eps = [(q, u) for q in range(Q) for u in range(Q) if q != u and rng.random() < 0.03]
+        with_eps = seed % 2 == 1
+        m = W.nfa_from_edges(Q, S, 0, edges, [3], eps_edges=eps if with_eps else ())
+        a = pf.load(m)
+        P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "partition": 2})
+        t = W.text_uniform(4800, 4, seed)
+        want = oracle.scan(W.eps_free(m) if with_eps else m, t)
+        assert ((want[:, 0] < 4096) & (want[:, 1] >= 4112)).sum() > 2000, seed
+        assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want), seed
+        P.pfsm_unload(pf.ctx, a)
 
 
 def test_eviction_and_reload(pf):

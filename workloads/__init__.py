@@ -103,6 +103,26 @@ def nfa_from_edges(Q: int, S: int, q0: int, edges, finals, eps_edges=(),
     return Nfa(bits=bits, q0=q0, final=fin, eps=eps, labels=labels)
 
 
+def live_core_nfa(K: int, seed: int, p: float = 0.3) -> Nfa:
+    """An NFA whose instances that start with symbol 0 never die: q0 --0-->
+    a core of K states (1..K) in which every state has a successor on every
+    symbol, plus random extra edges with probability p (the live set fills
+    most of the core); core state 1 --1--> G --2--> F, the only final state,
+    which has no successors. Over uniform DNA each live instance reports at
+    about one position in 16: some n^2 / 128 matches for a text of n
+    symbols, nearly all from instances that run far past their start."""
+    rng = np.random.default_rng(seed)
+    S = 4
+    G, F = K + 1, K + 2
+    edges = [(0, 0, 1)]
+    for q in range(1, K + 1):
+        for x in range(S):
+            ts = {int(rng.integers(1, K + 1))} | {t for t in range(1, K + 1) if rng.random() < p}
+            edges += [(q, x, t) for t in ts]
+    edges += [(1, 1, G), (G, 2, F)]
+    return nfa_from_edges(K + 3, S, 0, edges, [F])
+
+
 def dfa_as_nfa(d: Dfa) -> Nfa:
     """The same machine with delta returning singletons (dead edges dropped)."""
     edges = []
