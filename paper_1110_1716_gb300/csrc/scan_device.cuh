@@ -465,6 +465,41 @@ __device__ __forceinline__ void emit_direct(const OView &ov, uint32_t orig, uint
     }
 }
 
+// The matches of prefix records: lane l reports its n_l record entries
+// (step << 16 | final, from rec[ptr]) for start `start`. One warp prefix sum
+// over n_l places every lane's matches in the staging buffer (flushed when
+// full), instead of one ballot per match.
+template <int OUTW>
+__device__ __forceinline__ void emit_record_matches(uint32_t n_l, const uint32_t *rec, uint32_t ptr,
+                                                    uint32_t start, uint32_t *buf, uint32_t &sn,
+                                                    const OView &ov, const TileView &tv, int lane) {
+    uint32_t incl = n_l;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULLMASK, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULLMASK, incl, 31);
+    const uint32_t excl = incl - n_l;
+    uint32_t done = 0;   // ranks below this are staged (warp-uniform)
+    while (done < total) {
+        if (sn >= ov.stage_n) stage_flush<OUTW>(buf, sn, ov, tv.orig, lane);
+        const uint32_t hi = min(total, done + (ov.stage_n - sn));
+        const uint32_t a = max(excl, done), z = min(excl + n_l, hi);
+        for (uint32_t r = a; r < z; ++r) {
+            const uint32_t w = rec[ptr + (r - excl)];
+            uint32_t *p = buf + OUTW * (sn + (r - done));
+            if (OUTW == 4) *p++ = tv.orig;
+            p[0] = start;
+            p[1] = start + (w >> 16);
+            p[2] = w & 0xFFFFu;
+        }
+        sn += hi - done;
+        done = hi;
+    }
+    __syncwarp();
+}
+
 // ------------------------------------------------------------ continuation: DFA
 // Drains the work queue with lane refill: one symbol per lane per iteration.
 template <bool TAB_SMEM, int OUTW>
@@ -513,17 +548,9 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
                 }
             }
         }
-        while (__any_sync(FULLMASK, pm_left > 0)) {
-            const bool has = pm_left > 0;
-            uint32_t o = 0, f = 0;
-            if (has) {
-                const uint32_t w = sm.pool[pm_ptr];
-                o = w >> 16;
-                f = w & 0xFFFFu;
-                ++pm_ptr;
-                --pm_left;
-            }
-            warp_emit<OUTW>(has, start, start + o, f, sm.stage, sn, ov, tv, lane);
+        if (__any_sync(FULLMASK, pm_left > 0)) {
+            emit_record_matches<OUTW>(pm_left, sm.pool, pm_ptr, start, sm.stage, sn, ov, tv, lane);
+            pm_left = 0;
         }
         if (!__any_sync(FULLMASK, act)) {
             if (head >= qn) break;
@@ -1061,17 +1088,9 @@ __device__ void drain_nfa(const OView &ov, const MView &mv, const TileView &tv, 
         if (!__any_sync(FULLMASK, act)) break;
 
         // matches inside the first k steps, from the prefix record
-        while (__any_sync(FULLMASK, pm_left > 0)) {
-            const bool has = pm_left > 0;
-            uint32_t o = 0, f = 0;
-            if (has) {
-                const uint32_t w = rec[pm_ptr];
-                o = w >> 16;
-                f = w & 0xFFFFu;
-                ++pm_ptr;
-                --pm_left;
-            }
-            warp_emit<OUTW>(has, start, start + o, f, sm.stage, sn, ov, tv, lane);
+        if (__any_sync(FULLMASK, pm_left > 0)) {
+            emit_record_matches<OUTW>(pm_left, rec, pm_ptr, start, sm.stage, sn, ov, tv, lane);
+            pm_left = 0;
         }
         if (act && mode == MODE_LANE && cnt == 0) act = false;
 
@@ -1777,18 +1796,8 @@ __device__ void process_tile(const OView &ov, const MView &mv, const TileView &t
                         e = PT_SKIP;
                     }
                 }
-                while (__any_sync(FULLMASK, pm_left > 0)) {
-                    const bool has = pm_left > 0;
-                    uint32_t o = 0, f = 0;
-                    if (has) {
-                        const uint32_t w = sm.pool[pm_ptr];
-                        o = w >> 16;
-                        f = w & 0xFFFFu;
-                        ++pm_ptr;
-                        --pm_left;
-                    }
-                    warp_emit<OUTW>(has, b + off, b + off + o, f, sm.stage, sn, ov, tv, lane);
-                }
+                if (__any_sync(FULLMASK, pm_left > 0))
+                    emit_record_matches<OUTW>(pm_left, sm.pool, pm_ptr, b + off, sm.stage, sn, ov, tv, lane);
             }
             bool push = e != PT_SKIP;
             if (settle) {
