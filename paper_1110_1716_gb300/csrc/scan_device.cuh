@@ -370,6 +370,15 @@ constexpr uint32_t NFA_CARRY_INLINE = 8;
 // such instances over every SM, instead of in the drain of the warp that
 // queued it.
 constexpr uint32_t NFA_CARRY_AFTER = 256;
+// The same for DFA instances (chained scans): an instance still alive
+// DFA_CARRY_AFTER symbols past its start goes to carry_dfa, one thread per
+// instance over the whole grid. Instances that live that long are the
+// paper's quadratic case (a machine without a dead state: every instance
+// lives to the end of the text), where the early hand-over spreads them over
+// every SM; a shorter bound would also hand over the few longest instances
+// of ordinary scans, whose tail in the carry kernel then costs more than it
+// saves in the drain.
+constexpr uint32_t DFA_CARRY_AFTER = 256;
 
 // One staged tile: bytes [b, b + len) of a text are in shared memory.
 struct TileView {
@@ -561,9 +570,10 @@ __device__ void drain_dfa(const OView &ov, const MView &mv, const TileView &tv, 
         if (act) {
             if (pos >= n) {
                 act = false;
-            } else if (pos >= tile_end && !gmode) {
-                // chained: hand the instance to the carry queue; lazy (no
-                // queue) or a full queue: continue on the global text
+            } else if ((pos >= tile_end || pos - start >= DFA_CARRY_AFTER) && ov.carry_cap && !gmode) {
+                // chained: hand the instance to the carry queue past the
+                // staged text, or DFA_CARRY_AFTER symbols past its start;
+                // lazy (no queue) or a full queue: continue in place
                 const uint32_t ci = ov.carry_cap ? atomicAdd(ov.carry_n, 1u) : 0u;
                 if (ci < ov.carry_cap) {
                     uint32_t *c = ov.carry + 4 * ci;

@@ -7,30 +7,59 @@
 namespace pfsm {
 
 // ------------------------------------------------------------ DFA carry queue
-// Continues DFA instances that outlived their tile's staged text, reading the
-// text from global memory (chained data partitioning, Sec. III.D.2). Entries
-// are {job, start, pos, state}.
+// Continues DFA instances that outlived their tile's staged text (or ran
+// DFA_CARRY_AFTER symbols), one thread per instance, reading the text from
+// global memory (chained data partitioning, Sec. III.D.2). Entries are {job,
+// start, pos, state}. A table of at most 48 KB is read from a shared copy
+// (dynamic shared memory of the launch; none otherwise). The matches of the
+// lanes that report together are appended with one atomic.
 __global__ void __launch_bounds__(256) carry_dfa(const ScanArgs a) {
     // launched as a programmatic dependent of the tile kernel: its launch
     // overlaps the tile kernel's end, and this waits for that kernel to
     // complete (and its writes to be visible) before the queue is read
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nc = min(*a.carry_n, a.carry_cap);
+    if (blockIdx.x * blockDim.x >= nc) return;
     const uint64_t pol_keep = policy_evict_last();
-    const OView ov{a.out, a.cap, a.status, nullptr, a.carry, a.carry_n, a.carry_cap, a.stage_n};
+    const uint32_t QS = static_cast<uint32_t>(a.Q) * a.S;
+    const bool tab_sm = QS * 2 <= 48 * 1024;
+    const uint16_t *tab = a.dtab;
+    if (tab_sm) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(smem);
+        const uint32_t *g = reinterpret_cast<const uint32_t *>(a.dtab);
+        for (uint32_t i = threadIdx.x; i < (QS + 1) / 2; i += blockDim.x) d[i] = __ldg(g + i);
+        __syncthreads();
+        tab = reinterpret_cast<const uint16_t *>(smem);
+    }
+    const int lane = threadIdx.x & 31;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nc;
          idx += gridDim.x * blockDim.x) {
-        const uint32_t *c = a.carry + 4 * idx;
-        const uint32_t start = c[1];
-        uint32_t pos = c[2], s = c[3];
+        const uint4 c = *reinterpret_cast<const uint4 *>(a.carry + 4 * idx);
+        const uint32_t start = c.y;
+        uint32_t pos = c.z, s = c.w;
         while (pos < a.n) {
             const uint32_t ch = __ldg(a.text + pos);
             if (ch >= static_cast<uint32_t>(a.S)) break;
             if (!PFSM_OK_IDX(s < static_cast<uint32_t>(a.Q), a.status)) break;
-            const uint16_t e = ldg_u16_keep(a.dtab + s * a.S + ch, pol_keep);
+            const uint32_t ix = s * a.S + ch;
+            const uint16_t e = tab_sm ? tab[ix] : ldg_u16_keep(a.dtab + ix, pol_keep);
             if (e == DEAD16) break;
             s = e & 0x7FFFu;
-            if (e & FINAL_BIT) emit_direct<3>(ov, 0u, start, pos, s);
+            if (e & FINAL_BIT) {
+                // the lanes that report at this point together: one atomic
+                const uint32_t grp = __activemask();
+                const int lead = __ffs(grp) - 1;
+                unsigned long long base = 0;
+                if (lane == lead) base = atomicAdd(&a.status[0], static_cast<unsigned long long>(__popc(grp)));
+                base = __shfl_sync(grp, base, lead) + __popc(grp & lanemask_lt());
+                if (base < a.cap) {
+                    uint32_t *o = a.out + base * 3;
+                    o[0] = start;
+                    o[1] = pos;
+                    o[2] = s;
+                }
+            }
             ++pos;
         }
     }
@@ -167,7 +196,9 @@ cudaError_t launch_carry(const ScanArgs &a, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(grid));
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
+    // the table's shared copy (carry_dfa takes it when it is at most 48 KB)
+    const uint32_t tab_bytes = static_cast<uint32_t>(a.Q) * a.S * 2;
+    cfg.dynamicSmemBytes = tab_bytes <= 48 * 1024 ? ((tab_bytes + 3) & ~3u) : 0u;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

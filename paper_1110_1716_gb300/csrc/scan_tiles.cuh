@@ -100,20 +100,6 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
         fence_mbar_init();
     }
     __syncthreads();   // barriers initialised, the byte table expanded
-    if (b_all) {
-        // the bulk copies of the tables (bounded wait; on a timeout the
-        // CTA waits once more for them, bounded, and leaves)
-        if (tid == 0 && !mbar_wait_bounded(&misc->bar[1], 0)) misc->abort = 2;
-        __syncthreads();
-        if (misc->abort == 2) {
-            if (tid == 0) {
-                atomicOr(&a.status[1], ERR_TIMEOUT);
-                mbar_wait_bounded(&misc->bar[1], 0);
-            }
-            return;
-        }
-    }
-
     const uint32_t n = a.n;
     const uint32_t nb = a.nbuf;   // staged tile buffers, <= kTileBufs
     // this CTA's k-th tile is blockIdx.x + k * gridDim.x
@@ -134,6 +120,26 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
                     reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(a.text) + b - a.shift),
                     bytes, &misc->full[buf], pol_stream);
     };
+    // short texts: the first tile's copy goes out with the tables' copies
+    // still in flight, so the two round trips overlap
+    if constexpr (!PIPE) {
+        if (tid == 0 && my_tiles > 0) issue(0);
+    }
+    if (b_all) {
+        // the bulk copies of the tables (bounded wait; on a timeout the
+        // CTA waits once more for them and for a tile copy it issued,
+        // bounded, and leaves)
+        if (tid == 0 && !mbar_wait_bounded(&misc->bar[1], 0)) misc->abort = 2;
+        __syncthreads();
+        if (misc->abort == 2) {
+            if (tid == 0) {
+                atomicOr(&a.status[1], ERR_TIMEOUT);
+                mbar_wait_bounded(&misc->bar[1], 0);
+                if (!PIPE && my_tiles > 0) mbar_wait_bounded(&misc->full[0], 0);
+            }
+            return;
+        }
+    }
     uint32_t sn = 0;
     uint32_t wq_n = 0;   // entries in this warp's queue
     Pend pend{0u, 0u, 0u, 0u, false};   // the start this lane holds (lane-local settling,
@@ -224,7 +230,6 @@ __global__ void __launch_bounds__(SPT == 8 || KIND == 1 ? 512 : 544, 1) scan_til
             if (lane == 0) mbar_arrive(&misc->empty[buf]);
         }
     } else {
-        if (tid == 0 && my_tiles > 0) issue(0);
         for (uint32_t k = 0; k < my_tiles; ++k) {
             const int buf = static_cast<int>(k & 1);
             const uint32_t tile = blockIdx.x + k * gridDim.x;
