@@ -75,6 +75,13 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ BatchArgs A;
     __shared__ UnitDesc desc[kTileBufs];
+    // The views of the current machine and of the output live in shared
+    // memory: read from the machine table in global memory they would
+    // otherwise stay in registers across a whole tile (the NFA classes run
+    // at 128 registers per thread). ovs[1] is the lazy form (no carry).
+    __shared__ MView mv_sh;
+    __shared__ OView ovs[2];
+    __shared__ UnitDesc prev_sh[16];   // per filtering warp: its previous tile
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int NT = blockDim.x;
     const int NC = NT - 32;   // filtering threads
@@ -94,8 +101,13 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     uint8_t *arena = smem + A.sm_arena;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
-    const OView ov{A.sa.out, A.sa.cap, A.sa.status, A.job_counts, A.sa.carry, A.sa.carry_n,
-                   A.sa.carry_cap, A.sa.stage_n};
+    if (tid == 0) {
+        ovs[0] = OView{A.sa.out, A.sa.cap, A.sa.status, A.job_counts, A.sa.carry, A.sa.carry_n,
+                       A.sa.carry_cap, A.sa.stage_n};
+        ovs[1] = ovs[0];
+        ovs[1].carry_cap = 0;
+    }
+    const OView &ov = ovs[0];
     if (tid == 0) {
         for (int i = 0; i < kTileBufs; ++i) {
             mbar_init(&misc->full[i], 1);
@@ -234,8 +246,8 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     Smem smi = sm;
     // the previous tile's text: its queue is drained when the text changes
     bool have_prev = false;
-    UnitDesc prev{};
-    OView prev_ov = ov;
+    UnitDesc &prev = prev_sh[wid];
+    const OView *prev_ov = &ovs[0];
     // every filtering warp arrives and waits (bounded)
     auto meet_all = [&]() -> bool {
         __syncwarp();
@@ -247,17 +259,19 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
     // drains this warp's queue of the previous text (reading it from global
     // memory: its staged tile may be gone) and flushes its staged matches
     auto drain_prev = [&]() {
-        const MView pmv = mview_of(A.machs[prev.mach], A.sa.status);
+        // the arena and mv_sh still hold the previous tile's machine: a
+        // machine change restages them only after this drain
+        const MView &pmv = mv_sh;
         const TileView ptv{text_sm, prev.text, 0u, 0u, prev.n, prev.job, prev.orig};
         // the starts this warp still holds for the previous text (lane-local
         // settling, deferred deep-bitmap loads) go first: the arena still
         // holds that machine's tables
         if (KIND == 1 && __any_sync(0xffffffffu, pend.on))
-            settle_lanes<KIND, TAB, 4>(prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep,
+            settle_lanes<KIND, TAB, 4>(*prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep,
                                        static_cast<uint32_t>(A.machs[prev.mach].settle));
         if (KIND == 0 && __any_sync(0xffffffffu, pend.on))
-            dfa_consume<TAB, 4>(prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep);
-        drain<KIND, TAB, 4>(prev_ov, pmv, ptv, smi, wq_n, sn, lane, pol_keep);
+            dfa_consume<TAB, 4>(*prev_ov, pmv, ptv, smi, pend, wq_n, sn, lane, pol_keep);
+        drain<KIND, TAB, 4>(*prev_ov, pmv, ptv, smi, wq_n, sn, lane, pol_keep);
         stage_flush<4>(sm.stage, sn, ov, prev.orig, lane);
     };
     for (uint32_t k = 0;; ++k) {
@@ -297,6 +311,7 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
             smi.pool = M.a_pool != kNotStaged ? reinterpret_cast<const uint32_t *>(arena + M.a_pool) : M.pool;
             smi.coop = M.a_coop != kNotStaged
                            ? reinterpret_cast<uint32_t *>(arena + M.a_coop) + wid * 2 * M.Wq : sm.coop;
+            if (tid == 0) mv_sh = mview_of(M, A.sa.status);
             cur_mach = d.mach;
             if (!meet_all()) {
                 if (lane == 0) atomicOr(&A.sa.status[1], ERR_TIMEOUT);
@@ -304,12 +319,11 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
                 break;
             }
         }
-        const MView mv = mview_of(M, A.sa.status);
+        const MView &mv = mv_sh;
         const TileView tv{text_sm + buf * A.sa.text_buf, d.text, d.b, d.len, d.n, d.job, d.orig};
-        OView ovm = ov;
         // lazy partitioning for this machine; NFA machines of a batch are
         // always lazy (the batch carry queue holds DFA entries only)
-        if (M.lazy || KIND == 1) ovm.carry_cap = 0;
+        const OView &ovm = ovs[(M.lazy || KIND == 1) ? 1 : 0];
         smi.pk = pk_sm + buf * A.sa.pk_words;
         const uint32_t own_end = min(d.b + A.sa.tile, d.n);
         process_tile<KIND, SB, TAB, 4, 32, true>(ovm, mv, tv, smi, own_end, wq_n, sn, bad_symbol,
@@ -317,8 +331,9 @@ __global__ void __launch_bounds__(KIND == 1 ? 512 : 544, 1) scan_units(const Bat
         __syncwarp();
         if (lane == 0) mbar_arrive(&misc->empty[buf]);
         have_prev = true;
-        prev = d;
-        prev_ov = ovm;
+        if (lane == 0) prev = d;
+        __syncwarp();
+        prev_ov = &ovm;
     }
     if (have_prev && !aborted) drain_prev();
     if (bad_symbol) atomicOr(&A.sa.status[1], ERR_SYMBOL);

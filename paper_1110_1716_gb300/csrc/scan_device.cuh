@@ -347,13 +347,14 @@ struct OView {
     uint32_t *carry_n;                // DFA: [0] entries. NFA: see NFA_CARRY_WORDS
     uint32_t carry_cap;               // entries (0: lazy partitioning)
     uint32_t stage_n;                 // per-warp staging capacity (entries)
-    uint16_t *cpool = nullptr;        // NFA: states of carried sets of more than
-    uint32_t cpool_cap = 0;           //   NFA_CARRY_INLINE states
+    // (members below are zero when an initialiser list stops before them)
+    uint16_t *cpool;                  // NFA: states of carried sets of more than
+    uint32_t cpool_cap;               //   NFA_CARRY_INLINE states
     // NFA, single text: an instance started at i is carried from the end of
     // its own tile's staged text, min(n, (i / seg_tile + 1) seg_tile +
     // seg_halo), or from i + NFA_CARRY_AFTER if that comes first; seg_tile
     // 0: from the end of the tile staged when it runs
-    uint32_t seg_tile = 0, seg_halo = 0;
+    uint32_t seg_tile, seg_halo;
 };
 
 // NFA carry queue: entries of 8 words {job, start, pos, n, ...}. The first
