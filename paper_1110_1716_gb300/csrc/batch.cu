@@ -167,7 +167,7 @@ static int class_shape(pfsm_ctx *ctx, int cls) {
     a.nbuf = kind ? 3 : 2;
     const uint32_t share = ctx->smem_sm / static_cast<uint32_t>(ctas);
     const uint32_t budget =
-        std::min<uint32_t>(kSmemMax, share > ctx->smem_rsv ? share - ctx->smem_rsv : 0) - kSmemStatic;
+        std::min<uint32_t>(kSmemMax, share > ctx->smem_rsv ? share - ctx->smem_rsv : 0) - kBatchSmemStatic;
     uint32_t base = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
         a.tile = tile;

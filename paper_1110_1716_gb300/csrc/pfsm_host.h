@@ -16,7 +16,8 @@ namespace pfsm {
 constexpr uint64_t kDefaultBudget = 8ull << 30;
 constexpr uint32_t kCarryCap = 1u << 20;     // carry entries per stream slot
 constexpr uint32_t kSmemMax = 232448;        // opt-in shared memory per CTA
-constexpr uint32_t kSmemStatic = 2048;       // room left for static shared memory (batch kernels: 1.5 KB)
+constexpr uint32_t kSmemStatic = 1024;       // room left for static shared memory (single-text kernels: none)
+constexpr uint32_t kBatchSmemStatic = 2048;  // the batch class kernels' static shared memory (1.5 KB)
 constexpr int kEventRing = 256;              // timed launches kept in flight per stream
 
 struct Machine {
