@@ -846,7 +846,7 @@ __device__ __forceinline__ bool carry_nfa_lane(const OView &ov, uint32_t job, ui
 // The whole warp hands the set in `bits` (a bitset over Q) to the carry
 // queue, its states in cpool. False, with nothing queued, when there is no
 // room (an entry claimed without pool room is written empty).
-static __device__ __noinline__ bool carry_nfa_warp(const OView &ov, const MView &mv, uint32_t job,
+__device__ __forceinline__ bool carry_nfa_warp(const OView &ov, const MView &mv, uint32_t job,
                                                    uint32_t start, uint32_t pos, const uint32_t *bits,
                                                    int lane) {
     const uint32_t Wq = mv.Wq;
@@ -915,10 +915,11 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t x, uint32_t k) {
 // (chained partitioning) and room is left, otherwise it reads the global
 // text on (lazy).
 template <int OUTW>
-__device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
-                                      const uint32_t *band, const TileView &tv,
-                                      uint32_t *bits0, uint32_t *bits1, uint32_t start,
-                                      uint32_t pos, uint32_t seg_end, int lane, uint64_t pol_keep) {
+__device__ __forceinline__ void coop_run_body(const OView &ov, const MView &mv,
+                                              const uint32_t *band, const TileView &tv,
+                                              uint32_t *bits0, uint32_t *bits1, uint32_t start,
+                                              uint32_t pos, uint32_t seg_end, int lane,
+                                              uint64_t pol_keep) {
     const uint32_t Wq = mv.Wq, S = mv.S, n = tv.n;
     // single-text scans only: a batch's NFA machines are always lazy
     bool chain = OUTW == 3 && ov.carry_cap > 0;
@@ -977,6 +978,28 @@ __device__ __noinline__ void coop_run(const OView &ov, const MView &mv,
         __syncwarp();
     }
     __syncwarp();
+}
+
+// The batch kernels call the warp-wide run out of line (inlined, it costs
+// their NFA classes hundreds of bytes of spills at 128 registers); the
+// single-text kernels inline it, so that the views it reads need no stack
+// copy at every drain.
+template <int OUTW>
+__device__ __noinline__ void coop_run_call(const OView &ov, const MView &mv, const uint32_t *band,
+                                           const TileView &tv, uint32_t *bits0, uint32_t *bits1,
+                                           uint32_t start, uint32_t pos, uint32_t seg_end, int lane,
+                                           uint64_t pol_keep) {
+    coop_run_body<OUTW>(ov, mv, band, tv, bits0, bits1, start, pos, seg_end, lane, pol_keep);
+}
+template <int OUTW>
+__device__ __forceinline__ void coop_run(const OView &ov, const MView &mv, const uint32_t *band,
+                                         const TileView &tv, uint32_t *bits0, uint32_t *bits1,
+                                         uint32_t start, uint32_t pos, uint32_t seg_end, int lane,
+                                         uint64_t pol_keep) {
+    if constexpr (OUTW == 3)
+        coop_run_body<OUTW>(ov, mv, band, tv, bits0, bits1, start, pos, seg_end, lane, pol_keep);
+    else
+        coop_run_call<OUTW>(ov, mv, band, tv, bits0, bits1, start, pos, seg_end, lane, pol_keep);
 }
 
 enum : uint32_t { MODE_LANE = 0, MODE_COOP_SLOT = 1, MODE_COOP_POOL = 2 };
