@@ -514,6 +514,11 @@ def compact_configs(main_name, main, others, detail):
             "served_gbps": r4(sv["served_gbps"]), "burst_rps": r4(sv["burst_req_per_s"]),
             "plain_rps": r4(sv["plain_req_per_s"]),
             "p99_by_load": {k: r4(v["p99_ms"]) for k, v in sv["loads"].items()},
+            # the longest pass of the scheduler loop at each load, and how much
+            # of it the loop's thread spent on a CPU
+            "max_pass_ms_by_load": {k: [r4(v["max_loop_gap_ms"]),
+                                        r4(v["max_loop_gap_parts"].get("thread_cpu_ms", 0.0))]
+                                    for k, v in sv["loads"].items()},
             "small_budget": {"p50_ms": r4(sv["small_budget"]["p50_ms"]),
                              "p99_ms": r4(sv["small_budget"]["p99_ms"]),
                              "evictions": sv["small_budget"]["evictions"]}}
@@ -749,6 +754,7 @@ def measure_serving(P, pf_unused, torch, dev, n_req=100_000, loads=(0.25, 0.5, 0
                 "mean_ms": st["mean_ms"], "served_gbps": nbytes / el / 1e9, "matches_per_s": m / el,
                 "batches": st["batches"], "nomem_splits": st["nomem_splits"],
                 "max_loop_gap_ms": st["max_loop_gap_ms"], "max_loop_gap_at_s": st["max_loop_gap_at_s"],
+                "max_loop_gap_parts": st["max_loop_gap_parts"],
                 "max_batch_ms": st["max_batch_ms"], "max_admit_ms": st["max_admit_ms"],
                 "max_complete_ms": st["max_complete_ms"],
                 "evictions": st["residency_evictions"] - before["evictions"],

@@ -133,6 +133,7 @@ class Server:
         self.latencies: List[float] = []
         self.max_loop_gap_s = 0.0
         self.max_loop_gap_at = 0.0
+        self.max_loop_gap_parts = {}
         self.max_batch_s = 0.0
         self.max_admit_s = 0.0
         self.max_complete_s = 0.0
@@ -310,15 +311,24 @@ class Server:
         i, k = 0, len(due)
         self.running = True
         prev = time.perf_counter()
+        prev_cpu = time.thread_time()
+        parts = [0.0, 0.0, 0.0, 0.0]   # the last pass: intake, completion, admission, sleep
         try:
             while True:
                 now = time.perf_counter()
-                # the longest time the loop did not run (a stall of the host
-                # thread, as opposed to a batch that took long on the device)
+                cpu = time.thread_time()
+                # the longest pass of the loop (a stall of the host thread, as
+                # opposed to a batch that took long on the device), with where
+                # its time went and how much of it this thread was on a CPU
                 if now - prev > self.max_loop_gap_s:
                     self.max_loop_gap_s = now - prev
                     self.max_loop_gap_at = now - t0
+                    self.max_loop_gap_parts = {
+                        "intake_ms": parts[0] * 1e3, "complete_ms": parts[1] * 1e3,
+                        "admit_ms": parts[2] * 1e3, "sleep_ms": parts[3] * 1e3,
+                        "thread_cpu_ms": (cpu - prev_cpu) * 1e3}
                 prev = now
+                prev_cpu = cpu
                 with self.lock:
                     while i < k and due[i] <= now:
                         r = Request(self.next_rid, int(auts[i]),
@@ -327,6 +337,7 @@ class Server:
                         self.pending.append(r)
                         futs.append(r.future)
                         i += 1
+                t1 = time.perf_counter()
                 progressed = False
                 for slot in self.slots:
                     if slot.busy and slot.done.query():
@@ -334,17 +345,20 @@ class Server:
                         self._complete(slot)
                         self.max_complete_s = max(self.max_complete_s, time.perf_counter() - tc)
                         progressed = True
+                t2 = time.perf_counter()
                 for slot in self.slots:
                     if not slot.busy:
                         ta = time.perf_counter()
                         if self._admit(slot):
                             progressed = True
                         self.max_admit_s = max(self.max_admit_s, time.perf_counter() - ta)
+                t3 = time.perf_counter()
                 if i >= k and not self.pending and not any(s.busy for s in self.slots):
                     break
                 if not progressed:
                     nxt = due[i] if i < k else now + 20e-6
                     time.sleep(max(0.0, min(nxt - time.perf_counter(), 20e-6)))
+                parts = [t1 - now, t2 - t1, t3 - t2, time.perf_counter() - t3]
         finally:
             self.running = False
             if gc_was_enabled:
@@ -357,6 +371,7 @@ class Server:
         self.latencies = []
         self.max_loop_gap_s = 0.0   # longest pass of the trace loop
         self.max_loop_gap_at = 0.0  # its end, in seconds from the trace start
+        self.max_loop_gap_parts = {}  # that pass: time per step and on-CPU time
         self.max_batch_s = 0.0      # longest batch, launch to completion seen
         self.max_admit_s = 0.0      # longest packing + launch of a batch
         self.max_complete_s = 0.0   # longest hand-back of a batch's results
@@ -374,6 +389,7 @@ class Server:
                 "mean_ms": float(lat.mean() * 1e3), "batches": self.batches,
                 "max_loop_gap_ms": self.max_loop_gap_s * 1e3,
                 "max_loop_gap_at_s": self.max_loop_gap_at,
+                "max_loop_gap_parts": dict(self.max_loop_gap_parts),
                 "max_batch_ms": self.max_batch_s * 1e3,
                 "max_admit_ms": self.max_admit_s * 1e3,
                 "max_complete_ms": self.max_complete_s * 1e3,
