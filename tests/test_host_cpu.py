@@ -79,6 +79,20 @@ def test_tuner_descent_finds_the_minimum_axis_by_axis():
     assert evals == len(calls) and len({json.dumps(c, sort_keys=True) for c in calls}) == evals
 
 
+def test_tuner_descent_keeps_the_start_unless_a_candidate_wins_by_the_margin():
+    """A candidate replaces the best only when it takes less than `gain`
+    times its time: a 2 % gain is noise for the batch tuner (gain 0.97) and
+    a win for the single-scan tuner (gain 0.99)."""
+    from paper_1110_1716_gb300 import tune
+    cost = {0: 1.00, 1: 0.98, 2: 0.90}
+
+    def timer(p):
+        return cost[p["a"]] if p["a"] != 2 else None   # 2 does not fit
+
+    assert tune._descend({"a": 0}, {"a": [0, 1, 2]}, timer, gain=0.97)[0] == {"a": 0}
+    assert tune._descend({"a": 0}, {"a": [0, 1, 2]}, timer, gain=0.99)[0] == {"a": 1}
+
+
 # ---------------------------------------------------------------- serving: batch packing
 class _Req:
     def __init__(self, aut, n):
