@@ -298,13 +298,25 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
         pl.machs.push_back(d);
     }
     // jobs grouped by class, then by machine, so that consecutive units share
-    // tables; a sort of packed keys (class, slot, job index) keeps the order
-    // of the caller's jobs within a machine
-    std::vector<uint64_t> key(static_cast<size_t>(k));
-    for (int32_t i = 0; i < k; ++i)
-        key[i] = (static_cast<uint64_t>(cls_of[job_slot[i]]) << 56) |
-                 (static_cast<uint64_t>(job_slot[i]) << 32) | static_cast<uint32_t>(i);
-    std::sort(key.begin(), key.end());
+    // tables, keeping the order of the caller's jobs within a machine: a
+    // counting sort over the machine slots, taken in (class, slot) order
+    std::vector<uint32_t> slot_order(ids.size());
+    for (size_t i = 0; i < ids.size(); ++i) slot_order[i] = static_cast<uint32_t>(i);
+    std::sort(slot_order.begin(), slot_order.end(), [&](uint32_t x, uint32_t y) {
+        return cls_of[x] != cls_of[y] ? cls_of[x] < cls_of[y] : x < y;
+    });
+    std::vector<uint32_t> first(ids.size() + 1, 0);
+    for (int32_t i = 0; i < k; ++i) first[job_slot[i] + 1]++;
+    {
+        std::vector<uint32_t> count(first.begin() + 1, first.end());
+        uint32_t at = 0;
+        for (uint32_t sl : slot_order) {
+            first[sl] = at;
+            at += count[sl];
+        }
+    }
+    std::vector<uint32_t> key(static_cast<size_t>(k));   // job indices in (class, slot, index) order
+    for (int32_t i = 0; i < k; ++i) key[first[job_slot[i]]++] = static_cast<uint32_t>(i);
     uint64_t tiles_of[kBatchClasses] = {};
     for (int32_t i = 0; i < k; ++i) {
         const int c = cls_of[job_slot[i]];
@@ -319,7 +331,7 @@ static int plan_batch(pfsm_ctx *ctx, const pfsm_job *jobs, int32_t k, BatchPlan 
     int cur = -1;
     pl.jobs.reserve(static_cast<size_t>(k));
     for (int32_t r = 0; r < k; ++r) {
-        const int32_t x = static_cast<int32_t>(key[r] & 0xFFFFFFFFu);
+        const int32_t x = static_cast<int32_t>(key[r]);
         const pfsm_job &j = jobs[x];
         const uint32_t slot = job_slot[x];
         const int c = cls_of[slot];
