@@ -961,7 +961,12 @@ int scan_enqueue(pfsm_ctx *ctx, pfsm_aut aut, const uint8_t *text, uint64_t n, u
     if (pl.a.carry_cap && ctx->test_carry_cap) pl.a.carry_cap = std::min(pl.a.carry_cap, ctx->test_carry_cap);
     if (pl.a.cpool_cap && ctx->test_cpool_cap) pl.a.cpool_cap = std::min(pl.a.cpool_cap, ctx->test_cpool_cap);
     if (m.kind == 1 && !pl.a.coop_smem) {
-        const size_t need = static_cast<size_t>(pl.grid) * (pl.threads / 32) * 2 * m.dm.Wq;
+        // one pair of bitsets per warp of the tile kernel and, when the scan
+        // is chained, of the carry kernel (nsm CTAs of up to 256 threads)
+        size_t warps = static_cast<size_t>(pl.grid) * (pl.threads / 32);
+        if (pl.a.carry_cap)
+            warps = std::max(warps, static_cast<size_t>(ctx->nsm) * (std::min(pl.threads, 256) / 32));
+        const size_t need = warps * 2 * m.dm.Wq;
         if (ensure_words(&slot->coop, &slot->coop_words, need)) return PFSM_E_NOMEM;
         pl.a.coop_g = slot->coop;
     }

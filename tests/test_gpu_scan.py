@@ -327,6 +327,28 @@ def test_nfa_chained_partitioning_with_a_full_carry_queue(pf, K):
     assert np.array_equal(got, want)
 
 
+def test_nfa_chained_partitioning_with_bitsets_in_global_memory(pf):
+    """The live core of 24 states padded with unreachable states to Q =
+    12,288: the warp-wide bitsets (2 x 384 words per warp) no longer fit the
+    tile kernel's shared memory, so they and the carry kernel's live in a
+    global scratch sized for both kernels' warps; a short text (few tile-kernel
+    CTAs, a full grid of carry CTAs) against the oracle."""
+    core = W.live_core_nfa(24, 9)
+    Q = 12_288
+    bits = np.zeros((Q, core.S, Q // 32), dtype=np.uint32)
+    bits[:core.Q, :, :core.bits.shape[2]] = core.bits
+    fin = np.zeros(Q, dtype=np.uint8)
+    fin[:core.Q] = core.final
+    m = W.Nfa(bits=bits, q0=core.q0, final=fin)
+    a = pf.load(m)
+    P.pfsm_set_params(pf.ctx, a, {"tile": 4096, "halo": 16, "partition": 2})
+    t = W.text_uniform(6000, 4, 13)
+    want = oracle.scan(core, t)
+    assert len(want) > 100_000
+    assert np.array_equal(gpu_matches(pf, a, t, cap=len(want) + 16), want)
+    P.pfsm_unload(pf.ctx, a)
+
+
 def test_nfa_chained_partitioning_on_cyclic_sets(pf):
     """Random cyclic NFAs (sets grow and shrink; seeds picked so that
     thousands of matches come from instances that crossed the first tile's
