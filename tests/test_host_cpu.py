@@ -157,3 +157,36 @@ def test_bench_work_rate_counts_pair_steps():
     assert w["matches_agree"] and w["oracle_matches"] == res["matches"]
     assert w["achieved"] == w["pair_steps"] / 2e-3
     assert "frac" not in w and "peak" not in w
+
+
+def test_bench_compact_configs_keep_every_config():
+    """The one-line summary at the end of the bench line has an entry per
+    configuration (c0-c4 and both lazy/chained comparisons), with the
+    scheduler's longest pass and its on-CPU time per load."""
+    import bench
+
+    def scan(gbps):
+        return {"gbps": gbps, "kernel_ms": 0.1, "roofline": {"frac": 0.1},
+                "e2e": {"value": 1.0}, "matches": 7, "load_ms": 3.0, "device_bytes": 2e6}
+
+    loads = {k: {"p99_ms": 2.0, "max_loop_gap_ms": 9.0,
+                 "max_loop_gap_parts": {"thread_cpu_ms": 8.5}} for k in ("0.25", "0.5")}
+    others = {
+        "dna_dfa_1mib": scan(20.0), "byte_trie_1gib": scan(1400.0),
+        "batch_10k_texts": {"gbps": 240.0, "device_gbps": 260.0, "roofline": {"frac": 0.04},
+                            "e2e": {"value": 110.0}, "plain_gbps": 3.4, "speedup_vs_plain": 70.0,
+                            "params_source": "autotuner", "tuned_batch": {"threads": 0},
+                            "default_params_device_ms": 4.3, "device_ms": 4.3},
+        "long_lived_dfa_16kib": {"lazy": {"ms": 160.0}, "chained": {"ms": 12.0}, "matches": 5},
+        "long_lived_nfa_16kib": {"lazy": {"ms": 860.0}, "chained": {"ms": 100.0}, "matches": 6},
+        "serving": {"p50_ms": 1.0, "p99_ms": 5.0, "offered_load": 0.5, "served_gbps": 0.3,
+                    "burst_req_per_s": 5e4, "plain_req_per_s": 1e4, "loads": loads,
+                    "small_budget": {"p50_ms": 1.5, "p99_ms": 10.0, "evictions": 3}},
+    }
+    out = bench.compact_configs("motif_nfa_64mib", scan(300.0), others, {"main": {}})
+    assert list(out) == ["c0_dna_dfa_1mib", "c1_motif_nfa_64mib", "c2_byte_trie_1gib",
+                         "c3_batch_10k_texts", "f2_long_lived_dfa_16kib",
+                         "f2_long_lived_nfa_16kib", "c4_serving"]
+    assert out["f2_long_lived_nfa_16kib"] == {"lazy_ms": 860.0, "chained_ms": 100.0, "matches": 6}
+    assert out["c4_serving"]["max_pass_ms_by_load"]["0.25"] == [9.0, 8.5]
+    assert out["c3_batch_10k_texts"]["params_source"] == "autotuner"
